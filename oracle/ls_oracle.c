@@ -161,15 +161,31 @@ static void base_sort_u64(uint64_t* a, uint64_t n) {
 
 /* ----------------------------------------------------------------- RMI */
 
+/* Fixed pairwise tree over chunk partials: while more than one value is
+ * left, p[i] = p[2i] + p[2i+1] for each pair, an odd last value is carried
+ * up unchanged.  Empty input sums to +0.0. */
+static double tree_sum(double* p, uint64_t m) {
+  if (m == 0) return 0.0;
+  while (m > 1) {
+    uint64_t h = m / 2;
+    for (uint64_t i = 0; i < h; ++i) p[i] = p[2 * i] + p[2 * i + 1];
+    if (m & 1) p[h] = p[m - 1];
+    m = h + (m & 1);
+  }
+  return p[0];
+}
+
 /* The four least-squares sums over sample positions j in [st, en) of the
  * sorted sample, with X_j = v(s_j) - x0 and y_j = j / S (the empirical CDF
  * of Sec. 2.1: pos = N * P(A <= x)).  Canonical order: consecutive chunks
- * of 256 positions from st, each summed left to right from +0.0, then the
- * chunk partials summed left to right from +0.0. */
+ * of 256 positions from st, each summed left to right from +0.0; the chunk
+ * partials are then combined by tree_sum. */
 static void ls_sums(const uint64_t* s_ord, int dtype, uint64_t st, uint64_t en, double x0, uint64_t S,
                     double out[4]) {
-  double tot0 = 0.0, tot1 = 0.0, tot2 = 0.0, tot3 = 0.0;
-  for (uint64_t c0 = st; c0 < en; c0 += CHUNK) {
+  uint64_t nch = (en - st + CHUNK - 1) / CHUNK;
+  double* part = (double*)malloc(4 * (nch ? nch : 1) * sizeof(double));
+  uint64_t c = 0;
+  for (uint64_t c0 = st; c0 < en; c0 += CHUNK, ++c) {
     uint64_t c1 = (en - c0 > CHUNK) ? c0 + CHUNK : en;
     double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
     for (uint64_t j = c0; j < c1; ++j) {
@@ -182,15 +198,13 @@ static void ls_sums(const uint64_t* s_ord, int dtype, uint64_t st, uint64_t en, 
       p2 = p2 + xy;
       p3 = p3 + xx;
     }
-    tot0 = tot0 + p0;
-    tot1 = tot1 + p1;
-    tot2 = tot2 + p2;
-    tot3 = tot3 + p3;
+    part[c] = p0;
+    part[nch + c] = p1;
+    part[2 * nch + c] = p2;
+    part[3 * nch + c] = p3;
   }
-  out[0] = tot0;
-  out[1] = tot1;
-  out[2] = tot2;
-  out[3] = tot3;
+  for (int k = 0; k < 4; ++k) out[k] = tree_sum(part + k * nch, nch);
+  free(part);
 }
 
 /* Closed-form simple linear regression y = a X + b from the sums, slope
@@ -387,18 +401,41 @@ void lsref_fit_forward(const lsref_model* m, const uint64_t* sorted_sample, uint
  * to each leaf's (a_i, b_i) and the root's (a, b):
  *   dMSE/da_i = 2/S sum_{j in leaf i} r_j X_j,  dMSE/db_i = 2/S sum r_j,
  * X_j = xc_j - x0_i.  Each leaf's member list (index order) is summed in
- * chunks of 256 members, chunks then summed left to right. */
+ * chunks of 256 members left to right, chunks combined by tree_sum; the
+ * root term likewise over all S points. */
+static void grad_sums(const double* r, const double* X, const uint64_t* idx, uint64_t m, double* s_rx, double* s_r) {
+  uint64_t nch = (m + CHUNK - 1) / CHUNK;
+  double* part = (double*)malloc(2 * (nch ? nch : 1) * sizeof(double));
+  for (uint64_t c = 0; c < nch; ++c) {
+    uint64_t e = (m - c * CHUNK > CHUNK) ? (c + 1) * CHUNK : m;
+    double prx = 0.0, pr = 0.0;
+    for (uint64_t q = c * CHUNK; q < e; ++q) {
+      uint64_t j = idx ? idx[q] : q;
+      double rx = r[j] * X[j];
+      prx = prx + rx;
+      pr = pr + r[j];
+    }
+    part[c] = prx;
+    part[nch + c] = pr;
+  }
+  *s_rx = tree_sum(part, nch);
+  *s_r = tree_sum(part + nch, nch);
+  free(part);
+}
+
 void lsref_fit_backward(const lsref_model* m, const uint64_t* sorted_sample, uint64_t S, int dtype, double* grad_a,
                         double* grad_b, double* grad_root) {
   uint32_t L = m->L;
-  uint32_t* leaf = (uint32_t*)malloc((S ? S : 1) * sizeof(uint32_t));
-  double* tot_rx = (double*)calloc(L, sizeof(double));
-  double* tot_r = (double*)calloc(L, sizeof(double));
-  double* par_rx = (double*)calloc(L, sizeof(double));
-  double* par_r = (double*)calloc(L, sizeof(double));
-  uint64_t* seen = (uint64_t*)calloc(L, sizeof(uint64_t));
+  uint64_t n1 = S ? S : 1;
+  uint32_t* leaf = (uint32_t*)malloc(n1 * sizeof(uint32_t));
+  double* rl = (double*)malloc(n1 * sizeof(double));
+  double* Xl = (double*)malloc(n1 * sizeof(double));
+  double* rr = (double*)malloc(n1 * sizeof(double));
+  double* Xr = (double*)malloc(n1 * sizeof(double));
+  uint64_t* start = (uint64_t*)calloc((size_t)L + 1, sizeof(uint64_t));
+  uint64_t* fill = (uint64_t*)calloc((size_t)L + 1, sizeof(uint64_t));
+  uint64_t* members = (uint64_t*)malloc(n1 * sizeof(uint64_t));
   double Sd = (double)S;
-  double root_rx = 0.0, root_r = 0.0, rp_rx = 0.0, rp_r = 0.0;
   for (uint64_t j = 0; j < S; ++j) {
     double x = lsref_key_value(sorted_sample[j], dtype);
     double xc = dmax(x, m->xmin);
@@ -406,62 +443,44 @@ void lsref_fit_backward(const lsref_model* m, const uint64_t* sorted_sample, uin
     uint32_t i = root_leaf(m, xc);
     leaf[j] = i;
     double y = (double)j / Sd;
-    /* leaf term */
     double X = xc - m->leaf_x0[i];
     double p = m->leaf_a[i] * X;
     p = p + m->leaf_b[i];
-    double r = p - y;
-    double rx = r * X;
-    par_rx[i] = par_rx[i] + rx;
-    par_r[i] = par_r[i] + r;
-    seen[i] += 1;
-    if (seen[i] % CHUNK == 0) {
-      tot_rx[i] = tot_rx[i] + par_rx[i];
-      tot_r[i] = tot_r[i] + par_r[i];
-      par_rx[i] = 0.0;
-      par_r[i] = 0.0;
-    }
-    /* root term */
+    rl[j] = p - y;
+    Xl[j] = X;
     double XR = xc - m->root_x0;
     double pr = m->root_a * XR;
     pr = pr + m->root_b;
-    double rr = pr - y;
-    double rrx = rr * XR;
-    rp_rx = rp_rx + rrx;
-    rp_r = rp_r + rr;
-    if ((j + 1) % CHUNK == 0) {
-      root_rx = root_rx + rp_rx;
-      root_r = root_r + rp_r;
-      rp_rx = 0.0;
-      rp_r = 0.0;
-    }
+    rr[j] = pr - y;
+    Xr[j] = XR;
+    start[i + 1] += 1;
   }
-  if (S % CHUNK != 0) {
-    root_rx = root_rx + rp_rx;
-    root_r = root_r + rp_r;
-  }
+  for (uint32_t i = 0; i < L; ++i) start[i + 1] += start[i];
+  for (uint64_t j = 0; j < S; ++j) members[start[leaf[j]] + fill[leaf[j]]++] = j;
   for (uint32_t i = 0; i < L; ++i) {
-    if (seen[i] % CHUNK != 0) {
-      tot_rx[i] = tot_rx[i] + par_rx[i];
-      tot_r[i] = tot_r[i] + par_r[i];
-    }
-    double ga = 2.0 * tot_rx[i];
-    double gb = 2.0 * tot_r[i];
+    double srx, sr;
+    grad_sums(rl, Xl, members + start[i], start[i + 1] - start[i], &srx, &sr);
+    double ga = 2.0 * srx;
+    double gb = 2.0 * sr;
     grad_a[i] = ga / Sd;
     grad_b[i] = gb / Sd;
   }
   if (grad_root) {
-    double ga = 2.0 * root_rx;
-    double gb = 2.0 * root_r;
+    double srx, sr;
+    grad_sums(rr, Xr, NULL, S, &srx, &sr);
+    double ga = 2.0 * srx;
+    double gb = 2.0 * sr;
     grad_root[0] = ga / Sd;
     grad_root[1] = gb / Sd;
   }
   free(leaf);
-  free(tot_rx);
-  free(tot_r);
-  free(par_rx);
-  free(par_r);
-  free(seen);
+  free(rl);
+  free(Xl);
+  free(rr);
+  free(Xr);
+  free(start);
+  free(fill);
+  free(members);
 }
 
 /* ------------------------------------------------------------ splitter */
