@@ -1,0 +1,230 @@
+/*
+ * ls.h -- C ABI of the GB300 (sm_103a) learned SampleSort library.
+ *
+ * The library sorts arrays of 64-bit keys (IEEE doubles or unsigned 64-bit
+ * integers) in ascending order on one GPU, following arxiv 2307.08637
+ * ("LearnedSort as a learning-augmented SampleSort"):
+ *   - a two-layer RMI F(x) = f2^{floor(B f1(x))}(x) with a linear root and B
+ *     linear leaves (Sec. 2.1), trained in FP64 on a sorted random sample
+ *     (Sec. 2.2, 1% by default), made monotone by per-leaf clamps (Sec. 4);
+ *   - each key goes to bucket floor(B F(x)) (Sec. 2.2 partitioning), which is
+ *     the SampleSort partition of the B-1 implicit learned pivots of Alg. 4;
+ *   - the SampleSort splitter tree with IPS4o equality buckets (Sec. 2.4) is
+ *     the alternative partitioner, chosen by Alg. 5 (BuildPartitionModel)
+ *     or forced through ls_params.partitioner;
+ *   - oversized buckets are partitioned again, all-equal buckets are left as
+ *     they are (homogeneity check, Sec. 2.2), small buckets are sorted by a
+ *     shared-memory base case.
+ *
+ * Keys are ordered by ord(x): for doubles IEEE totalOrder (-0.0 < +0.0),
+ * for u64 the integer order.  NaN keys are rejected.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers on the context's device; h_*
+ *     are host pointers.  The caller owns every buffer it passes in.
+ *   - Calls are asynchronous on the given stream unless stated otherwise.
+ *     Errors that can be seen on the host (bad arguments, too-small
+ *     workspace) are returned before anything is launched and leave the
+ *     buffers untouched.  Errors found on the device (NaN key, a bounded
+ *     wait that ran out) are recorded in a device status word; read it with
+ *     ls_last_device_status().  After such an error the contents of d_keys
+ *     are unspecified (still a permutation of some of the input's bytes).
+ *   - No exceptions cross this boundary.  A context is not thread-safe: use
+ *     one context per host thread.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CUDA stream handle (cudaStream_t), passed as an opaque pointer so this
+ * header needs no CUDA include.  NULL is the legacy default stream. */
+typedef void* ls_stream_t;
+
+typedef enum {
+  LS_OK = 0,
+  LS_EINVAL = 1,    /* bad argument (null pointer, bad dtype, fanout range) */
+  LS_ENOMEM = 2,    /* workspace too small, or host/device allocation failed */
+  LS_ENAN = 3,      /* a key is NaN (f64 only) */
+  LS_ETIMEOUT = 4,  /* a bounded device wait ran out */
+  LS_ECUDA = 5,     /* a CUDA runtime call failed */
+  LS_ENOTIMPL = 6,  /* option not implemented */
+  LS_EDEVICE = 7    /* device-side consistency check failed */
+} ls_status;
+
+typedef enum { LS_F64 = 0, LS_U64 = 1 } ls_dtype;
+
+/* Partition model choice (Alg. 5). */
+typedef enum {
+  LS_PART_AUTO = 0,     /* RMI if n >= min_learned_n, sample dups <= dup_frac
+                           and the sample is not imbalanced; else the tree */
+  LS_PART_LEARNED = 1,  /* always the RMI (tree only if the fit is not finite) */
+  LS_PART_SPLITTER = 2  /* always the splitter tree */
+} ls_partitioner;
+
+/* How a bucket of a learned partition is split again (Sec. 3.3). */
+typedef enum {
+  LS_RECURSE_REFINE_GLOBAL = 0, /* LearnedSort 2.0: sample once, reuse the
+                                   model: child = floor(F B^(k+1)) - B g */
+  LS_RECURSE_RETRAIN = 1        /* AIPS2o: new sample and model per bucket */
+} ls_recurse;
+
+/* Per-key bucket search used by the partition passes.  Every mode gives
+ * identical bucket ids; they differ only in speed. */
+typedef enum {
+  LS_CLASSIFY_AUTO = 0,      /* learned: directory; splitter: tree search */
+  LS_CLASSIFY_DIRECTORY = 1, /* radix directory over the pivots + <=k compares */
+  LS_CLASSIFY_TREE = 2,      /* branchless binary search over the pivots */
+  LS_CLASSIFY_DIRECT = 3     /* learned only: FP64 RMI per key (diagnostic) */
+} ls_classify_mode;
+
+#define LS_MAX_FANOUT 4096
+#define LS_MAX_LEVELS 48
+
+typedef struct {
+  uint32_t fanout;               /* B = RMI leaves = learned buckets, 2..4096 (1000) */
+  uint32_t splitter_fanout;      /* largest splitter-tree fanout B_s, 2..4096 (1024) */
+  uint32_t basecase_threshold;   /* T: buckets with <= T keys go to the base case (16) */
+  uint32_t max_depth;            /* deeper buckets are sorted directly (16) */
+  uint32_t min_sample;           /* sample size floor (256) */
+  uint32_t auto_splitter_fanout; /* B_s when AUTO falls back to the tree (256) */
+  double sample_rate;            /* S = ceil(r n) (0.01) */
+  double dup_frac;               /* Alg. 5 duplicate bound (0.10) */
+  double imbalance_tau;          /* reject the RMI if a sample bucket > tau S/B (8) */
+  uint64_t min_learned_n;        /* Alg. 5 size bound (1e5) */
+  uint64_t seed;                 /* sampling seed */
+  int32_t partitioner;           /* ls_partitioner */
+  int32_t recurse_model;         /* ls_recurse */
+  int32_t classify_mode;         /* ls_classify_mode (speed only) */
+  uint32_t tile_keys;            /* keys per partition tile, 0 = library default */
+} ls_params;
+
+/* The trained two-layer RMI (all FP64), as exported by ls_fit. */
+typedef struct {
+  uint32_t L;          /* number of leaves (= fanout B) */
+  uint32_t S;          /* sample size it was trained on */
+  double xmin, xmax;   /* clamp range: smallest and largest sample key */
+  double root_x0, root_a, root_b;
+  double leaf_x0[LS_MAX_FANOUT];
+  double leaf_a[LS_MAX_FANOUT];
+  double leaf_b[LS_MAX_FANOUT];
+  double leaf_lo[LS_MAX_FANOUT];
+  double leaf_hi[LS_MAX_FANOUT];
+  uint32_t leaf_count[LS_MAX_FANOUT]; /* sample points routed to each leaf */
+} ls_model;
+
+/* Decision codes (per partitioned bucket). */
+#define LS_DEC_NONE 0
+#define LS_DEC_LEARNED 1
+#define LS_DEC_SPLITTER 2
+#define LS_DEC_SPLITTER_EQ 3
+#define LS_DEC_HOMOGENEOUS 4
+
+typedef struct {
+  uint64_t items, learned, splitter, splitter_eq, homogeneous, noprogress;
+  uint64_t base_items, base_keys, fallback_items, fallback_keys;
+  uint64_t keys, max_child, sumsq_child, eq_keys;
+} ls_level_stats;
+
+typedef struct {
+  int32_t status;               /* device status of the call (LS_OK, LS_ENAN, ...) */
+  int32_t root_decision;        /* LS_DEC_* of the first array's root */
+  uint64_t root_sample_size;
+  uint64_t root_dups;           /* #{j >= 1 : ord(s_j) == ord(s_{j-1})} of the root sample */
+  uint64_t root_imbalance_max;  /* largest root-sample bucket under the RMI */
+  uint32_t root_nbuckets;
+  uint32_t levels_used;
+  ls_level_stats level[LS_MAX_LEVELS];
+  double ms_total;              /* host-observed time of the call (stats only) */
+  uint64_t kernel_launches;     /* kernels this call launched */
+} ls_stats;
+
+typedef struct ls_ctx ls_ctx;
+
+/* Fill *p with the defaults listed beside each field of ls_params. */
+void ls_params_default(ls_params* p);
+
+/* Create a context bound to CUDA device `device` (made current inside every
+ * call).  The context owns small pinned host buffers and an optional cached
+ * device buffer for ls_sort_host.  *out is NULL on failure. */
+ls_status ls_create(ls_ctx** out, int device);
+void ls_destroy(ls_ctx* ctx);
+
+/* Bytes of device workspace ls_sort / ls_sort_segmented need for n keys in
+ * nseg segments with these parameters.  The workspace holds an n-key
+ * ping-pong buffer plus tables; it is caller-owned device memory. */
+ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dtype, const ls_params* p,
+                            size_t* bytes);
+
+/* Sort d_keys[0..n) ascending by ord (the sorting problem of Sec. 1-2).
+ * In place from the caller's view; the library ping-pongs through
+ * d_workspace (>= ls_workspace_size bytes, 256-byte aligned).  Stream
+ * ordered; the call synchronises `stream` between recursion levels, so it
+ * returns after the sort is complete.  out_stats (nullable) receives the
+ * decisions and per-level statistics. */
+ls_status ls_sort(ls_ctx* ctx, void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p, void* d_workspace,
+                  size_t ws_bytes, ls_stats* out_stats, ls_stream_t stream);
+
+/* Sort nseg independent arrays: segment s is d_keys[h_offsets[s] ..
+ * h_offsets[s+1]) (host array of nseg+1 non-decreasing offsets).  Every
+ * segment gets its own sample, model and decisions (Alg. 5 per segment).
+ * h_seg_decision (nullable, nseg entries) receives each root decision. */
+ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets, uint32_t nseg, ls_dtype dtype,
+                            const ls_params* p, void* d_workspace, size_t ws_bytes, ls_stats* out_stats,
+                            int32_t* h_seg_decision, ls_stream_t stream);
+
+/* End-to-end sort of a HOST array: copies h_keys to the device, sorts, and
+ * copies the result back (h_keys is overwritten).  Device memory is cached
+ * in the context between calls.  Synchronous. */
+ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, const ls_params* p, ls_stats* out_stats);
+
+/* Train the root model exactly as ls_sort would (sample with the root's
+ * seed, sort the sample, fit; Sec. 2.2 / Alg. 5) and copy it to *out_model.
+ * Also returns the root decision inputs in *out_stats (nullable).
+ * d_sorted_sample (nullable, >= sample size keys) receives the sorted
+ * sample as key bits.  Synchronous. */
+ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p,
+                 ls_model* out_model, ls_stats* out_stats, void* d_sorted_sample, ls_stream_t stream);
+
+/* Bucket ids of d_keys[0..n) under a given model (host struct, copied to
+ * the device): id = clamp(floor(F(x) B^(k+1)) - B g, 0, B-1) with B =
+ * model->L (k = 0, g = 0 is floor(B F(x)) of Sec. 2.2).  d_ids (nullable)
+ * gets n uint32 ids, d_hist (nullable) B uint64 counts (overwritten).  mode
+ * picks the evaluation: LS_CLASSIFY_DIRECT evaluates the FP64 RMI per key;
+ * the others compile the model into its B-1 exact pivots (Alg. 4) first.
+ * Asynchronous. */
+ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype,
+                      uint32_t k, uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist, ls_stream_t stream);
+
+/* Forward and backward pass of the RMI's least-squares objective on a
+ * sorted sample (key bits, S keys): pred_j = f_leaf(s_j)(s_j) (raw linear
+ * leaf), resid_j = pred_j - j/S, and the gradient of MSE = (1/S) sum resid^2
+ * with respect to every leaf's (a_i, b_i) and the root's (a, b).  Outputs
+ * are device arrays (nullable): d_pred[S], d_resid[S], d_grad_a[L],
+ * d_grad_b[L], d_grad_root[2].  Asynchronous. */
+ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_sample, uint64_t S, ls_dtype dtype,
+                      double* d_pred, double* d_resid, double* d_grad_a, double* d_grad_b, double* d_grad_root,
+                      ls_stream_t stream);
+
+/* Synchronise `stream` and return the device status word of the last call
+ * on this context (LS_OK, LS_ENAN, LS_ETIMEOUT or LS_EDEVICE), then clear it. */
+ls_status ls_last_device_status(ls_ctx* ctx, ls_stream_t stream);
+
+/* Serialise / load a model (versioned POD with a checksum).  *bytes is the
+ * buffer size on input and the bytes used on output; pass buf = NULL to
+ * query the size. */
+ls_status ls_model_export(const ls_model* m, void* buf, size_t* bytes);
+ls_status ls_model_import(ls_model* m, const void* buf, size_t bytes);
+
+/* Human-readable name of a status code (static string). */
+const char* ls_status_string(ls_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H */

@@ -21,6 +21,15 @@
 static double dmax(double p, double q) { return (p < q) ? q : p; }
 static double dmin(double p, double q) { return (q < p) ? q : p; }
 
+/* Integer index from a floored double: values that are not > 0 (negatives,
+ * zeros, NaN from a non-finite model) give 0, values >= hi give hi.  Equal
+ * to min(max(t, 0), hi) for every non-NaN t. */
+static uint32_t clamp_index(double t, uint32_t hi) {
+  if (!(t > 0.0)) return 0;
+  if (!(t < (double)hi)) return hi;
+  return (uint32_t)t;
+}
+
 /* ------------------------------------------------------------------ keys */
 
 /* Order-preserving map to uint64: for doubles this is IEEE totalOrder
@@ -234,9 +243,7 @@ static uint32_t root_leaf(const lsref_model* m, double xc) {
   t = t + m->root_b;
   t = t * (double)m->L;
   t = floor(t);
-  t = dmax(t, 0.0);
-  t = dmin(t, (double)(m->L - 1));
-  return (uint32_t)t;
+  return clamp_index(t, m->L - 1);
 }
 
 uint32_t lsref_model_leaf(const lsref_model* m, double x) {
@@ -355,9 +362,7 @@ static uint32_t refine_id_value(const lsref_model* m, double x, uint32_t B, doub
   double t = F * P;
   t = floor(t);
   t = t - Bg;
-  t = dmax(t, 0.0);
-  t = dmin(t, (double)(B - 1));
-  return (uint32_t)t;
+  return clamp_index(t, B - 1);
 }
 
 uint32_t lsref_refine_id(const lsref_model* m, uint64_t bits, int dtype, uint32_t B, uint32_t k, uint64_t g) {
@@ -610,7 +615,6 @@ static lsref_level_stats* lvl(sctx* c, uint32_t level) {
   static lsref_level_stats dummy;
   if (!c->tr) return &dummy;
   uint32_t l = level < LSREF_MAX_LEVELS ? level : LSREF_MAX_LEVELS - 1;
-  if (l + 1 > c->tr->levels_used) c->tr->levels_used = l + 1;
   return &c->tr->level[l];
 }
 
@@ -932,7 +936,15 @@ static int run_sort(uint64_t* keys, const uint64_t* off, uint32_t nseg, int dtyp
     if (it.model && --it.model->refs == 0) free(it.model);
   }
   for (uint64_t i = 0; i < n; ++i) keys[i] = lsref_unord(keys[i], dtype);
-  if (tr) tr->status = rc;
+  if (tr) {
+    /* levels used: the deepest level where anything was recorded */
+    tr->levels_used = 0;
+    for (uint32_t l = 0; l < LSREF_MAX_LEVELS; ++l) {
+      const lsref_level_stats* q = &tr->level[l];
+      if (q->items || q->base_items || q->homogeneous || q->fallback_items) tr->levels_used = l + 1;
+    }
+    tr->status = rc;
+  }
   free(st.v);
   free(c.tmp);
   free(c.ids);

@@ -4,7 +4,7 @@
  * THIS IS TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only tests/, the
  * smoke check in __graft_entry__.py and the cpu_baseline / reference leg of
  * bench.py may load it.  It shares no code, header, table or constant
- * generator with the CUDA library under paper_2307_08637_gb300/.
+ * generator with the CUDA library.
  *
  * What it computes (arxiv 2307.08637, "LearnedSort as a learning-augmented
  * SampleSort"):

@@ -1,0 +1,1120 @@
+// ls_api.cu -- C ABI and host orchestration of learned SampleSort on GB300.
+//
+// ls_sort runs the recursion of Sec. 2.2 / Sec. 4 level by level.  Each
+// level's buckets that still need partitioning ("items") are planned on the
+// host in batches; every per-key step runs in the kernels of ls_fit.cu and
+// ls_partition.cu.  Per batch:
+//   fresh items (their own sample: the root, RETRAIN buckets, buckets of a
+//   splitter partition, no-progress redos): sample -> sort -> duplicate count
+//   -> FP64 RMI fit -> exact learned pivots -> sample imbalance -> Alg. 5
+//   decision -> splitter table when the tree is chosen;
+//   refine items (LearnedSort 2.0's second round: same model, finer buckets):
+//   exact pivots of floor(F(x) B^(k+1)) - B g, or direct FP64 for small items;
+//   then K1 (classify + histogram), K2 (scan + children), K3 (scatter).
+// After each level the finished spans are sorted (base case), copied home, or
+// sorted by the depth-limit fallback.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "ls_kernels.h"
+
+using namespace lsg;
+
+struct ls_ctx {
+  int device = 0;
+  unsigned int* d_status = nullptr;
+  // cached device memory for ls_fit / ls_classify / ls_fit_grad / ls_sort_host
+  void* d_cache = nullptr;
+  size_t d_cache_bytes = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+constexpr uint32_t kBatchItems = 2048;
+constexpr uint32_t kDirBits = 13;
+constexpr size_t kAlign = 256;
+
+inline size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+inline uint32_t pow2ceil(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      fprintf(stderr, "ls: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return LS_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+ls_status validate_params(const ls_params* p) {
+  if (!p) return LS_EINVAL;
+  if (p->fanout < 2 || p->fanout > LS_MAX_FANOUT) return LS_EINVAL;
+  if (p->splitter_fanout < 2 || p->splitter_fanout > LS_MAX_FANOUT / 2) return LS_EINVAL;
+  if (p->auto_splitter_fanout < 2) return LS_EINVAL;
+  if (p->basecase_threshold < 1 || p->basecase_threshold > kMaxBaseCase) return LS_EINVAL;
+  if (p->max_depth >= LS_MAX_LEVELS - 2) return LS_EINVAL;
+  if (p->min_sample < 2) return LS_EINVAL;
+  if (!(p->sample_rate >= 0.0) || !(p->dup_frac >= 0.0) || !(p->imbalance_tau > 0.0)) return LS_EINVAL;
+  if (p->partitioner < 0 || p->partitioner > 2) return LS_EINVAL;
+  if (p->recurse_model < 0 || p->recurse_model > 1) return LS_EINVAL;
+  if (p->classify_mode < 0 || p->classify_mode > 3) return LS_EINVAL;
+  return LS_OK;
+}
+
+uint64_t sample_size(uint64_t n, const ls_params* p) {
+  if (n == 0) return 0;
+  double want = std::ceil(p->sample_rate * (double)n);
+  uint64_t S;
+  if (!(want < (double)n)) S = n;
+  else if (want < 1.0) S = 0;
+  else S = (uint64_t)want;
+  if (S < p->min_sample) S = p->min_sample;
+  if (S > n) S = n;
+  return S;
+}
+
+double pow_exact(uint32_t B, uint32_t e) {
+  double P = 1.0;
+  for (uint32_t i = 0; i < e; ++i) P = P * (double)B;
+  return P;
+}
+
+RunParams make_rp(const ls_params* p, int dt) {
+  RunParams r;
+  r.B = p->fanout;
+  r.bs_max = p->splitter_fanout;
+  r.bs_auto = p->auto_splitter_fanout;
+  r.T = p->basecase_threshold;
+  r.max_depth = p->max_depth;
+  r.min_sample = p->min_sample;
+  r.sample_rate = p->sample_rate;
+  r.dup_frac = p->dup_frac;
+  r.tau = p->imbalance_tau;
+  r.min_learned_n = p->min_learned_n;
+  r.seed = p->seed;
+  r.partitioner = p->partitioner;
+  r.recurse = p->recurse_model;
+  r.classify_mode = p->classify_mode;
+  r.dt = dt;
+  r.tile = kTileKeys;
+  r.dir_bits = kDirBits;
+  return r;
+}
+
+// Workspace layout for n keys, nseg segments.
+struct Layout {
+  uint64_t n = 0;
+  uint32_t L = 0, nbc = 0, cells = 0;
+  uint64_t icap = 0, scap = 0, mcap = 0, base_cap = 0, large_cap = 0, copy_cap = 0, fb_cap = 0;
+  uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0;
+  size_t total = 0;
+  size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
+      o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
+      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_incl, o_chunkctr;
+  size_t stmp_elems = 0;
+  size_t misc_bytes = 0;
+};
+
+Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
+  Layout l;
+  l.n = n;
+  l.L = p->fanout;
+  uint32_t eqmax = 2 * p->splitter_fanout - 1;  // 2m+1 buckets, m <= B_s - 1 splitters
+  l.nbc = pow2ceil(std::max<uint32_t>(std::max<uint32_t>(p->fanout, eqmax), 2));
+  l.cells = 1u << kDirBits;
+  uint64_t T = p->basecase_threshold;
+  l.icap = n / (T + 1) + nseg + 16;
+  uint64_t smax = sample_size(n ? n : 1, p);
+  l.scap = std::max<uint64_t>(smax, 64ull * p->min_sample) + 1024;
+  l.mcap = 1024 + n / 65536;
+  l.base_cap = n / 2 + 1024;
+  l.large_cap = n / (kWarpSortMax + 1) + 1024;
+  l.copy_cap = n / 2 + 64 * 1024;
+  l.fb_cap = n / (T + 1) + 1024;
+  l.rchunk_cap = l.scap / kChunk + kBatchItems + 8;
+  l.lchunk_cap = l.scap / kChunk + (uint64_t)kBatchItems * l.L + 8;
+  l.stmp_elems = scan_tmp_elems((size_t)kBatchItems * l.L + 8) + 64;
+  l.chunk_cap = n / kChunkKeys + kBatchItems + nseg + 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = up(off + bytes);
+    return r;
+  };
+  l.o_buf = take(n * 8);
+  l.o_cur = take(l.icap * sizeof(Item));
+  l.o_next = take(l.icap * sizeof(Item));
+  l.o_plans = take(kBatchItems * sizeof(Plan));
+  l.o_counts = take((size_t)kBatchItems * l.nbc * 8);
+  l.o_cursors = take((size_t)kBatchItems * l.nbc * 8);
+  l.o_pivots = take((size_t)kBatchItems * l.nbc * 8);
+  l.o_dirs = take((size_t)kBatchItems * (l.cells + 1) * 2);
+  l.o_small = take(l.base_cap * sizeof(Span));
+  l.o_large = take(l.large_cap * sizeof(Span));
+  l.o_copy = take(l.copy_cap * sizeof(Span));
+  l.o_fb = take(l.fb_cap * sizeof(Span));
+  l.o_models = take(l.mcap * sizeof(DModel));
+  l.o_leaves = take(l.mcap * l.L * sizeof(Leaf));
+  l.o_leafcnt = take(l.mcap * l.L * 4);
+  l.o_samp0 = take(l.scap * 8);
+  l.o_samp1 = take(l.scap * 8);
+  l.o_rpart = take(8 * l.rchunk_cap * 8);
+  l.o_lstart = take((size_t)kBatchItems * (l.L + 1) * 4);
+  l.o_lcnt = take(((size_t)kBatchItems * l.L + 8) * 8);
+  l.o_lpre = take(((size_t)kBatchItems * l.L + 8) * 8);
+  l.o_lpart = take(4 * l.lchunk_cap * 8);
+  l.o_leafof = take(l.scap * 4);
+  l.o_stmp = take(l.stmp_elems * 8);
+  l.o_stats = take(LS_MAX_LEVELS * sizeof(DevLevelStats));
+  l.o_ctr = take(sizeof(LevelCounters));
+  l.o_agg = take(l.chunk_cap * l.nbc * 4);
+  l.o_incl = take(l.chunk_cap * l.nbc * 8);
+  l.o_chunkctr = take(8);
+  l.misc_bytes = 16 * (kBatchItems + 8) * 8;
+  l.o_misc = take(l.misc_bytes);
+  l.total = off;
+  return l;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+// Host mirror of one batch.
+struct Batch {
+  std::vector<Item> items;
+  std::vector<Plan> plans;
+  uint64_t ntiles = 0;
+};
+
+struct Sorter {
+  ls_ctx* ctx;
+  const ls_params* p;
+  RunParams rp;
+  Layout lay;
+  void* ws;
+  cudaStream_t st;
+  uint64_t* A;
+  uint64_t* Bb;
+  int dt;
+  std::vector<int> model_free;
+  std::vector<uint8_t> model_used;
+  uint64_t launches = 0;
+  int32_t* seg_decision = nullptr;  // host, per segment
+  uint32_t nseg = 0;
+  std::vector<Item> root_recorded;
+
+  int alloc_model() {
+    if (model_free.empty()) return -1;
+    int m = model_free.back();
+    model_free.pop_back();
+    return m;
+  }
+};
+
+// Full range of ord values a key of dtype dt can have (NaN excluded).
+void ord_range(int dt, uint64_t* lo, uint64_t* hi) {
+  if (dt == LS_U64) {
+    *lo = 0;
+    *hi = ~0ull;
+  } else {
+    *lo = kOrdMinF64;
+    *hi = kOrdMaxF64;
+  }
+}
+
+// Plan and run one batch of items (all at the same level).
+ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, bool record_root,
+                    ls_stats* stats) {
+  const bool check_nan = level0;
+  const ls_params* p = s.p;
+  Layout& L = s.lay;
+  cudaStream_t st = s.st;
+  std::vector<Plan> plans(nitems);
+  std::vector<uint32_t> fresh, cand, refine_tab;
+  std::vector<uint64_t> samp_prefix(1, 0), cand_soff(1, 0), rchunk_prefix(1, 0), sort_off(1, 0),
+      sort_cpre(1, 0);
+  uint64_t tiles = 0;
+  uint64_t max_s = 0;
+  std::vector<Item> its(items, items + nitems);
+  for (uint32_t i = 0; i < nitems; ++i) {
+    Item& it = its[i];
+    Plan& pl = plans[i];
+    memset(&pl, 0, sizeof pl);
+    pl.chunk_begin = tiles;
+    tiles += (it.n + kChunkKeys - 1) / kChunkKeys;
+    pl.cnt_off = (uint64_t)i * L.nbc;
+    pl.tab_off = (uint64_t)i * L.nbc;
+    pl.dir_off = (uint64_t)i * (L.cells + 1);
+    pl.minv = ~0ull;
+    pl.maxv = 0;
+    pl.model = -1;
+    bool is_fresh = it.kind != KIND_REFINE;
+    if (it.kind == KIND_REFINE) {
+      double P = pow_exact(p->fanout, it.mk + 1u);
+      if (P > kRefineLimit) {
+        is_fresh = true;
+        it.kind = KIND_FRESH;  // beyond FP64 resolution: draw a new sample
+        it.model = -1;
+      } else {
+        pl.P = P;
+        pl.Bg = (double)((uint64_t)p->fanout * it.mg);
+        pl.model = it.model;
+        pl.decision = LS_DEC_LEARNED;
+        pl.nb = p->fanout;
+        pl.nb_pad = pow2ceil(p->fanout);
+        pl.kmax = p->fanout - 1;
+        bool direct = p->classify_mode == LS_CLASSIFY_DIRECT || it.n < 4ull * p->fanout;
+        pl.cls = direct ? CLS_DIRECT : (p->classify_mode == LS_CLASSIFY_TREE ? CLS_TREE : CLS_DIR);
+        if (!direct) refine_tab.push_back(i);
+      }
+    }
+    if (is_fresh) {
+      pl.fresh = 1;
+      uint64_t S = sample_size(it.n, p);
+      pl.S = (uint32_t)S;
+      pl.sample_off = samp_prefix.back();
+      fresh.push_back(i);
+      samp_prefix.push_back(samp_prefix.back() + S);
+      sort_off.push_back(sort_off.back() + S);
+      sort_cpre.push_back(sort_cpre.back() + (S + kSortChunk - 1) / kSortChunk);
+      max_s = std::max(max_s, S);
+      bool want = it.kind != KIND_FORCE_SPLITTER &&
+                  (p->partitioner == LS_PART_LEARNED ||
+                   (p->partitioner == LS_PART_AUTO && it.n >= p->min_learned_n));
+      if (want) {
+        int m = s.alloc_model();
+        if (m < 0) return LS_ENOMEM;
+        pl.model = m;
+        pl.want = 1;
+        pl.P = (double)p->fanout;
+        pl.Bg = 0.0;
+        pl.nb_pad = pow2ceil(p->fanout);
+        pl.fit_slot = (uint32_t)cand.size();
+        cand.push_back(i);
+        cand_soff.push_back(cand_soff.back() + S);
+        rchunk_prefix.push_back(rchunk_prefix.back() + (S + kChunk - 1) / kChunk);
+      }
+    }
+  }
+  if (samp_prefix.back() > L.scap) return LS_ENOMEM;
+  // upload items + plans + index lists
+  Item* d_items = at<Item>(s.ws, L.o_cur);
+  Plan* d_plans = at<Plan>(s.ws, L.o_plans);
+  CK(cudaMemcpyAsync(d_items, its.data(), nitems * sizeof(Item), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_plans, plans.data(), nitems * sizeof(Plan), cudaMemcpyHostToDevice, st));
+  uint64_t* misc = at<uint64_t>(s.ws, L.o_misc);
+  const size_t M = kBatchItems + 8;
+  uint32_t* d_fresh = reinterpret_cast<uint32_t*>(misc + 0 * M);
+  uint64_t* d_sprefix = misc + 1 * M;
+  uint32_t* d_cand = reinterpret_cast<uint32_t*>(misc + 2 * M);
+  uint64_t* d_csoff = misc + 3 * M;
+  uint64_t* d_rcp = misc + 4 * M;
+  uint64_t* d_soff = misc + 5 * M;
+  uint64_t* d_scpre = misc + 6 * M;
+  uint32_t* d_reftab = reinterpret_cast<uint32_t*>(misc + 7 * M);
+  if (!fresh.empty()) {
+    CK(cudaMemcpyAsync(d_fresh, fresh.data(), fresh.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sprefix, samp_prefix.data(), samp_prefix.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_soff, sort_off.data(), sort_off.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_scpre, sort_cpre.data(), sort_cpre.size() * 8, cudaMemcpyHostToDevice, st));
+  }
+  if (!cand.empty()) {
+    CK(cudaMemcpyAsync(d_cand, cand.data(), cand.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_csoff, cand_soff.data(), cand_soff.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_rcp, rchunk_prefix.data(), rchunk_prefix.size() * 8, cudaMemcpyHostToDevice, st));
+  }
+  if (!refine_tab.empty())
+    CK(cudaMemcpyAsync(d_reftab, refine_tab.data(), refine_tab.size() * 4, cudaMemcpyHostToDevice, st));
+
+  uint64_t* pivots = at<uint64_t>(s.ws, L.o_pivots);
+  uint16_t* dirs = at<uint16_t>(s.ws, L.o_dirs);
+  DModel* models = at<DModel>(s.ws, L.o_models);
+  Leaf* leaves = at<Leaf>(s.ws, L.o_leaves);
+  unsigned long long* counts = at<unsigned long long>(s.ws, L.o_counts);
+  unsigned long long* cursors = at<unsigned long long>(s.ws, L.o_cursors);
+  CK(cudaMemsetAsync(counts, 0, (size_t)nitems * L.nbc * 8, st));
+
+  // ---- fresh items: sample, sort, dups, fit, pivots, decision
+  const uint64_t* sorted = nullptr;
+  if (!fresh.empty()) {
+    FreshArgs f;
+    f.items = d_items;
+    f.plans = d_plans;
+    f.fresh = d_fresh;
+    f.samp_prefix = d_sprefix;
+    f.nfresh = (uint32_t)fresh.size();
+    f.total_samples = samp_prefix.back();
+    f.keysA = s.A;
+    f.keysB = s.Bb;
+    uint64_t* samp0 = at<uint64_t>(s.ws, L.o_samp0);
+    uint64_t* samp1 = at<uint64_t>(s.ws, L.o_samp1);
+    launch_sample_gather(f, s.rp, samp0, st);
+    sorted = segmented_sort_u64(samp0, samp1, d_soff, d_scpre, (uint32_t)fresh.size(), sort_cpre.back(), max_s,
+                                st, &s.launches);
+    launch_dups(f, sorted, st);
+    s.launches += 2;
+    if (!cand.empty()) {
+      FitArgs fa;
+      fa.plans = d_plans;
+      fa.items = d_items;
+      fa.cand = d_cand;
+      fa.cand_soff = d_csoff;
+      fa.rchunk_prefix = d_rcp;
+      fa.ncand = (uint32_t)cand.size();
+      fa.total_rchunks = rchunk_prefix.back();
+      fa.total_cand_samples = cand_soff.back();
+      fa.lchunk_bound = cand_soff.back() / kChunk + (uint64_t)cand.size() * L.L + 8;
+      fa.samp = sorted;
+      fa.models = models;
+      fa.leaves = leaves;
+      fa.L = L.L;
+      fa.rpart = at<double>(s.ws, L.o_rpart);
+      fa.leaf_start = at<uint32_t>(s.ws, L.o_lstart);
+      fa.lchunk_cnt = at<uint64_t>(s.ws, L.o_lcnt);
+      fa.lchunk_prefix = at<uint64_t>(s.ws, L.o_lpre);
+      fa.scan_tmp = at<uint64_t>(s.ws, L.o_stmp);
+      fa.scan_tmp_elems = L.stmp_elems;
+      fa.lpart = at<double>(s.ws, L.o_lpart);
+      fa.leaf_of = at<uint32_t>(s.ws, L.o_leafof);
+      fa.leaf_cnt = at<uint32_t>(s.ws, L.o_leafcnt);
+      if (fa.total_rchunks > L.rchunk_cap || fa.lchunk_bound > L.lchunk_cap) return LS_ENOMEM;
+      launch_fit(fa, s.rp, st, &s.launches);
+      launch_learned_pivots(d_plans, d_items, d_cand, fa.ncand, pow2ceil(p->fanout), models, leaves, pivots, s.rp,
+                            st);
+      launch_imbalance(fa, pivots, counts, s.rp, st, &s.launches);
+      s.launches += 1;
+    }
+    launch_decide(f, models, s.rp, st);
+    launch_splitter_build(f, sorted, pivots, s.rp, st);
+    s.launches += 2;
+  }
+  if (!refine_tab.empty()) {
+    launch_learned_pivots(d_plans, d_items, d_reftab, (uint32_t)refine_tab.size(), pow2ceil(p->fanout), models,
+                          leaves, pivots, s.rp, st);
+    s.launches += 1;
+  }
+  launch_dir_build(d_plans, nitems, L.cells, pivots, dirs, st);
+  s.launches += 1;
+
+  // ---- partition passes
+  PassArgs pa;
+  pa.items = d_items;
+  pa.plans = d_plans;
+  pa.nitems = nitems;
+  pa.nchunks = tiles;
+  if (tiles > L.chunk_cap) return LS_ENOMEM;
+  pa.agg = at<uint32_t>(s.ws, L.o_agg);
+  pa.incl = at<unsigned long long>(s.ws, L.o_incl);
+  pa.chunk_ctr = at<unsigned long long>(s.ws, L.o_chunkctr);
+  pa.keysA = s.A;
+  pa.keysB = s.Bb;
+  pa.outA = s.A;
+  pa.outB = s.Bb;
+  pa.pivots = pivots;
+  pa.dirs = dirs;
+  pa.models = models;
+  pa.leaves = leaves;
+  pa.counts = counts;
+  pa.cursors = cursors;
+  pa.status = s.ctx->d_status;
+  pa.check_nan = check_nan && s.dt == LS_F64;
+  pa.nb_pad_max = L.nbc;
+  pa.dir_cells_max = L.cells;
+  launch_classify_hist(pa, s.rp, st);
+
+  ChildArgs ca;
+  ca.items = d_items;
+  ca.plans = d_plans;
+  ca.nitems = nitems;
+  ca.pivots = pivots;
+  ca.counts = counts;
+  ca.cursors = cursors;
+  ca.next = at<Item>(s.ws, L.o_next);
+  ca.next_cap = L.icap;
+  ca.base_small = at<Span>(s.ws, L.o_small);
+  ca.base_large = at<Span>(s.ws, L.o_large);
+  ca.base_cap = L.base_cap;
+  ca.large_cap = L.large_cap;
+  ca.copy = at<Span>(s.ws, L.o_copy);
+  ca.copy_cap = L.copy_cap;
+  ca.fallback = at<Span>(s.ws, L.o_fb);
+  ca.fallback_cap = L.fb_cap;
+  ca.ctr = at<LevelCounters>(s.ws, L.o_ctr);
+  ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
+  launch_children(ca, s.rp, st);
+  launch_scatter(pa, s.rp, st);
+  s.launches += 3;
+  CK(cudaGetLastError());
+
+  if (record_root && stats) {
+    Plan rp0;
+    CK(cudaMemcpyAsync(&rp0, d_plans, sizeof(Plan), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (rp0.minv == rp0.maxv) {
+      // homogeneity is checked before any model is built (Sec. 2.2): the
+      // sample the device drew speculatively is not part of the decision
+      stats->root_decision = LS_DEC_HOMOGENEOUS;
+    } else {
+      stats->root_decision = rp0.decision;
+      stats->root_nbuckets = rp0.nb;
+      stats->root_sample_size = rp0.S;
+      stats->root_dups = rp0.dups;
+      stats->root_imbalance_max = rp0.imb;
+    }
+  }
+  if (s.seg_decision && level0) {
+    // per-segment root decisions (level-0 batches)
+    std::vector<Plan> hp(nitems);
+    CK(cudaMemcpyAsync(hp.data(), d_plans, nitems * sizeof(Plan), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (uint32_t i = 0; i < nitems; ++i) {
+      if (its[i].level != 0 || its[i].segment >= s.nseg) continue;
+      s.seg_decision[its[i].segment] = (hp[i].minv == hp[i].maxv) ? LS_DEC_HOMOGENEOUS : hp[i].decision;
+    }
+  }
+  return LS_OK;
+}
+
+// Sort / copy the finished spans of one level.
+ls_status finish_spans(Sorter& s, const LevelCounters& c) {
+  Layout& L = s.lay;
+  if (c.n_base_small) launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.dt, s.st);
+  if (c.n_base_large)
+    launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.dt, s.st);
+  if (c.n_copy) launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.st);
+  if (c.n_fallback) launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.dt, s.st);
+  s.launches += (c.n_base_small > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
+  CK(cudaGetLastError());
+  return LS_OK;
+}
+
+ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32_t nseg, ls_dtype dtype,
+                    const ls_params* p, void* ws, size_t ws_bytes, ls_stats* out_stats, int32_t* seg_dec,
+                    cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!ctx || (!d_keys && h_off[nseg] > 0) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  ls_status vs = validate_params(p);
+  if (vs != LS_OK) return vs;
+  for (uint32_t s = 0; s < nseg; ++s)
+    if (h_off[s + 1] < h_off[s]) return LS_EINVAL;
+  uint64_t n = h_off[nseg];
+  for (uint32_t s = 0; s < nseg; ++s)
+    if (h_off[s + 1] - h_off[s] >= (1ull << 32)) return LS_EINVAL;
+  Layout lay = compute_layout(n, nseg, p);
+  if (n > 0 && (!ws || ws_bytes < lay.total)) return LS_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  ls_stats local;
+  ls_stats* stats = out_stats ? out_stats : &local;
+  memset(stats, 0, sizeof *stats);
+  stats->root_decision = LS_DEC_NONE;
+  if (seg_dec)
+    for (uint32_t s = 0; s < nseg; ++s) seg_dec[s] = LS_DEC_NONE;
+  if (n == 0) return LS_OK;
+
+  Sorter s;
+  s.ctx = ctx;
+  s.p = p;
+  s.dt = dtype;
+  s.rp = make_rp(p, dtype);
+  s.lay = lay;
+  s.ws = ws;
+  s.st = st;
+  s.A = d_keys;
+  s.Bb = at<uint64_t>(ws, lay.o_buf);
+  s.seg_decision = seg_dec;
+  s.nseg = nseg;
+  for (int m = (int)lay.mcap - 1; m >= 0; --m) s.model_free.push_back(m);
+
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), st));
+  DevLevelStats* d_stats = at<DevLevelStats>(ws, lay.o_stats);
+  LevelCounters* d_ctr = at<LevelCounters>(ws, lay.o_ctr);
+  CK(cudaMemsetAsync(d_stats, 0, LS_MAX_LEVELS * sizeof(DevLevelStats), st));
+
+  // level 0: one root item per segment; small roots straight to the base case
+  uint64_t olo, ohi;
+  ord_range(dtype, &olo, &ohi);
+  std::vector<Item> items;
+  std::vector<Span> small, large;
+  ls_level_stats root_base;
+  memset(&root_base, 0, sizeof root_base);
+  for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
+    uint64_t len = h_off[sgi + 1] - h_off[sgi];
+    if (len <= 1) continue;
+    if (len <= p->basecase_threshold) {
+      Span sp{h_off[sgi], (uint32_t)len, 0u};
+      (len <= kWarpSortMax ? small : large).push_back(sp);
+      root_base.base_items += 1;
+      root_base.base_keys += len;
+      continue;
+    }
+    Item it;
+    memset(&it, 0, sizeof it);
+    it.lo = h_off[sgi];
+    it.n = len;
+    it.segment = sgi;
+    it.level = 0;
+    it.kind = KIND_FRESH;
+    it.model = -1;
+    it.buf = 0;
+    it.ord_lo = olo;
+    it.ord_hi = ohi;
+    items.push_back(it);
+  }
+  if (!small.empty() || !large.empty()) {
+    CK(cudaMemcpyAsync(at<Span>(ws, lay.o_small), small.data(), small.size() * sizeof(Span), cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaMemcpyAsync(at<Span>(ws, lay.o_large), large.data(), large.size() * sizeof(Span), cudaMemcpyHostToDevice,
+                       st));
+    LevelCounters c;
+    memset(&c, 0, sizeof c);
+    c.n_base_small = small.size();
+    c.n_base_large = large.size();
+    ls_status r = finish_spans(s, c);
+    if (r != LS_OK) return r;
+    CK(cudaStreamSynchronize(st));
+  }
+
+  bool first = true;
+  uint32_t level = 0;
+  ls_status result = LS_OK;
+  while (!items.empty()) {
+    CK(cudaMemsetAsync(d_ctr, 0, sizeof(LevelCounters), st));
+    // items of this level are replaced by the device list of the next level,
+    // so keep a host copy and upload per batch into the "current" slot
+    std::vector<Item> cur;
+    cur.swap(items);
+    for (size_t b0 = 0; b0 < cur.size();) {
+      // batch by item count and by sample capacity
+      size_t b1 = b0;
+      uint64_t sacc = 0;
+      while (b1 < cur.size() && b1 - b0 < kBatchItems) {
+        const Item& it = cur[b1];
+        bool fr = it.kind != KIND_REFINE || pow_exact(p->fanout, it.mk + 1u) > kRefineLimit;
+        uint64_t S = fr ? sample_size(it.n, p) : 0;
+        if (b1 > b0 && sacc + S > lay.scap) break;
+        sacc += S;
+        ++b1;
+      }
+      bool record = first && b0 == 0 && out_stats && cur[0].segment == 0;
+      ls_status r = run_batch(s, cur.data() + b0, (uint32_t)(b1 - b0), level == 0, record, stats);
+      if (r != LS_OK) return r;
+      first = false;
+      b0 = b1;
+    }
+    LevelCounters c;
+    CK(cudaMemcpyAsync(&c, d_ctr, sizeof c, cudaMemcpyDeviceToHost, st));
+    unsigned int dstat = 0;
+    CK(cudaMemcpyAsync(&dstat, ctx->d_status, sizeof dstat, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c.overflow) {
+      fprintf(stderr, "ls: workspace list capacity exceeded at level %u\n", level);
+      return LS_ENOMEM;
+    }
+    if (dstat != 0) {
+      result = (ls_status)dstat;
+      break;
+    }
+    ls_status r = finish_spans(s, c);
+    if (r != LS_OK) return r;
+    if (c.n_next) {
+      items.resize(c.n_next);
+      CK(cudaMemcpyAsync(items.data(), at<Item>(ws, lay.o_next), c.n_next * sizeof(Item), cudaMemcpyDeviceToHost,
+                         st));
+      CK(cudaStreamSynchronize(st));
+      // keep only models still referenced by refine items
+      std::vector<uint8_t> live(lay.mcap, 0);
+      for (const Item& it : items)
+        if (it.kind == KIND_REFINE && it.model >= 0) live[it.model] = 1;
+      s.model_free.clear();
+      for (int m = (int)lay.mcap - 1; m >= 0; --m)
+        if (!live[m]) s.model_free.push_back(m);
+    }
+    ++level;
+  }
+  // statistics
+  std::vector<DevLevelStats> hs(LS_MAX_LEVELS);
+  CK(cudaMemcpyAsync(hs.data(), d_stats, LS_MAX_LEVELS * sizeof(DevLevelStats), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  memcpy(stats->level, hs.data(), sizeof(stats->level));
+  stats->level[0].base_items += root_base.base_items;
+  stats->level[0].base_keys += root_base.base_keys;
+  uint32_t used = 0;
+  for (uint32_t l = 0; l < LS_MAX_LEVELS; ++l) {
+    const ls_level_stats& q = stats->level[l];
+    if (q.items || q.base_items || q.homogeneous || q.fallback_items) used = l + 1;
+  }
+  stats->levels_used = used;
+  stats->status = result;
+  stats->kernel_launches = s.launches;
+  ctx->launches += s.launches;
+  stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return result;
+}
+
+ls_status ensure_cache(ls_ctx* ctx, size_t bytes) {
+  if (ctx->d_cache_bytes >= bytes) return LS_OK;
+  if (ctx->d_cache) cudaFree(ctx->d_cache);
+  ctx->d_cache = nullptr;
+  ctx->d_cache_bytes = 0;
+  if (cudaMalloc(&ctx->d_cache, bytes) != cudaSuccess) return LS_ENOMEM;
+  ctx->d_cache_bytes = bytes;
+  return LS_OK;
+}
+
+// Host model <-> device model (one slot).
+void model_to_device_layout(const ls_model* m, DModel* dm, std::vector<Leaf>& lv) {
+  memset(dm, 0, sizeof *dm);
+  dm->xmin = m->xmin;
+  dm->xmax = m->xmax;
+  dm->rx0 = m->root_x0;
+  dm->ra = m->root_a;
+  dm->rb = m->root_b;
+  dm->L = m->L;
+  dm->S = m->S;
+  dm->leaf_off = 0;
+  dm->ok = 1;
+  lv.resize(m->L);
+  for (uint32_t i = 0; i < m->L; ++i) lv[i] = Leaf{m->leaf_x0[i], m->leaf_a[i], m->leaf_b[i], m->leaf_lo[i], m->leaf_hi[i]};
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+
+extern "C" {
+
+void ls_params_default(ls_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->fanout = 1000;
+  p->splitter_fanout = 1024;
+  p->basecase_threshold = 16;
+  p->max_depth = 16;
+  p->min_sample = 256;
+  p->auto_splitter_fanout = 256;
+  p->sample_rate = 0.01;
+  p->dup_frac = 0.10;
+  p->imbalance_tau = 8.0;
+  p->min_learned_n = 100000;
+  p->seed = 0x5EEDull;
+  p->partitioner = LS_PART_AUTO;
+  p->recurse_model = LS_RECURSE_REFINE_GLOBAL;
+  p->classify_mode = LS_CLASSIFY_AUTO;
+  p->tile_keys = 0;
+}
+
+ls_status ls_create(ls_ctx** out, int device) {
+  if (!out) return LS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LS_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return LS_ECUDA;
+  ls_ctx* c = new (std::nothrow) ls_ctx();
+  if (!c) return LS_ENOMEM;
+  c->device = device;
+  if (cudaMalloc(&c->d_status, sizeof(unsigned int)) != cudaSuccess) {
+    delete c;
+    return LS_ECUDA;
+  }
+  cudaMemset(c->d_status, 0, sizeof(unsigned int));
+  *out = c;
+  return LS_OK;
+}
+
+void ls_destroy(ls_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_cache) cudaFree(ctx->d_cache);
+  delete ctx;
+}
+
+ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dtype, const ls_params* p,
+                            size_t* bytes) {
+  (void)ctx;
+  if (!bytes || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  ls_status vs = validate_params(p);
+  if (vs != LS_OK) return vs;
+  *bytes = compute_layout(n, nseg ? nseg : 1, p).total;
+  return LS_OK;
+}
+
+ls_status ls_sort(ls_ctx* ctx, void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p, void* d_workspace,
+                  size_t ws_bytes, ls_stats* out_stats, ls_stream_t stream) {
+  uint64_t off[2] = {0, n};
+  return sort_impl(ctx, static_cast<uint64_t*>(d_keys), off, 1, dtype, p, d_workspace, ws_bytes, out_stats,
+                   nullptr, static_cast<cudaStream_t>(stream));
+}
+
+ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets, uint32_t nseg, ls_dtype dtype,
+                            const ls_params* p, void* d_workspace, size_t ws_bytes, ls_stats* out_stats,
+                            int32_t* h_seg_decision, ls_stream_t stream) {
+  if (!h_offsets || nseg == 0) return LS_EINVAL;
+  return sort_impl(ctx, static_cast<uint64_t*>(d_keys), h_offsets, nseg, dtype, p, d_workspace, ws_bytes,
+                   out_stats, h_seg_decision, static_cast<cudaStream_t>(stream));
+}
+
+ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, const ls_params* p,
+                       ls_stats* out_stats) {
+  if (!ctx || (!h_keys && n)) return LS_EINVAL;
+  ls_status vs = validate_params(p);
+  if (vs != LS_OK) return vs;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  size_t wsb = compute_layout(n, 1, p).total;
+  size_t keyb = up(n * 8);
+  ls_status r = ensure_cache(ctx, keyb + wsb + kAlign);
+  if (r != LS_OK) return r;
+  char* base = static_cast<char*>(ctx->d_cache);
+  void* d_keys = base;
+  void* d_ws = base + keyb;
+  if (cudaMemcpy(d_keys, h_keys, n * 8, cudaMemcpyHostToDevice) != cudaSuccess) return LS_ECUDA;
+  r = ls_sort(ctx, d_keys, n, dtype, p, d_ws, wsb, out_stats, nullptr);
+  if (r != LS_OK) return r;
+  if (cudaMemcpy(h_keys, d_keys, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LS_ECUDA;
+  return LS_OK;
+}
+
+ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p,
+                 ls_model* out_model, ls_stats* out_stats, void* d_sorted_sample, ls_stream_t stream) {
+  if (!ctx || !d_keys || n < 2 || !out_model || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  ls_status vs = validate_params(p);
+  if (vs != LS_OK) return vs;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  // a one-item "sort" workspace is enough for the fresh-item pipeline; the
+  // partition passes are not run
+  ls_params q = *p;
+  if (q.partitioner == LS_PART_SPLITTER) q.partitioner = LS_PART_LEARNED;  // fit regardless
+  Layout lay = compute_layout(n, 1, &q);
+  ls_status r = ensure_cache(ctx, lay.total + kAlign);
+  if (r != LS_OK) return r;
+  void* ws = ctx->d_cache;
+  Sorter s;
+  s.ctx = ctx;
+  s.p = &q;
+  s.dt = dtype;
+  s.rp = make_rp(&q, dtype);
+  s.lay = lay;
+  s.ws = ws;
+  s.st = st;
+  s.A = static_cast<uint64_t*>(const_cast<void*>(d_keys));
+  s.Bb = at<uint64_t>(ws, lay.o_buf);
+  s.model_free.push_back(0);
+  // Run only the fresh pipeline of the root: reuse run_batch's planning by
+  // hand (no partition passes).
+  Item it;
+  memset(&it, 0, sizeof it);
+  it.n = n;
+  it.kind = KIND_FRESH;
+  it.model = -1;
+  ord_range(dtype, &it.ord_lo, &it.ord_hi);
+  uint64_t S = sample_size(n, &q);
+  Plan pl;
+  memset(&pl, 0, sizeof pl);
+  pl.S = (uint32_t)S;
+  pl.fresh = 1;
+  pl.want = 1;
+  pl.model = 0;
+  pl.P = (double)q.fanout;
+  pl.nb_pad = pow2ceil(q.fanout);
+  pl.minv = ~0ull;
+  Item* d_items = at<Item>(ws, lay.o_cur);
+  Plan* d_plans = at<Plan>(ws, lay.o_plans);
+  uint64_t* misc = at<uint64_t>(ws, lay.o_misc);
+  const size_t M = kBatchItems + 8;
+  uint32_t zero = 0;
+  uint64_t pre[2] = {0, S};
+  uint64_t rcp[2] = {0, (S + kChunk - 1) / kChunk};
+  uint64_t scp[2] = {0, (S + kSortChunk - 1) / kSortChunk};
+  CK(cudaMemcpyAsync(d_items, &it, sizeof it, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_plans, &pl, sizeof pl, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc, &zero, 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + M, pre, 16, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + 2 * M, &zero, 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + 3 * M, pre, 16, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + 4 * M, rcp, 16, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + 5 * M, pre, 16, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(misc + 6 * M, scp, 16, cudaMemcpyHostToDevice, st));
+  FreshArgs f;
+  f.items = d_items;
+  f.plans = d_plans;
+  f.fresh = reinterpret_cast<uint32_t*>(misc);
+  f.samp_prefix = misc + M;
+  f.nfresh = 1;
+  f.total_samples = S;
+  f.keysA = s.A;
+  f.keysB = s.Bb;
+  uint64_t* samp0 = at<uint64_t>(ws, lay.o_samp0);
+  uint64_t* samp1 = at<uint64_t>(ws, lay.o_samp1);
+  launch_sample_gather(f, s.rp, samp0, st);
+  const uint64_t* sorted = segmented_sort_u64(samp0, samp1, misc + 5 * M, misc + 6 * M, 1, scp[1], S, st,
+                                              &s.launches);
+  launch_dups(f, sorted, st);
+  FitArgs fa;
+  fa.plans = d_plans;
+  fa.items = d_items;
+  fa.cand = reinterpret_cast<uint32_t*>(misc + 2 * M);
+  fa.cand_soff = misc + 3 * M;
+  fa.rchunk_prefix = misc + 4 * M;
+  fa.ncand = 1;
+  fa.total_rchunks = rcp[1];
+  fa.total_cand_samples = S;
+  fa.lchunk_bound = S / kChunk + lay.L + 8;
+  fa.samp = sorted;
+  fa.models = at<DModel>(ws, lay.o_models);
+  fa.leaves = at<Leaf>(ws, lay.o_leaves);
+  fa.L = lay.L;
+  fa.rpart = at<double>(ws, lay.o_rpart);
+  fa.leaf_start = at<uint32_t>(ws, lay.o_lstart);
+  fa.lchunk_cnt = at<uint64_t>(ws, lay.o_lcnt);
+  fa.lchunk_prefix = at<uint64_t>(ws, lay.o_lpre);
+  fa.scan_tmp = at<uint64_t>(ws, lay.o_stmp);
+  fa.scan_tmp_elems = lay.stmp_elems;
+  fa.lpart = at<double>(ws, lay.o_lpart);
+  fa.leaf_of = at<uint32_t>(ws, lay.o_leafof);
+  fa.leaf_cnt = at<uint32_t>(ws, lay.o_leafcnt);
+  launch_fit(fa, s.rp, st, &s.launches);
+  uint64_t* pivots = at<uint64_t>(ws, lay.o_pivots);
+  unsigned long long* counts = at<unsigned long long>(ws, lay.o_counts);
+  CK(cudaMemsetAsync(counts, 0, (size_t)lay.nbc * 8, st));
+  launch_learned_pivots(d_plans, d_items, fa.cand, 1, pow2ceil(q.fanout), fa.models, fa.leaves, pivots, s.rp, st);
+  launch_imbalance(fa, pivots, counts, s.rp, st, &s.launches);
+  ls_params q2 = *p;  // decision with the caller's partitioner
+  RunParams rp2 = make_rp(&q2, dtype);
+  launch_decide(f, fa.models, rp2, st);
+  CK(cudaGetLastError());
+  // copy out
+  DModel dm;
+  std::vector<Leaf> lv(lay.L);
+  std::vector<uint32_t> lc(lay.L);
+  Plan hp;
+  CK(cudaMemcpyAsync(&dm, fa.models, sizeof dm, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(lv.data(), fa.leaves, lay.L * sizeof(Leaf), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(lc.data(), fa.leaf_cnt, lay.L * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hp, d_plans, sizeof hp, cudaMemcpyDeviceToHost, st));
+  if (d_sorted_sample) {
+    // ord -> key bits on the host side of the copy is not possible on device
+    // memory directly; copy through a host vector
+    std::vector<uint64_t> hs(S);
+    CK(cudaMemcpyAsync(hs.data(), sorted, S * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (auto& v : hs) v = unord(v, dtype);
+    CK(cudaMemcpyAsync(d_sorted_sample, hs.data(), S * 8, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  memset(out_model, 0, sizeof *out_model);
+  out_model->L = dm.L;
+  out_model->S = dm.S;
+  out_model->xmin = dm.xmin;
+  out_model->xmax = dm.xmax;
+  out_model->root_x0 = dm.rx0;
+  out_model->root_a = dm.ra;
+  out_model->root_b = dm.rb;
+  for (uint32_t i = 0; i < lay.L; ++i) {
+    out_model->leaf_x0[i] = lv[i].x0;
+    out_model->leaf_a[i] = lv[i].a;
+    out_model->leaf_b[i] = lv[i].b;
+    out_model->leaf_lo[i] = lv[i].lo;
+    out_model->leaf_hi[i] = lv[i].hi;
+    out_model->leaf_count[i] = lc[i];
+  }
+  if (out_stats) {
+    memset(out_stats, 0, sizeof *out_stats);
+    out_stats->root_sample_size = S;
+    out_stats->root_dups = hp.dups;
+    out_stats->root_imbalance_max = hp.imb;
+    out_stats->root_decision = hp.decision == LS_DEC_LEARNED ? LS_DEC_LEARNED : LS_DEC_SPLITTER;
+    out_stats->status = dm.ok ? LS_OK : LS_EDEVICE;
+  }
+  return LS_OK;
+}
+
+ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype, uint32_t k,
+                      uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist, ls_stream_t stream) {
+  if (!ctx || !model || (!d_keys && n) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < 0 || mode > 3) return LS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  uint32_t B = model->L;
+  double P = pow_exact(B, k + 1);
+  if (P > kRefineLimit) return LS_EINVAL;
+  double Bg = (double)((uint64_t)B * g);
+  uint32_t nbp = pow2ceil(B);
+  uint32_t cells = 1u << kDirBits;
+  size_t need = up(sizeof(DModel)) + up(B * sizeof(Leaf)) + up(sizeof(Item)) + up(sizeof(Plan)) + up(nbp * 8) +
+                up((cells + 1) * 2) + up(8);
+  ls_status r = ensure_cache(ctx, need + kAlign);
+  if (r != LS_OK) return r;
+  char* b = static_cast<char*>(ctx->d_cache);
+  DModel* d_m = reinterpret_cast<DModel*>(b);
+  b += up(sizeof(DModel));
+  Leaf* d_l = reinterpret_cast<Leaf*>(b);
+  b += up(B * sizeof(Leaf));
+  Item* d_it = reinterpret_cast<Item*>(b);
+  b += up(sizeof(Item));
+  Plan* d_pl = reinterpret_cast<Plan*>(b);
+  b += up(sizeof(Plan));
+  uint64_t* d_piv = reinterpret_cast<uint64_t*>(b);
+  b += up(nbp * 8);
+  uint16_t* d_dir = reinterpret_cast<uint16_t*>(b);
+  b += up((cells + 1) * 2);
+  uint32_t* d_list = reinterpret_cast<uint32_t*>(b);
+  DModel dm;
+  std::vector<Leaf> lv;
+  model_to_device_layout(model, &dm, lv);
+  CK(cudaMemcpyAsync(d_m, &dm, sizeof dm, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_l, lv.data(), B * sizeof(Leaf), cudaMemcpyHostToDevice, st));
+  if (d_hist) CK(cudaMemsetAsync(d_hist, 0, B * 8, st));
+  if (mode == LS_CLASSIFY_DIRECT) {
+    launch_direct_classify(d_m, d_l, static_cast<const uint64_t*>(d_keys), n, dtype, P, Bg, B, d_ids,
+                           reinterpret_cast<unsigned long long*>(d_hist), st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return LS_OK;
+  }
+  Item it;
+  memset(&it, 0, sizeof it);
+  ord_range(dtype, &it.ord_lo, &it.ord_hi);
+  it.n = n;
+  it.kind = KIND_REFINE;
+  Plan pl;
+  memset(&pl, 0, sizeof pl);
+  pl.model = 0;
+  pl.P = P;
+  pl.Bg = Bg;
+  pl.nb = B;
+  pl.nb_pad = nbp;
+  pl.decision = LS_DEC_LEARNED;
+  pl.cls = (mode == LS_CLASSIFY_TREE) ? CLS_TREE : CLS_DIR;
+  uint32_t zero = 0;
+  CK(cudaMemcpyAsync(d_it, &it, sizeof it, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_pl, &pl, sizeof pl, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_list, &zero, 4, cudaMemcpyHostToDevice, st));
+  RunParams rp;
+  memset(&rp, 0, sizeof rp);
+  rp.B = B;
+  rp.dt = dtype;
+  launch_learned_pivots(d_pl, d_it, d_list, 1, nbp, d_m, d_l, d_piv, rp, st);
+  launch_dir_build(d_pl, 1, cells, d_piv, d_dir, st);
+  launch_table_classify(d_pl, d_piv, d_dir, static_cast<const uint64_t*>(d_keys), n, dtype, d_ids,
+                        reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return LS_OK;
+}
+
+ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_sample, uint64_t S, ls_dtype dtype,
+                      double* d_pred, double* d_resid, double* d_grad_a, double* d_grad_b, double* d_grad_root,
+                      ls_stream_t stream) {
+  if (!ctx || !model || !d_sorted_sample || S == 0 || S >= (1ull << 32)) return LS_EINVAL;
+  if (model->L < 1 || model->L > LS_MAX_FANOUT || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  uint32_t L = model->L;
+  size_t sb = fit_grad_scratch_bytes(S, L);
+  size_t need = up(sizeof(DModel)) + up(L * sizeof(Leaf)) + up(sb);
+  ls_status r = ensure_cache(ctx, need + kAlign);
+  if (r != LS_OK) return r;
+  char* b = static_cast<char*>(ctx->d_cache);
+  DModel* d_m = reinterpret_cast<DModel*>(b);
+  b += up(sizeof(DModel));
+  Leaf* d_l = reinterpret_cast<Leaf*>(b);
+  b += up(L * sizeof(Leaf));
+  DModel dm;
+  std::vector<Leaf> lv;
+  model_to_device_layout(model, &dm, lv);
+  CK(cudaMemcpyAsync(d_m, &dm, sizeof dm, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_l, lv.data(), L * sizeof(Leaf), cudaMemcpyHostToDevice, st));
+  launch_fit_grad(d_m, d_l, static_cast<const uint64_t*>(d_sorted_sample), S, dtype, d_pred, d_resid, d_grad_a,
+                  d_grad_b, d_grad_root, b, sb, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return LS_OK;
+}
+
+ls_status ls_last_device_status(ls_ctx* ctx, ls_stream_t stream) {
+  if (!ctx) return LS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned int v = 0;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LS_ECUDA;
+  if (cudaMemcpy(&v, ctx->d_status, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return LS_ECUDA;
+  cudaMemset(ctx->d_status, 0, sizeof v);
+  return (ls_status)v;
+}
+
+static uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+ls_status ls_model_export(const ls_model* m, void* buf, size_t* bytes) {
+  if (!m || !bytes) return LS_EINVAL;
+  const size_t need = 16 + sizeof(ls_model) + 8;
+  if (!buf) {
+    *bytes = need;
+    return LS_OK;
+  }
+  if (*bytes < need) return LS_ENOMEM;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  const uint64_t magic = 0x4C534D4F44454C31ull;  // "LSMODEL1"
+  const uint64_t size = sizeof(ls_model);
+  memcpy(o, &magic, 8);
+  memcpy(o + 8, &size, 8);
+  memcpy(o + 16, m, sizeof(ls_model));
+  uint64_t h = fnv1a(m, sizeof(ls_model));
+  memcpy(o + 16 + sizeof(ls_model), &h, 8);
+  *bytes = need;
+  return LS_OK;
+}
+
+ls_status ls_model_import(ls_model* m, const void* buf, size_t bytes) {
+  if (!m || !buf) return LS_EINVAL;
+  const size_t need = 16 + sizeof(ls_model) + 8;
+  if (bytes < need) return LS_EINVAL;
+  const unsigned char* o = static_cast<const unsigned char*>(buf);
+  uint64_t magic, size, h;
+  memcpy(&magic, o, 8);
+  memcpy(&size, o + 8, 8);
+  if (magic != 0x4C534D4F44454C31ull || size != sizeof(ls_model)) return LS_EINVAL;
+  memcpy(&h, o + 16 + sizeof(ls_model), 8);
+  if (h != fnv1a(o + 16, sizeof(ls_model))) return LS_EINVAL;
+  memcpy(m, o + 16, sizeof(ls_model));
+  if (m->L < 1 || m->L > LS_MAX_FANOUT) return LS_EINVAL;
+  return LS_OK;
+}
+
+const char* ls_status_string(ls_status s) {
+  switch (s) {
+    case LS_OK: return "ok";
+    case LS_EINVAL: return "invalid argument";
+    case LS_ENOMEM: return "out of memory / workspace too small";
+    case LS_ENAN: return "NaN key";
+    case LS_ETIMEOUT: return "device wait timed out";
+    case LS_ECUDA: return "CUDA error";
+    case LS_ENOTIMPL: return "not implemented";
+    case LS_EDEVICE: return "device consistency check failed";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

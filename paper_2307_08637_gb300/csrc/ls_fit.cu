@@ -1,0 +1,1028 @@
+// ls_fit.cu -- the "training" side of learned SampleSort on GB300:
+//   Sample(A, l, r) of Alg. 2-5 (counter-based SplitMix64 positions),
+//   segmented sample sort (bitonic chunks + merge path),
+//   the FP64 closed-form least-squares fit of the two-layer RMI (Sec. 2.1-2.2),
+//   the monotone clamps of Sec. 4,
+//   the exact learned pivots (Alg. 4's implicit pivots, as lower bounds),
+//   Alg. 5's model choice, SampleSort splitter tables with IPS4o equality
+//   buckets (Sec. 2.4), the radix directory over a pivot table, and the
+//   forward / backward pass of the fit objective.
+#include <cfloat>
+#include <cmath>
+
+#include "ls_kernels.h"
+
+namespace lsg {
+
+namespace {
+
+constexpr int kTPB = 256;
+
+inline unsigned grid_for(uint64_t n, int tpb = kTPB) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// Largest f in [0, n) with prefix[f] <= g (prefix has n+1 non-decreasing entries).
+__device__ __forceinline__ uint32_t find_seg(const uint64_t* __restrict__ prefix, uint32_t n, uint64_t g) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (prefix[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Closed-form least squares y = a X + b from (n, sum X, sum y, sum Xy, sum X^2),
+// slope clamped at 0 (every model non-decreasing).
+__device__ __forceinline__ void linfit(double n, double sx, double sy, double sxy, double sxx, double* a,
+                                       double* b) {
+  double t1 = __dmul_rn(n, sxx);
+  double t2 = __dmul_rn(sx, sx);
+  double D = __dsub_rn(t1, t2);
+  double A = 0.0;
+  if (D > 0.0) {
+    double u1 = __dmul_rn(n, sxy);
+    double u2 = __dmul_rn(sx, sy);
+    double num = __dsub_rn(u1, u2);
+    A = __ddiv_rn(num, D);
+  }
+  A = dmax(A, 0.0);
+  double ax = __dmul_rn(A, sx);
+  double r = __dsub_rn(sy, ax);
+  *a = A;
+  *b = __ddiv_rn(r, n);
+}
+
+// One chunk (<= 256 consecutive positions [j0, j1)) of the least-squares sums:
+// X_j = v(s_j) - x0, y_j = j / S, summed left to right from +0.0.
+__device__ __forceinline__ void chunk_sums(const uint64_t* __restrict__ s, uint64_t j0, uint64_t j1, double x0,
+                                           double Sd, int dt, double out[4]) {
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+  for (uint64_t j = j0; j < j1; ++j) {
+    double X = __dsub_rn(ord_value(s[j], dt), x0);
+    double y = __ddiv_rn(__ull2double_rn(j), Sd);
+    double xy = __dmul_rn(X, y);
+    double xx = __dmul_rn(X, X);
+    p0 = __dadd_rn(p0, X);
+    p1 = __dadd_rn(p1, y);
+    p2 = __dadd_rn(p2, xy);
+    p3 = __dadd_rn(p3, xx);
+  }
+  out[0] = p0;
+  out[1] = p1;
+  out[2] = p2;
+  out[3] = p3;
+}
+
+// Fixed pairwise tree over m partials, done by one thread in place:
+// p[i] = p[2i] + p[2i+1], an odd last value carried up (same shape as the
+// oracle's tree_sum).  Empty -> +0.0.
+__device__ double thread_tree_sum(double* p, uint64_t m) {
+  if (m == 0) return 0.0;
+  while (m > 1) {
+    uint64_t h = m >> 1;
+    for (uint64_t i = 0; i < h; ++i) p[i] = __dadd_rn(p[2 * i], p[2 * i + 1]);
+    if (m & 1) p[h] = p[m - 1];
+    m = h + (m & 1);
+  }
+  return p[0];
+}
+
+// Same tree done by a whole block, ping-ponging between p and q (same size).
+__device__ double block_tree_sum(double* p, double* q, uint64_t m) {
+  if (m == 0) return 0.0;
+  while (m > 1) {
+    uint64_t h = m >> 1;
+    for (uint64_t i = threadIdx.x; i < h; i += blockDim.x) q[i] = __dadd_rn(p[2 * i], p[2 * i + 1]);
+    if ((m & 1) && threadIdx.x == 0) q[h] = p[m - 1];
+    __syncthreads();
+    double* t = p;
+    p = q;
+    q = t;
+    m = h + (m & 1);
+  }
+  double r = p[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ sampling
+
+__global__ void k_sample_gather(FreshArgs f, RunParams rp, uint64_t* __restrict__ samp) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= f.total_samples) return;
+  uint32_t fi = find_seg(f.samp_prefix, f.nfresh, g);
+  uint64_t j = g - f.samp_prefix[fi];
+  uint32_t pi = f.fresh[fi];
+  const Item& it = f.items[pi];
+  const Plan& pl = f.plans[pi];
+  uint64_t n = it.n;
+  uint64_t pos;
+  if ((uint64_t)pl.S >= n) {
+    pos = j;  // S == n: every key, in index order
+  } else {
+    uint64_t h = seed_item(rp.seed, it.segment, it.level, it.gidx);
+    uint64_t r = splitmix64(h + (j + 1) * kGolden);
+    pos = __umul64hi(r, n);
+  }
+  const uint64_t* src = it.buf ? f.keysB : f.keysA;
+  samp[pl.sample_off + j] = ord_of(src[it.lo + pos], rp.dt);
+}
+
+__global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  bool valid = g < f.total_samples;
+  uint32_t fi = valid ? find_seg(f.samp_prefix, f.nfresh, g) : 0xFFFFFFFFu;
+  bool dup = false;
+  if (valid) {
+    uint64_t j = g - f.samp_prefix[fi];
+    dup = (j > 0) && (samp[g] == samp[g - 1]);
+  }
+  unsigned dmask = __ballot_sync(0xFFFFFFFFu, dup);
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, fi);
+  unsigned lane = threadIdx.x & 31;
+  if (valid && lane == (unsigned)(__ffs(peers) - 1)) {
+    unsigned c = __popc(dmask & peers);
+    if (c) atomicAdd(&f.plans[f.fresh[fi]].dups, (unsigned long long)c);
+  }
+}
+
+// ------------------------------------------------ segmented sample sort
+
+__global__ void __launch_bounds__(kTPB) k_sort_chunks(uint64_t* __restrict__ a, const uint64_t* __restrict__ off,
+                                                      const uint64_t* __restrict__ cpre, uint32_t nseg) {
+  __shared__ uint64_t sm[kSortChunk];
+  uint64_t c = blockIdx.x;
+  uint32_t s = find_seg(cpre, nseg, c);
+  uint64_t base = off[s] + (c - cpre[s]) * kSortChunk;
+  uint64_t end = off[s + 1];
+  if (end > base + kSortChunk) end = base + kSortChunk;
+  uint32_t len = (uint32_t)(end - base);
+  for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) sm[i] = (i < len) ? a[base + i] : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= kSortChunk; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+        uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          uint64_t x = sm[i], y = sm[ixj];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            sm[i] = y;
+            sm[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) a[base + i] = sm[i];
+}
+
+// One merge pass: within each segment, runs [2pw, 2pw+w) and [2pw+w, 2pw+2w)
+// are merged (merge path, 8 outputs per thread; ties take the left run).
+__global__ void __launch_bounds__(kTPB) k_merge_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                     const uint64_t* __restrict__ off,
+                                                     const uint64_t* __restrict__ cpre, uint32_t nseg, uint64_t w) {
+  uint64_t c = blockIdx.x;
+  uint32_t s = find_seg(cpre, nseg, c);
+  uint64_t sb = off[s];
+  uint64_t len = off[s + 1] - sb;
+  uint64_t o = (c - cpre[s]) * kSortChunk + (uint64_t)threadIdx.x * 8;
+  if (o >= len) return;
+  uint64_t a0 = (o / (2 * w)) * (2 * w);
+  uint64_t a1 = a0 + w < len ? a0 + w : len;
+  uint64_t b1 = a0 + 2 * w < len ? a0 + 2 * w : len;
+  uint64_t na = a1 - a0, nbb = b1 - a1;
+  const uint64_t* A = in + sb + a0;
+  const uint64_t* Bv = in + sb + a1;
+  uint64_t diag = o - a0;
+  uint64_t lo = diag > nbb ? diag - nbb : 0;
+  uint64_t hi = diag < na ? diag : na;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (A[mid] <= Bv[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  uint64_t i = lo, j = diag - lo;
+  uint64_t lim = b1 - o < 8 ? b1 - o : 8;
+  for (uint64_t k = 0; k < lim; ++k) {
+    bool takeA = (j >= nbb) || (i < na && A[i] <= Bv[j]);
+    out[sb + o + k] = takeA ? A[i++] : Bv[j++];
+  }
+}
+
+// ---------------------------------------------------------------- fit
+
+__global__ void k_fit_root_partials(FitArgs a, RunParams rp) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= a.total_rchunks) return;
+  uint32_t c = find_seg(a.rchunk_prefix, a.ncand, g);
+  uint64_t k = g - a.rchunk_prefix[c];
+  const Plan& pl = a.plans[a.cand[c]];
+  uint64_t S = pl.S;
+  const uint64_t* s = a.samp + pl.sample_off;
+  double x0 = ord_value(s[0], rp.dt);
+  uint64_t j0 = k * kChunk;
+  uint64_t j1 = j0 + kChunk < S ? j0 + kChunk : S;
+  double out[4];
+  chunk_sums(s, j0, j1, x0, __ull2double_rn(S), rp.dt, out);
+  for (int q = 0; q < 4; ++q) a.rpart[q * a.total_rchunks + g] = out[q];
+}
+
+// Per candidate: tree-combine the root chunk partials, fit the root.
+__global__ void k_fit_root_finish(FitArgs a, RunParams rp) {
+  uint32_t c = blockIdx.x;
+  const Plan& pl = a.plans[a.cand[c]];
+  uint64_t b0 = a.rchunk_prefix[c];
+  uint64_t m = a.rchunk_prefix[c + 1] - b0;
+  __shared__ double sums[4];
+  for (int q = 0; q < 4; ++q) {
+    double* p = a.rpart + q * a.total_rchunks + b0;
+    double* t = a.rpart + (4 + q) * a.total_rchunks + b0;  // ping-pong half
+    double v = block_tree_sum(p, t, m);
+    if (threadIdx.x == 0) sums[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t S = pl.S;
+    const uint64_t* s = a.samp + pl.sample_off;
+    DModel& m0 = a.models[pl.model];
+    m0.xmin = ord_value(s[0], rp.dt);
+    m0.xmax = ord_value(s[S - 1], rp.dt);
+    m0.rx0 = m0.xmin;
+    double ra, rb;
+    linfit(__ull2double_rn(S), sums[0], sums[1], sums[2], sums[3], &ra, &rb);
+    m0.ra = ra;
+    m0.rb = rb;
+    m0.L = a.L;
+    m0.S = (uint32_t)S;
+    m0.leaf_off = (uint64_t)pl.model * a.L;
+    m0.ok = 0;
+  }
+}
+
+// Route every sample point to its leaf (stored), then mark run starts.
+__global__ void k_fit_route_leaf(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_of) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= a.total_cand_samples) return;
+  uint32_t c = find_seg(a.cand_soff, a.ncand, g);
+  uint64_t j = g - a.cand_soff[c];
+  const Plan& pl = a.plans[a.cand[c]];
+  DModel m = a.models[pl.model];
+  leaf_of[g] = root_leaf(m, ord_value(a.samp[pl.sample_off + j], rp.dt));
+}
+
+__global__ void k_fit_route_starts(FitArgs a, const uint32_t* __restrict__ leaf_of) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= a.total_cand_samples) return;
+  uint32_t c = find_seg(a.cand_soff, a.ncand, g);
+  uint64_t j = g - a.cand_soff[c];
+  uint64_t S = a.cand_soff[c + 1] - a.cand_soff[c];
+  uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
+  uint32_t lf = leaf_of[g];
+  lf = lf < a.L ? lf : a.L - 1;  // root_leaf is already clamped; never index past the run table
+  if (j == 0) {
+    for (uint32_t i = 0; i <= lf; ++i) ls[i] = 0;
+  } else {
+    uint32_t prev = leaf_of[g - 1];
+    prev = prev < a.L ? prev : a.L - 1;
+    for (uint32_t i = prev + 1; i <= lf; ++i) ls[i] = (uint32_t)j;
+  }
+  if (j == S - 1) {
+    for (uint32_t i = lf + 1; i <= a.L; ++i) ls[i] = (uint32_t)S;
+  }
+}
+
+__global__ void k_fit_leaf_chunk_count(FitArgs a) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint64_t tot = (uint64_t)a.ncand * a.L;
+  if (g > tot) return;
+  if (g == tot) {
+    a.lchunk_cnt[g] = 0;
+    return;
+  }
+  uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
+  const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
+  uint64_t cnt = ls[i + 1] > ls[i] ? ls[i + 1] - ls[i] : 0;
+  a.lchunk_cnt[g] = (cnt + kChunk - 1) / kChunk;
+}
+
+__global__ void k_fit_leaf_partials(FitArgs a, RunParams rp) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint32_t tot = a.ncand * a.L;
+  if (g >= a.lchunk_prefix[tot] || g >= a.lchunk_bound) return;
+  uint32_t ci = find_seg(a.lchunk_prefix, tot, g);
+  uint64_t k = g - a.lchunk_prefix[ci];
+  uint32_t c = ci / a.L, i = ci % a.L;
+  const Plan& pl = a.plans[a.cand[c]];
+  const uint64_t* s = a.samp + pl.sample_off;
+  const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
+  uint64_t S = pl.S;
+  uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
+  uint64_t st = ls[i] < en ? ls[i] : en;
+  if (st >= en) return;
+  double x0 = ord_value(s[st], rp.dt);
+  uint64_t j0 = st + k * kChunk;
+  uint64_t j1 = j0 + kChunk < en ? j0 + kChunk : en;
+  double out[4];
+  chunk_sums(s, j0, j1, x0, __ull2double_rn((uint64_t)pl.S), rp.dt, out);
+  for (int q = 0; q < 4; ++q) a.lpart[q * a.lchunk_bound + g] = out[q];
+}
+
+__global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_cnt) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)a.ncand * a.L) return;
+  uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
+  const Plan& pl = a.plans[a.cand[c]];
+  const uint64_t* s = a.samp + pl.sample_off;
+  const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
+  uint64_t S = pl.S;
+  uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
+  uint64_t st = ls[i] < en ? ls[i] : en;
+  uint64_t cnt = en - st;
+  DModel m = a.models[pl.model];
+  Leaf l;
+  if (cnt == 0) {
+    l.x0 = m.xmin;
+    l.a = 0.0;
+    l.b = 0.0;
+    l.lo = 0.0;
+    l.hi = 0.0;
+  } else {
+    uint64_t p0 = a.lchunk_prefix[g];
+    uint64_t nch = a.lchunk_prefix[g + 1] - p0;
+    double sm[4];
+    for (int q = 0; q < 4; ++q) sm[q] = thread_tree_sum(a.lpart + q * a.lchunk_bound + p0, nch);
+    double x_first = ord_value(s[st], rp.dt);
+    double x_last = ord_value(s[en - 1], rp.dt);
+    l.x0 = x_first;
+    linfit(__ull2double_rn(cnt), sm[0], sm[1], sm[2], sm[3], &l.a, &l.b);
+    l.lo = leaf_eval(l, x_first);  // raw min of the leaf (slope >= 0)
+    l.hi = leaf_eval(l, x_last);   // raw max
+  }
+  a.leaves[m.leaf_off + i] = l;
+  leaf_cnt[m.leaf_off + i] = (uint32_t)cnt;
+}
+
+// Monotone RMI (Sec. 4): hi_i = max(0, max over non-empty j <= i of raw
+// maxima); lo_i = max(raw_lo_i, hi_{i-1}); empty leaves take hi_{i-1}.  The
+// values are never -0.0 and never NaN for a finite model, so max is
+// associative and a parallel prefix max gives the sequential result bit for
+// bit.  One block per candidate; also sets the model's finite flag.
+__global__ void __launch_bounds__(1024) k_fit_monotone(FitArgs a, const uint32_t* __restrict__ leaf_cnt) {
+  uint32_t c = blockIdx.x;
+  const Plan& pl = a.plans[a.cand[c]];
+  DModel& md = a.models[pl.model];
+  Leaf* lv = a.leaves + md.leaf_off;
+  const uint32_t* cn = leaf_cnt + md.leaf_off;
+  uint32_t L = a.L;
+  uint32_t per = (L + blockDim.x - 1) / blockDim.x;
+  uint32_t i0 = threadIdx.x * per;
+  double loc = 0.0;  // running max of raw maxima in my range (floor +0.0 is the initial hi)
+  bool fin = true;
+  for (uint32_t i = i0; i < i0 + per && i < L; ++i) {
+    if (cn[i]) loc = dmax(loc, lv[i].hi);
+    Leaf l = lv[i];
+    fin = fin && isfinite(l.a) && isfinite(l.b) && isfinite(l.lo) && isfinite(l.hi);
+  }
+  // exclusive block scan of maxima
+  __shared__ double wsum[32];
+  unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double incl = loc;
+  for (int d = 1; d < 32; d <<= 1) {
+    double o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl = dmax(incl, o);
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned nw = blockDim.x >> 5;
+    double v = lane < nw ? wsum[lane] : 0.0;
+    for (int d = 1; d < 32; d <<= 1) {
+      double o = __shfl_up_sync(0xFFFFFFFFu, v, d);
+      if (lane >= (unsigned)d) v = dmax(v, o);
+    }
+    if (lane < nw) wsum[lane] = v;
+  }
+  __syncthreads();
+  double excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  if (lane == 0) excl = 0.0;
+  if (wid > 0) excl = dmax(excl, wsum[wid - 1]);
+  // sequential pass over my range with the exclusive prefix
+  double hprev = excl;
+  for (uint32_t i = i0; i < i0 + per && i < L; ++i) {
+    Leaf l = lv[i];
+    if (cn[i] == 0) {
+      l.lo = hprev;
+      l.hi = hprev;
+    } else {
+      l.lo = dmax(l.lo, hprev);
+      l.hi = dmax(l.hi, l.lo);
+    }
+    hprev = l.hi;
+    lv[i] = l;
+  }
+  int allfin = __syncthreads_and(fin ? 1 : 0);
+  if (threadIdx.x == 0) {
+    double range = __dsub_rn(md.xmax, md.xmin);
+    bool ok = allfin && isfinite(md.xmin) && isfinite(md.xmax) && isfinite(range) && isfinite(md.ra) &&
+              isfinite(md.rb);
+    md.ok = ok ? 1u : 0u;
+  }
+}
+
+// --------------------------------------------------- learned pivots
+
+// v(u) = F(key(u)) * P: continuous refinement value of ord u.
+__device__ __forceinline__ double refine_value(const DModel& m, const Leaf* lv, uint64_t u, double P, int dt) {
+  return __dmul_rn(model_F(m, lv, ord_value(u, dt)), P);
+}
+
+// Smallest u in [lo, hi] with v(u) >= t, given v(lo) < t <= v(hi).  v is
+// monotone in u, so any bracketing search is exact; interpolation steps are
+// interleaved with bisection so at most ~3*64 evaluations are needed.
+__device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64_t lo, uint64_t hi, double t,
+                                 double P, double vlo, double vhi) {
+  uint64_t L = lo, H = hi;
+  double vL = vlo, vH = vhi;
+  for (int it = 0; it < 256 && H - L > 1; ++it) {
+    uint64_t span = H - L;
+    uint64_t mid;
+    if ((it % 3) != 2 && vH > vL) {
+      double frac = (t - vL) / (vH - vL);
+      double off = frac * (double)span;
+      uint64_t o;
+      if (!(off >= 1.0)) o = 1;
+      else if (off >= (double)(span - 1)) o = span - 1;
+      else o = (uint64_t)off;
+      mid = L + o;
+    } else {
+      mid = L + (span >> 1);
+    }
+    double vm = refine_value(m, lv, mid, P, dt);
+    if (vm >= t) {
+      H = mid;
+      vH = vm;
+    } else {
+      L = mid;
+      vL = vm;
+    }
+  }
+  return H;
+}
+
+__global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
+                                 uint32_t nb_pad, const DModel* models, const Leaf* leaves,
+                                 uint64_t* __restrict__ pivots, RunParams rp) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)nlist * nb_pad) return;
+  uint32_t li = (uint32_t)(g / nb_pad), j = (uint32_t)(g % nb_pad);
+  uint32_t pi = list[li];
+  Plan& pl = plans[pi];
+  const Item& it = items[pi];
+  DModel m = models[pl.model];
+  const Leaf* lv = leaves + m.leaf_off;
+  uint32_t B = rp.B;
+  double P = pl.P, Bg = pl.Bg;
+  uint64_t lo = it.ord_lo, hi = it.ord_hi;
+  uint64_t* T = pivots + pl.tab_off;
+  uint32_t kmin = refine_id(m, lv, ord_value(lo, rp.dt), P, Bg, B);
+  uint32_t kmax = refine_id(m, lv, ord_value(hi, rp.dt), P, Bg, B);
+  if (j == 0) {
+    T[0] = lo;
+    pl.kmax = kmax;
+    pl.nb = B;
+    pl.nb_pad = nb_pad;
+    return;
+  }
+  if (j >= B) {
+    T[j] = ~0ull;
+    return;
+  }
+  if (j <= kmin) {
+    T[j] = lo;
+    return;
+  }
+  if (j > kmax) {
+    T[j] = hi;
+    return;
+  }
+  double t = __dadd_rn((double)j, Bg);
+  double vlo = refine_value(m, lv, lo, P, rp.dt);
+  double vhi = refine_value(m, lv, hi, P, rp.dt);
+  T[j] = search_pivot(m, lv, rp.dt, lo, hi, t, P, vlo, vhi);
+}
+
+// Classify the candidates' own samples with their learned pivots (sample
+// imbalance test) and keep the largest bucket.
+__global__ void k_imbalance_count(FitArgs a, const uint64_t* __restrict__ pivots,
+                                  unsigned long long* __restrict__ cnt) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= a.total_cand_samples) return;
+  uint32_t c = find_seg(a.cand_soff, a.ncand, g);
+  uint64_t j = g - a.cand_soff[c];
+  const Plan& pl = a.plans[a.cand[c]];
+  if (!a.models[pl.model].ok) return;
+  uint64_t u = a.samp[pl.sample_off + j];
+  uint32_t b = pivot_count(pivots + pl.tab_off, pl.nb_pad, u);
+  b = b < pl.kmax ? b : pl.kmax;
+  atomicAdd(&cnt[pl.cnt_off + b], 1ull);
+}
+
+__global__ void k_imbalance_max(FitArgs a, unsigned long long* __restrict__ cnt) {
+  uint32_t c = blockIdx.x;
+  Plan& pl = a.plans[a.cand[c]];
+  unsigned long long mx = 0;
+  for (uint32_t b = threadIdx.x; b < pl.nb_pad; b += blockDim.x) {
+    unsigned long long v = cnt[pl.cnt_off + b];
+    mx = v > mx ? v : mx;
+    cnt[pl.cnt_off + b] = 0;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    unsigned long long o = __shfl_down_sync(0xFFFFFFFFu, mx, d);
+    mx = o > mx ? o : mx;
+  }
+  __shared__ unsigned long long wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long r = 0;
+    for (unsigned w = 0; w < blockDim.x / 32; ++w) r = wm[w] > r ? wm[w] : r;
+    if (a.models[pl.model].ok) pl.imb = r;
+  }
+}
+
+// Alg. 5 BuildPartitionModel: RMI iff the input is large and the sample has
+// few duplicates (and, in AUTO, the sample is not badly imbalanced).
+__global__ void k_decide(FreshArgs f, const DModel* models, RunParams rp) {
+  uint32_t fi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fi >= f.nfresh) return;
+  uint32_t pi = f.fresh[fi];
+  Plan& pl = f.plans[pi];
+  const Item& it = f.items[pi];
+  bool learned = false;
+  bool want = false;
+  if (it.kind != KIND_FORCE_SPLITTER && pl.want) {
+    if (rp.partitioner == LS_PART_LEARNED) {
+      want = true;
+    } else if (rp.partitioner == LS_PART_AUTO) {
+      double frac = __ddiv_rn(__ull2double_rn(pl.dups), __ull2double_rn((uint64_t)pl.S));
+      want = (it.n >= rp.min_learned_n) && (frac <= rp.dup_frac);
+    }
+  }
+  if (!want) pl.imb = 0;  // Alg. 5 never fits a model it does not want
+  if (want && models[pl.model].ok) {
+    {
+      learned = true;
+      if (rp.partitioner == LS_PART_AUTO) {
+        double thr = __dmul_rn(rp.tau, __ull2double_rn((uint64_t)pl.S));
+        thr = __ddiv_rn(thr, (double)rp.B);
+        thr = dmax(thr, 16.0);
+        if (__ull2double_rn(pl.imb) > thr) learned = false;
+      }
+    }
+  }
+  if (learned) {
+    pl.decision = LS_DEC_LEARNED;
+    pl.cls = (rp.classify_mode == LS_CLASSIFY_TREE) ? CLS_TREE
+             : (rp.classify_mode == LS_CLASSIFY_DIRECT) ? CLS_DIRECT
+                                                         : CLS_DIR;
+  } else {
+    pl.decision = LS_DEC_SPLITTER;  // refined to SPLITTER_EQ by the table build
+    pl.model = -1;
+  }
+}
+
+// SampleSort splitters from the sorted sample (Sec. 2.4): B_s - 1 equally
+// spaced sample elements; equality buckets if two splitters coincide (or
+// forced).  Written as exact pivots: bucket = #{j : T[j] <= ord}.
+__global__ void __launch_bounds__(1024) k_splitter_build(FreshArgs f, const uint64_t* __restrict__ samp,
+                                                         uint64_t* __restrict__ pivots, RunParams rp) {
+  uint32_t pi = f.fresh[blockIdx.x];
+  Plan& pl = f.plans[pi];
+  const Item& it = f.items[pi];
+  if (pl.decision == LS_DEC_LEARNED) return;
+  __shared__ uint64_t spl[LS_MAX_FANOUT];
+  __shared__ uint16_t pos[LS_MAX_FANOUT];
+  __shared__ uint32_t wtot[32];
+  __shared__ int s_dup;
+  uint64_t S = pl.S;
+  const uint64_t* s = samp + pl.sample_off;
+  bool force = it.kind == KIND_FORCE_SPLITTER;
+  uint32_t bsmax = rp.bs_max;
+  if (!force && rp.partitioner == LS_PART_AUTO && rp.bs_auto < bsmax) bsmax = rp.bs_auto;
+  uint32_t bs = 1;
+  while ((uint64_t)bs * 2 <= bsmax && (uint64_t)bs * 2 <= S && bs * 2 <= LS_MAX_FANOUT) bs *= 2;
+  if (bs < 2) bs = 2;
+  uint32_t ns = bs - 1;
+  if (threadIdx.x == 0) s_dup = 0;
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < ns; k += blockDim.x) spl[k] = s[((uint64_t)(k + 1) * S) / bs];
+  __syncthreads();
+  for (uint32_t k = threadIdx.x + 1; k < ns; k += blockDim.x)
+    if (spl[k] == spl[k - 1]) s_dup = 1;
+  __syncthreads();
+  bool eq = s_dup || force;
+  uint64_t* T = pivots + pl.tab_off;
+  uint64_t lo = it.ord_lo, hi = it.ord_hi;
+  uint32_t nb;
+  uint32_t npiv;  // pivots T[1..npiv]
+  if (eq) {
+    // unique positions: exclusive scan of "new value" flags (4 per thread max)
+    uint32_t per = (ns + blockDim.x - 1) / blockDim.x;
+    uint32_t k0 = threadIdx.x * per;
+    uint32_t cntl = 0;
+    for (uint32_t k = k0; k < k0 + per && k < ns; ++k) cntl += (k == 0 || spl[k] != spl[k - 1]);
+    unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = cntl;
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= (unsigned)d) incl += o;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned nw = blockDim.x >> 5;
+      uint32_t v = lane < nw ? wtot[lane] : 0;
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xFFFFFFFFu, v, d);
+        if (lane >= (unsigned)d) v += o;
+      }
+      if (lane < nw) wtot[lane] = v;
+    }
+    __syncthreads();
+    uint32_t excl = incl - cntl + (wid > 0 ? wtot[wid - 1] : 0);
+    for (uint32_t k = k0; k < k0 + per && k < ns; ++k) {
+      if (k == 0 || spl[k] != spl[k - 1]) pos[excl++] = (uint16_t)k;
+    }
+    uint32_t m = wtot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    nb = 2 * m + 1;
+    npiv = 2 * m;
+    for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) {
+      uint64_t u = spl[pos[q]];
+      T[2 * q + 1] = u;
+      T[2 * q + 2] = (u == ~0ull) ? ~0ull : u + 1;  // u + 1 overflow: never reached
+    }
+  } else {
+    nb = bs;
+    npiv = ns;
+    for (uint32_t k = threadIdx.x; k < ns; k += blockDim.x) {
+      uint64_t u = spl[k];
+      T[k + 1] = (u == ~0ull) ? ~0ull : u + 1;
+    }
+  }
+  __syncthreads();
+  // kmax = number of pivots a key <= hi can reach (pivots are sorted):
+  // u_q counts iff u_q <= hi, u_q + 1 counts iff u_q < hi.
+  uint32_t cnt_le = 0;
+  if (eq) {
+    uint32_t m = (nb - 1) / 2;
+    for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) {
+      uint64_t u = spl[pos[q]];
+      cnt_le += (u <= hi) + (u < hi);
+    }
+  } else {
+    for (uint32_t k = threadIdx.x; k < ns; k += blockDim.x) cnt_le += (spl[k] < hi);
+  }
+  __shared__ uint32_t s_k;
+  if (threadIdx.x == 0) s_k = 0;
+  __syncthreads();
+  for (int d = 16; d > 0; d >>= 1) cnt_le += __shfl_down_sync(0xFFFFFFFFu, cnt_le, d);
+  if ((threadIdx.x & 31) == 0 && cnt_le) atomicAdd(&s_k, cnt_le);
+  __syncthreads();
+  uint32_t kmax = s_k;
+  uint32_t nb_pad = 2;
+  while (nb_pad < nb) nb_pad <<= 1;
+  for (uint32_t j = threadIdx.x; j < nb_pad; j += blockDim.x) {
+    if (j == 0) T[0] = lo;
+    else if (j > npiv || j > kmax) T[j] = ~0ull;
+    else if (T[j] < lo) T[j] = lo;
+  }
+  if (threadIdx.x == 0) {
+    pl.nb = nb;
+    pl.nb_pad = nb_pad;
+    pl.kmax = kmax;
+    pl.decision = eq ? LS_DEC_SPLITTER_EQ : LS_DEC_SPLITTER;
+    pl.cls = (rp.classify_mode == LS_CLASSIFY_DIRECTORY) ? CLS_DIR : CLS_TREE;
+    pl.model = -1;
+  }
+}
+
+__global__ void k_dir_build(Plan* plans, uint32_t nplans, uint32_t cells, const uint64_t* __restrict__ pivots,
+                            uint16_t* __restrict__ dirs) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  uint64_t per = (uint64_t)cells + 1;
+  if (g >= (uint64_t)nplans * per) return;
+  uint32_t pi = (uint32_t)(g / per), c = (uint32_t)(g % per);
+  Plan& pl = plans[pi];
+  if (pl.cls != CLS_DIR) return;
+  const uint64_t* T = pivots + pl.tab_off;
+  uint32_t kmax = pl.kmax;
+  uint64_t dlo, dhi;
+  uint32_t shift = 0;
+  if (kmax == 0) {
+    dlo = ~0ull;
+    dhi = ~0ull;
+  } else {
+    dlo = T[1];
+    dhi = T[kmax];
+    uint64_t span = dhi - dlo;
+    uint32_t lc = 31 - __clz(cells);
+    uint32_t bl = span ? 64 - __clzll((long long)span) : 0;
+    shift = bl > lc ? bl - lc : 0;
+  }
+  uint16_t* D = dirs + pl.dir_off;
+  uint32_t v;
+  if (kmax == 0) {
+    v = 0;
+  } else {
+    uint64_t add = shift >= 64 ? 0 : ((uint64_t)c << shift);
+    uint64_t x = (add > ~0ull - dlo) ? ~0ull : dlo + add;
+    v = pivot_count(T, pl.nb_pad, x);
+    v = v < kmax ? v : kmax;
+  }
+  D[c] = (uint16_t)v;
+  if (c == 0) {
+    pl.dir_lo = dlo;
+    pl.dir_hi = dhi;
+    pl.dir_shift = shift;
+    pl.dir_cells = cells;
+  }
+}
+
+// ------------------------------------------------ fit forward / backward
+
+struct GradScratch {
+  double* rl;      // leaf residuals
+  double* Xl;      // leaf X
+  double* rr;      // root residuals
+  double* Xr;      // root X
+  uint64_t* key;   // (leaf << 32) | j
+  uint64_t* key2;  // sort scratch
+  uint64_t* segoff;   // 2
+  uint64_t* cpre;     // 2
+  uint32_t* lstart;   // L + 1
+  uint64_t* lch;      // L + 1 chunk counts / prefix
+  uint64_t* lchp;     // L + 1
+  uint64_t* stmp;     // scan tmp
+  size_t stmp_elems;
+  double* part;       // 2 * (S/256 + L + 2) * 2
+  double* rpart;      // 4 * (S/256 + 1)
+};
+
+__global__ void k_grad_fwd(const DModel* mp, const Leaf* leaves, const uint64_t* __restrict__ bits, uint64_t S,
+                           int dt, double* pred, double* resid, GradScratch g) {
+  uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (j >= S) return;
+  DModel m = *mp;
+  double x = key_value(bits[j], dt);
+  double xc = dmax(x, m.xmin);
+  xc = dmin(xc, m.xmax);
+  uint32_t i = root_leaf(m, xc);
+  Leaf l = leaves[i];
+  double y = __ddiv_rn(__ull2double_rn(j), __ull2double_rn(S));
+  double X = __dsub_rn(xc, l.x0);
+  double p = __dmul_rn(l.a, X);
+  p = __dadd_rn(p, l.b);
+  double r = __dsub_rn(p, y);
+  if (pred) pred[j] = p;
+  if (resid) resid[j] = r;
+  g.rl[j] = r;
+  g.Xl[j] = X;
+  double XR = __dsub_rn(xc, m.rx0);
+  double pr = __dmul_rn(m.ra, XR);
+  pr = __dadd_rn(pr, m.rb);
+  g.rr[j] = __dsub_rn(pr, y);
+  g.Xr[j] = XR;
+  g.key[j] = ((uint64_t)i << 32) | j;
+}
+
+__global__ void k_grad_leaf_starts(const uint64_t* __restrict__ sorted, uint64_t S, uint32_t L, uint32_t* lstart) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= S) return;
+  uint32_t lf = (uint32_t)(sorted[q] >> 32);
+  lf = lf < L ? lf : L - 1;
+  if (q == 0) {
+    for (uint32_t i = 0; i <= lf; ++i) lstart[i] = 0;
+  } else {
+    uint32_t prev = (uint32_t)(sorted[q - 1] >> 32);
+    prev = prev < L ? prev : L - 1;
+    for (uint32_t i = prev + 1; i <= lf; ++i) lstart[i] = (uint32_t)q;
+  }
+  if (q == S - 1)
+    for (uint32_t i = lf + 1; i <= L; ++i) lstart[i] = (uint32_t)S;
+}
+
+__global__ void k_grad_chunk_count(const uint32_t* lstart, uint32_t L, uint64_t* lch) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > L) return;
+  lch[i] = (i == L) ? 0 : ((uint64_t)(lstart[i + 1] - lstart[i]) + kChunk - 1) / kChunk;
+}
+
+__global__ void k_grad_leaf_partials(const uint64_t* __restrict__ sorted, const uint32_t* lstart, const uint64_t* lchp,
+                                     uint32_t L, uint64_t bound, GradScratch g) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= lchp[L] || q >= bound) return;
+  uint32_t i = find_seg(lchp, L, q);
+  uint64_t k = q - lchp[i];
+  uint64_t st = lstart[i], en = lstart[i + 1];
+  uint64_t a0 = st + k * kChunk;
+  uint64_t a1 = a0 + kChunk < en ? a0 + kChunk : en;
+  double prx = 0.0, pr = 0.0;
+  for (uint64_t t = a0; t < a1; ++t) {
+    uint64_t j = sorted[t] & 0xFFFFFFFFull;
+    double rx = __dmul_rn(g.rl[j], g.Xl[j]);
+    prx = __dadd_rn(prx, rx);
+    pr = __dadd_rn(pr, g.rl[j]);
+  }
+  g.part[q] = prx;
+  g.part[bound + q] = pr;
+}
+
+__global__ void k_grad_leaf_finish(const uint64_t* lchp, uint32_t L, uint64_t bound, uint64_t S, GradScratch g,
+                                   double* grad_a, double* grad_b) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  uint64_t p0 = lchp[i], m = lchp[i + 1] - p0;
+  double srx = thread_tree_sum(g.part + p0, m);
+  double sr = thread_tree_sum(g.part + bound + p0, m);
+  double Sd = __ull2double_rn(S);
+  if (grad_a) grad_a[i] = __ddiv_rn(__dmul_rn(2.0, srx), Sd);
+  if (grad_b) grad_b[i] = __ddiv_rn(__dmul_rn(2.0, sr), Sd);
+}
+
+__global__ void k_grad_root_partials(uint64_t S, uint64_t nch, GradScratch g) {
+  uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  uint64_t a0 = c * kChunk, a1 = a0 + kChunk < S ? a0 + kChunk : S;
+  double prx = 0.0, pr = 0.0;
+  for (uint64_t j = a0; j < a1; ++j) {
+    double rx = __dmul_rn(g.rr[j], g.Xr[j]);
+    prx = __dadd_rn(prx, rx);
+    pr = __dadd_rn(pr, g.rr[j]);
+  }
+  g.rpart[c] = prx;
+  g.rpart[nch + c] = pr;
+}
+
+__global__ void k_grad_root_finish(uint64_t S, uint64_t nch, GradScratch g, double* grad_root) {
+  double srx = block_tree_sum(g.rpart, g.rpart + 2 * nch, nch);
+  double sr = block_tree_sum(g.rpart + nch, g.rpart + 3 * nch, nch);
+  if (threadIdx.x == 0 && grad_root) {
+    double Sd = __ull2double_rn(S);
+    grad_root[0] = __ddiv_rn(__dmul_rn(2.0, srx), Sd);
+    grad_root[1] = __ddiv_rn(__dmul_rn(2.0, sr), Sd);
+  }
+}
+
+}  // namespace
+
+// ===================================================== host launchers
+
+uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, const uint64_t* d_chunk_prefix,
+                             uint32_t nseg, uint64_t total_chunks, uint64_t max_len, cudaStream_t st,
+                             uint64_t* launches) {
+  if (total_chunks == 0) return a;
+  k_sort_chunks<<<(unsigned)total_chunks, kTPB, 0, st>>>(a, d_off, d_chunk_prefix, nseg);
+  ++*launches;
+  uint64_t* cur = a;
+  uint64_t* oth = b;
+  for (uint64_t w = kSortChunk; w < max_len; w *= 2) {
+    k_merge_pass<<<(unsigned)total_chunks, kTPB, 0, st>>>(cur, oth, d_off, d_chunk_prefix, nseg, w);
+    ++*launches;
+    uint64_t* t = cur;
+    cur = oth;
+    oth = t;
+  }
+  return cur;
+}
+
+void launch_sample_gather(const FreshArgs& f, const RunParams& rp, uint64_t* samp, cudaStream_t st) {
+  if (!f.total_samples) return;
+  k_sample_gather<<<grid_for(f.total_samples), kTPB, 0, st>>>(f, rp, samp);
+}
+
+void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st) {
+  if (!f.total_samples) return;
+  k_dups<<<grid_for(f.total_samples), kTPB, 0, st>>>(f, samp);
+}
+
+void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches) {
+  if (!a.ncand) return;
+  k_fit_root_partials<<<grid_for(a.total_rchunks, 128), 128, 0, st>>>(a, rp);
+  k_fit_root_finish<<<a.ncand, 1024, 0, st>>>(a, rp);
+  cudaMemsetAsync(a.leaf_start, 0, (size_t)a.ncand * (a.L + 1) * sizeof(uint32_t), st);
+  k_fit_route_leaf<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, rp, a.leaf_of);
+  k_fit_route_starts<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, a.leaf_of);
+  uint64_t tot = (uint64_t)a.ncand * a.L;
+  k_fit_leaf_chunk_count<<<grid_for(tot + 1), kTPB, 0, st>>>(a);
+  launch_scan_exclusive_u64(a.lchunk_cnt, a.lchunk_prefix, tot, a.scan_tmp, a.scan_tmp_elems, st);
+  k_fit_leaf_partials<<<grid_for(a.lchunk_bound, 128), 128, 0, st>>>(a, rp);
+  k_fit_leaf_finish<<<grid_for(tot, 128), 128, 0, st>>>(a, rp, a.leaf_cnt);
+  k_fit_monotone<<<a.ncand, 1024, 0, st>>>(a, a.leaf_cnt);
+  *launches += 12;
+}
+
+void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,
+                           const DModel* models, const Leaf* leaves, uint64_t* pivots, const RunParams& rp,
+                           cudaStream_t st) {
+  if (!nlist) return;
+  uint64_t n = (uint64_t)nlist * nb_pad;
+  k_learned_pivots<<<grid_for(n, 128), 128, 0, st>>>(plans, items, list, nlist, nb_pad, models, leaves, pivots, rp);
+}
+
+void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,
+                      cudaStream_t st, uint64_t* launches) {
+  (void)rp;
+  if (!a.ncand) return;
+  k_imbalance_count<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, pivots, cnt_pool);
+  k_imbalance_max<<<a.ncand, kTPB, 0, st>>>(a, cnt_pool);
+  *launches += 2;
+}
+
+void launch_decide(const FreshArgs& f, const DModel* models, const RunParams& rp, cudaStream_t st) {
+  if (!f.nfresh) return;
+  k_decide<<<grid_for(f.nfresh, 128), 128, 0, st>>>(f, models, rp);
+}
+
+void launch_splitter_build(const FreshArgs& f, const uint64_t* samp, uint64_t* pivots, const RunParams& rp,
+                           cudaStream_t st) {
+  if (!f.nfresh) return;
+  k_splitter_build<<<f.nfresh, 1024, 0, st>>>(f, samp, pivots, rp);
+}
+
+void launch_dir_build(Plan* plans, uint32_t nplans, uint32_t cells, const uint64_t* pivots, uint16_t* dirs,
+                      cudaStream_t st) {
+  if (!nplans) return;
+  uint64_t n = (uint64_t)nplans * (cells + 1);
+  k_dir_build<<<grid_for(n), kTPB, 0, st>>>(plans, nplans, cells, pivots, dirs);
+}
+
+size_t fit_grad_scratch_bytes(uint64_t S, uint32_t L) {
+  uint64_t nch = (S + kChunk - 1) / kChunk;
+  uint64_t bound = nch + L + 2;
+  size_t b = 0;
+  b += 4 * S * sizeof(double);          // rl Xl rr Xr
+  b += 2 * S * sizeof(uint64_t);        // key key2
+  b += 4 * sizeof(uint64_t);            // segoff cpre
+  b += (L + 1) * sizeof(uint32_t) + 64;
+  b += 2 * (L + 1) * sizeof(uint64_t);
+  b += scan_tmp_elems(L + 1) * sizeof(uint64_t);
+  b += 2 * bound * sizeof(double);
+  b += 4 * (nch + 1) * sizeof(double);
+  return b + 1024;
+}
+
+void launch_fit_grad(const DModel* model, const Leaf* leaves, const uint64_t* sample_bits, uint64_t S, int dt,
+                     double* pred, double* resid, double* grad_a, double* grad_b, double* grad_root, void* scratch,
+                     size_t scratch_bytes, cudaStream_t st) {
+  (void)scratch_bytes;
+  if (S == 0) return;
+  DModel hm;
+  cudaMemcpyAsync(&hm, model, sizeof(DModel), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  uint32_t L = hm.L;
+  uint64_t nch = (S + kChunk - 1) / kChunk;
+  uint64_t bound = nch + L + 2;
+  char* p = static_cast<char*>(scratch);
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  GradScratch g;
+  g.rl = reinterpret_cast<double*>(take(S * 8));
+  g.Xl = reinterpret_cast<double*>(take(S * 8));
+  g.rr = reinterpret_cast<double*>(take(S * 8));
+  g.Xr = reinterpret_cast<double*>(take(S * 8));
+  g.key = reinterpret_cast<uint64_t*>(take(S * 8));
+  g.key2 = reinterpret_cast<uint64_t*>(take(S * 8));
+  g.segoff = reinterpret_cast<uint64_t*>(take(16));
+  g.cpre = reinterpret_cast<uint64_t*>(take(16));
+  g.lstart = reinterpret_cast<uint32_t*>(take((L + 1) * 4));
+  g.lch = reinterpret_cast<uint64_t*>(take((L + 1) * 8));
+  g.lchp = reinterpret_cast<uint64_t*>(take((L + 1) * 8));
+  g.stmp_elems = scan_tmp_elems(L + 1);
+  g.stmp = reinterpret_cast<uint64_t*>(take(g.stmp_elems * 8));
+  g.part = reinterpret_cast<double*>(take(2 * bound * 8));
+  g.rpart = reinterpret_cast<double*>(take(4 * (nch + 1) * 8));
+  const Leaf* lv = leaves + hm.leaf_off;
+  k_grad_fwd<<<grid_for(S), kTPB, 0, st>>>(model, lv, sample_bits, S, dt, pred, resid, g);
+  uint64_t hoff[2] = {0, S};
+  uint64_t hcp[2] = {0, (S + kSortChunk - 1) / kSortChunk};
+  cudaMemcpyAsync(g.segoff, hoff, sizeof hoff, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(g.cpre, hcp, sizeof hcp, cudaMemcpyHostToDevice, st);
+  uint64_t dummy = 0;
+  uint64_t* sorted = segmented_sort_u64(g.key, g.key2, g.segoff, g.cpre, 1, hcp[1], S, st, &dummy);
+  k_grad_leaf_starts<<<grid_for(S), kTPB, 0, st>>>(sorted, S, L, g.lstart);
+  k_grad_chunk_count<<<grid_for(L + 1), kTPB, 0, st>>>(g.lstart, L, g.lch);
+  launch_scan_exclusive_u64(g.lch, g.lchp, L, g.stmp, g.stmp_elems, st);
+  k_grad_leaf_partials<<<grid_for(bound), kTPB, 0, st>>>(sorted, g.lstart, g.lchp, L, bound, g);
+  k_grad_leaf_finish<<<grid_for(L), kTPB, 0, st>>>(g.lchp, L, bound, S, g, grad_a, grad_b);
+  k_grad_root_partials<<<grid_for(nch), kTPB, 0, st>>>(S, nch, g);
+  k_grad_root_finish<<<1, 1024, 0, st>>>(S, nch, g, grad_root);
+  cudaStreamSynchronize(st);  // hoff / hcp live on this stack frame
+}
+
+}  // namespace lsg

@@ -1,0 +1,172 @@
+// ls_kernels.h -- host-side launch wrappers of the library's CUDA kernels
+// (internal; not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ls_common.cuh"
+
+namespace lsg {
+
+// Run parameters copied into kernels by value.
+struct RunParams {
+  uint32_t B;             // learned fanout
+  uint32_t bs_max;        // splitter fanout when forced / LEARNED fallback
+  uint32_t bs_auto;       // splitter fanout when AUTO picks the tree
+  uint32_t T;             // base-case threshold
+  uint32_t max_depth;
+  uint32_t min_sample;
+  double sample_rate;
+  double dup_frac;
+  double tau;
+  uint64_t min_learned_n;
+  uint64_t seed;
+  int32_t partitioner;    // ls_partitioner
+  int32_t recurse;        // ls_recurse
+  int32_t classify_mode;  // ls_classify_mode
+  int32_t dt;             // 0 f64, 1 u64
+  uint32_t tile;          // keys per partition tile
+  uint32_t dir_bits;      // log2 of directory cells
+};
+
+// ---- generic helpers (ls_partition.cu)
+void launch_scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, uint64_t* tmp, size_t tmp_elems,
+                               cudaStream_t st);
+size_t scan_tmp_elems(size_t n);
+void launch_fill_u64(uint64_t* p, uint64_t v, size_t n, cudaStream_t st);
+
+// ---- segmented sort of u64 values (ls_fit.cu)
+// Sorts each segment [off[s], off[s+1]) of `a` ascending.  `b` is scratch of
+// the same size; returns the buffer that holds the result (a or b).
+uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, const uint64_t* d_chunk_prefix,
+                             uint32_t nseg, uint64_t total_chunks, uint64_t max_len, cudaStream_t st,
+                             uint64_t* launches);
+
+// ---- fresh-item pipeline (ls_fit.cu)
+struct FreshArgs {
+  const Item* items;       // batch items
+  Plan* plans;             // batch plans
+  const uint32_t* fresh;   // plan indices of fresh items
+  const uint64_t* samp_prefix;  // nfresh+1 sample offsets
+  uint32_t nfresh;
+  uint64_t total_samples;
+  const uint64_t* keysA;
+  const uint64_t* keysB;
+};
+void launch_sample_gather(const FreshArgs& f, const RunParams& rp, uint64_t* samp, cudaStream_t st);
+void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st);
+
+struct FitArgs {
+  Plan* plans;
+  const Item* items;
+  const uint32_t* cand;        // plan indices of fit candidates
+  const uint64_t* cand_soff;   // ncand+1 prefix of sample sizes (candidates only, offsets into samp)
+  const uint64_t* rchunk_prefix; // ncand+1 prefix of root chunks
+  uint32_t ncand;
+  uint64_t total_rchunks;
+  uint64_t total_cand_samples;
+  uint64_t lchunk_bound;       // upper bound on leaf chunks
+  const uint64_t* samp;        // sorted samples (ord), indexed by plan.sample_off
+  DModel* models;
+  Leaf* leaves;
+  uint32_t L;
+  // scratch
+  double* rpart;               // 4 * total_rchunks
+  uint32_t* leaf_start;        // ncand * (L+1)
+  uint64_t* lchunk_cnt;        // ncand*L + 1
+  uint64_t* lchunk_prefix;     // ncand*L + 1
+  uint64_t* scan_tmp;
+  size_t scan_tmp_elems;
+  double* lpart;               // 4 * lchunk_bound
+  uint32_t* leaf_of;           // total_cand_samples
+  uint32_t* leaf_cnt;          // per model slot * L (sample points per leaf)
+};
+void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches);
+
+// Exact learned pivots for items whose plan has decision candidate LEARNED:
+// list of plan indices; thread per (item, j < nb_pad).
+void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,
+                           const DModel* models, const Leaf* leaves, uint64_t* pivots, const RunParams& rp,
+                           cudaStream_t st);
+// Sample-bucket maximum under the RMI (imbalance test) for fit candidates.
+void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,
+                      cudaStream_t st, uint64_t* launches);
+// Alg. 5 decision for every fresh item; then splitter tables where needed.
+void launch_decide(const FreshArgs& f, const DModel* models, const RunParams& rp, cudaStream_t st);
+void launch_splitter_build(const FreshArgs& f, const uint64_t* samp, uint64_t* pivots, const RunParams& rp,
+                           cudaStream_t st);
+// Radix directory over every plan with cls == CLS_DIR (thread per cell).
+void launch_dir_build(Plan* plans, uint32_t nplans, uint32_t cells, const uint64_t* pivots, uint16_t* dirs,
+                      cudaStream_t st);
+
+// ---- forward / backward of the fit objective (ls_fit.cu)
+void launch_fit_grad(const DModel* model, const Leaf* leaves, const uint64_t* sample_bits, uint64_t S, int dt,
+                     double* pred, double* resid, double* grad_a, double* grad_b, double* grad_root,
+                     void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t fit_grad_scratch_bytes(uint64_t S, uint32_t L);
+
+// ---- partition passes (ls_partition.cu)
+struct PassArgs {
+  const Item* items;
+  Plan* plans;
+  uint32_t nitems;
+  uint64_t nchunks;
+  const uint64_t* keysA;
+  const uint64_t* keysB;
+  uint64_t* outA;
+  uint64_t* outB;
+  const uint64_t* pivots;
+  const uint16_t* dirs;
+  const DModel* models;
+  const Leaf* leaves;
+  unsigned long long* counts;   // per plan: nb counts
+  unsigned long long* cursors;  // per plan: nb bucket bases in the destination
+  uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
+  unsigned long long* incl;     // per chunk: inclusive prefixes | kReady (K3)
+  unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
+  unsigned int* status;         // device status word
+  int check_nan;
+  uint32_t nb_pad_max;
+  uint32_t dir_cells_max;
+};
+void launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st);
+void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
+
+struct ChildArgs {
+  const Item* items;
+  Plan* plans;
+  uint32_t nitems;
+  const uint64_t* pivots;
+  unsigned long long* counts;
+  unsigned long long* cursors;
+  Item* next;
+  uint64_t next_cap;
+  Span* base_small;
+  Span* base_large;
+  uint64_t base_cap;
+  uint64_t large_cap;
+  Span* copy;
+  uint64_t copy_cap;
+  Span* fallback;
+  uint64_t fallback_cap;
+  LevelCounters* ctr;
+  DevLevelStats* stats;
+};
+void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st);
+
+void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, int dt, cudaStream_t st);
+void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, int dt,
+                       cudaStream_t st);
+void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, cudaStream_t st);
+void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, int dt, cudaStream_t st);
+
+// ls_classify helpers
+void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,
+                            double Bg, uint32_t B, uint32_t* ids, unsigned long long* hist, cudaStream_t st);
+void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs, const uint64_t* keys,
+                           uint64_t n, int dt, uint32_t* ids, unsigned long long* hist, uint32_t nb_pad,
+                           uint32_t cells, cudaStream_t st);
+
+}  // namespace lsg

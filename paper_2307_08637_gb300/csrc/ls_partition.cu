@@ -1,0 +1,1060 @@
+// ls_partition.cu -- the partitioning side of learned SampleSort on GB300:
+//   K1  classify + per-item histogram (+ min/max for the homogeneity check of
+//       Sec. 2.2, + NaN check), shared-memory histograms with warp-aggregated
+//       atomics (__match_any_sync);
+//   K2  per item: exclusive scan of bucket counts, bucket write cursors,
+//       children (next level / base case / final), level statistics;
+//   K3  scatter: classify again, rank keys per bucket in shared memory, take
+//       each bucket's slice of the output with one atomic fetch-and-add per
+//       (tile, bucket) (the IPS4o parallelisation idea of Sec. 2.4), stage the
+//       tile bucket-by-bucket in shared memory and write contiguous runs;
+//   base case: warp-register bitonic sort (<= 256 keys) and shared-memory
+//       bitonic sort (<= 8192 keys); fallback merge sort past max_depth.
+#include <cstdio>
+
+#include "ls_kernels.h"
+
+namespace lsg {
+
+namespace {
+
+constexpr int kTPB = 256;
+constexpr int kKPT = 16;  // keys per thread per tile
+constexpr uint32_t kTile = kTPB * kKPT;
+static_assert(kTile == kTileKeys, "tile size shared with the host planner");
+constexpr uint32_t kCopyPiece = 65536;
+
+inline unsigned grid_for(uint64_t n, int tpb = kTPB) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// Plan index owning global chunk c (plans sorted by chunk_begin).
+__device__ __forceinline__ uint32_t find_plan(const Plan* __restrict__ plans, uint32_t n, uint64_t c) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (plans[mid].chunk_begin <= c) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Warp-aggregated shared-memory increment; returns the key's rank among the
+// keys of its bucket counted so far in this block.  b == ~0u is "no key".
+__device__ __forceinline__ uint32_t agg_inc(uint32_t* h, uint32_t b) {
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+  unsigned lane = threadIdx.x & 31;
+  int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader && b != 0xFFFFFFFFu) base = atomicAdd(&h[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+struct Cls {
+  uint64_t dir_lo, dir_hi;
+  double P, Bg;
+  uint32_t nb_pad, kmax, shift, B;
+  int32_t model;
+  uint8_t cls;
+};
+
+__device__ __forceinline__ uint32_t classify_key(uint64_t bits, const Cls& c, const uint64_t* sT, const uint16_t* sD,
+                                                 const DModel* models, const Leaf* leaves, int dt) {
+  if (c.cls == CLS_DIRECT) {
+    const DModel& m = models[c.model];
+    return refine_id(m, leaves + m.leaf_off, key_value(bits, dt), c.P, c.Bg, c.B);
+  }
+  uint64_t u = ord_of(bits, dt);
+  uint32_t b = (c.cls == CLS_DIR) ? pivot_count_dir(sT, sD, c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
+                                  : pivot_count(sT, c.nb_pad, u);
+  return b < c.kmax ? b : c.kmax;
+}
+
+// Load item pi's classifier into shared memory (all threads).
+__device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, uint16_t* sD) {
+  const Plan& pl = a.plans[pi];
+  c.cls = pl.cls;
+  c.nb_pad = pl.nb_pad;
+  c.kmax = pl.kmax;
+  c.dir_lo = pl.dir_lo;
+  c.dir_hi = pl.dir_hi;
+  c.shift = pl.dir_shift;
+  c.P = pl.P;
+  c.Bg = pl.Bg;
+  c.B = rp.B;
+  c.model = pl.model;
+  if (c.cls == CLS_DIRECT) {
+    c.kmax = rp.B - 1;
+    return;
+  }
+  const uint64_t* T = a.pivots + pl.tab_off;
+  for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) sT[j] = T[j];
+  if (c.cls == CLS_DIR) {
+    const uint16_t* D = a.dirs + pl.dir_off;
+    for (uint32_t j = threadIdx.x; j <= pl.dir_cells; j += blockDim.x) sD[j] = D[j];
+  }
+}
+
+// ------------------------------------------------------------------ K1
+
+// Classify every key of every chunk, histogram per chunk in shared memory;
+// write the chunk's bucket counts (dense row, used by K3's lookback), add
+// them to the item's totals, and track the item's min / max ord.
+__global__ void __launch_bounds__(kTPB) k_classify_hist(PassArgs a, RunParams rp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* sH = reinterpret_cast<uint32_t*>(sT + a.nb_pad_max);
+  uint16_t* sD = reinterpret_cast<uint16_t*>(sH + a.nb_pad_max);
+  for (uint32_t j = threadIdx.x; j < a.nb_pad_max; j += blockDim.x) sH[j] = 0;
+  uint32_t cur = 0xFFFFFFFFu;
+  Cls c;
+  bool nan = false;
+  for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+    uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    if (pi != cur) {
+      __syncthreads();
+      load_cls(a, rp, pi, c, sT, sD);
+      cur = pi;
+      __syncthreads();
+    }
+    const Item& it = a.items[pi];
+    const Plan& pl = a.plans[pi];
+    uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
+    uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
+    unsigned long long mn = ~0ull, mx = 0;
+    for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
+      uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+      uint64_t v[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        uint32_t idx = k * kTPB + threadIdx.x;
+        v[k] = idx < len ? src[t0 + idx] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        uint32_t idx = k * kTPB + threadIdx.x;
+        uint32_t b = 0xFFFFFFFFu;
+        if (idx < len) {
+          uint64_t bits = v[k];
+          if (a.check_nan && (bits & 0x7FF0000000000000ull) == 0x7FF0000000000000ull &&
+              (bits & 0x000FFFFFFFFFFFFFull))
+            nan = true;
+          uint64_t u = ord_of(bits, rp.dt);
+          mn = u < mn ? u : mn;
+          mx = u > mx ? u : mx;
+          b = classify_key(bits, c, sT, sD, a.models, a.leaves, rp.dt);
+        }
+        agg_inc(sH, b);
+      }
+    }
+    __syncthreads();
+    uint32_t* row = a.agg + ch * a.nb_pad_max;
+    for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) {
+      uint32_t h = sH[j];
+      row[j] = h;
+      if (h) {
+        atomicAdd(&a.counts[pl.cnt_off + j], (unsigned long long)h);
+        sH[j] = 0;
+      }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      unsigned long long o1 = __shfl_down_sync(0xFFFFFFFFu, mn, d);
+      unsigned long long o2 = __shfl_down_sync(0xFFFFFFFFu, mx, d);
+      mn = o1 < mn ? o1 : mn;
+      mx = o2 > mx ? o2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (mn != ~0ull) atomicMin(&a.plans[pi].minv, mn);
+      atomicMax(&a.plans[pi].maxv, mx);
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(nan ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_ENAN);
+}
+
+// ------------------------------------------------------------------ K3
+
+// Stable scatter.  Chunks are taken in order from a global counter.  A
+// chunk's per-bucket prefix (keys of the same bucket in earlier chunks of
+// the item) comes from a decoupled lookback over the chunk rows: a
+// predecessor's inclusive prefix if it has published one, else its K1
+// count -- K1 counts always exist, so the lookback never waits.  Inside a
+// chunk the tiles are processed in order; inside a tile each warp owns 512
+// consecutive keys and ranks them in order with warp-private counters, so
+// every key keeps its relative order within its bucket (the stable counting
+// sort of the partitioning step).
+__global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kWarps = kTPB / 32;
+  const uint32_t nbp = a.nb_pad_max;
+  uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* sRun = sT + nbp;                              // next destination per bucket
+  uint64_t* stage = sRun + nbp;                           // kTile keys
+  uint32_t* sLs = reinterpret_cast<uint32_t*>(stage + kTile);  // tile-local start per bucket
+  uint32_t* sCnt = sLs + nbp;                             // tile count per bucket
+  uint16_t* wcnt = reinterpret_cast<uint16_t*>(sCnt + nbp);  // [kWarps][nbp]
+  uint16_t* sid = wcnt + kWarps * nbp;                    // kTile bucket ids
+  uint16_t* sD = sid + kTile;
+  __shared__ uint32_t wsum[kWarps];
+  __shared__ unsigned long long s_chunk;
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint32_t j = threadIdx.x; j < kWarps * nbp; j += blockDim.x) wcnt[j] = 0;
+  uint32_t cur = 0xFFFFFFFFu;
+  Cls c;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_chunk = atomicAdd(a.chunk_ctr, 1ull);
+    __syncthreads();
+    uint64_t ch = s_chunk;
+    if (ch >= a.nchunks) break;
+    uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    const Plan& pl = a.plans[pi];
+    if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
+    if (pi != cur) {
+      load_cls(a, rp, pi, c, sT, sD);
+      cur = pi;
+    }
+    const Item& it = a.items[pi];
+    const uint32_t nbk = c.nb_pad;
+    // lookback: destination of this chunk's first key of each bucket
+    const uint64_t cfirst = pl.chunk_begin;
+    const uint32_t* aggrow = a.agg + ch * nbp;
+    for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
+      unsigned long long sum = 0;
+      for (uint64_t c2 = ch; c2-- > cfirst;) {
+        unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(&a.incl[c2 * nbp + b]);
+        if (v & kReady) {
+          sum += v & ~kReady;
+          break;
+        }
+        sum += a.agg[c2 * nbp + b];
+      }
+      a.incl[ch * nbp + b] = kReady | (sum + aggrow[b]);
+      sRun[b] = a.cursors[pl.cnt_off + b] + sum;
+    }
+    __threadfence();
+    __syncthreads();
+    uint64_t c0 = (ch - cfirst) * kChunkKeys;
+    uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
+    uint64_t* dst = it.buf ? a.outA : a.outB;
+    bool oob = false;
+    for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
+      uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+      uint64_t v[kKPT];
+      uint32_t bk[kKPT];
+      uint32_t rk[kKPT];
+      uint16_t* myc = wcnt + wid * nbp;
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        uint32_t pos = wid * (32 * kKPT) + k * 32 + lane;
+        v[k] = pos < len ? src[t0 + pos] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        uint32_t pos = wid * (32 * kKPT) + k * 32 + lane;
+        uint32_t b = pos < len ? classify_key(v[k], c, sT, sD, a.models, a.leaves, rp.dt) : 0xFFFFFFFFu;
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if ((int)lane == leader && b != 0xFFFFFFFFu) {
+          old = myc[b];
+          myc[b] = (uint16_t)(old + __popc(peers));
+        }
+        old = __shfl_sync(0xFFFFFFFFu, old, leader);
+        rk[k] = old + __popc(peers & ((1u << lane) - 1u));
+        bk[k] = b;
+        __syncwarp();
+      }
+      __syncthreads();
+      // per bucket: exclusive prefix over warps (in place) and tile count
+      for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          uint32_t x = wcnt[w * nbp + b];
+          wcnt[w * nbp + b] = (uint16_t)t;
+          t += x;
+        }
+        sCnt[b] = t;
+      }
+      __syncthreads();
+      // exclusive scan of tile counts over buckets -> tile-local starts
+      uint32_t per = (nbk + kTPB - 1) / kTPB;
+      uint32_t j0 = threadIdx.x * per;
+      uint32_t loc = 0;
+      for (uint32_t j = j0; j < j0 + per && j < nbk; ++j) loc += sCnt[j];
+      uint32_t incl = loc;
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= (unsigned)d) incl += o;
+      }
+      if (lane == 31) wsum[wid] = incl;
+      __syncthreads();
+      if (wid == 0) {
+        uint32_t w = lane < (unsigned)kWarps ? wsum[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+          uint32_t o = __shfl_up_sync(0xFFFFFFFFu, w, d);
+          if (lane >= (unsigned)d) w += o;
+        }
+        if (lane < (unsigned)kWarps) wsum[lane] = w;
+      }
+      __syncthreads();
+      uint32_t run = incl - loc + (wid > 0 ? wsum[wid - 1] : 0);
+      for (uint32_t j = j0; j < j0 + per && j < nbk; ++j) {
+        sLs[j] = run;
+        run += sCnt[j];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        if (bk[k] != 0xFFFFFFFFu) {
+          uint32_t p = sLs[bk[k]] + myc[bk[k]] + rk[k];
+          stage[p] = v[k];
+          sid[p] = (uint16_t)bk[k];
+        }
+      }
+      __syncthreads();
+      for (uint32_t p = threadIdx.x; p < len; p += kTPB) {
+        uint32_t b = sid[p];
+        uint64_t o = sRun[b] + (p - sLs[b]);
+        if (o >= it.lo && o < it.lo + it.n) dst[o] = stage[p];
+        else oob = true;  // K1 and K3 disagree: never write outside the item
+      }
+      __syncthreads();
+      for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
+        sRun[b] += sCnt[b];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) wcnt[w * nbp + b] = 0;
+      }
+    }
+    if (oob) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
+  }
+}
+
+// ------------------------------------------------------------------ K2
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim 1024).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* wtmp, uint32_t* total) {
+  unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = x;
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl += o;
+  }
+  __syncthreads();
+  if (lane == 31) wtmp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? wtmp[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t o = __shfl_up_sync(0xFFFFFFFFu, w, d);
+      if (lane >= (unsigned)d) w += o;
+    }
+    if (lane < nw) wtmp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t r = incl - x + (wid > 0 ? wtmp[wid - 1] : 0);
+  if (total) *total = wtmp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* tmp) {
+  for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, d);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = x;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (threadIdx.x == 0)
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) r += tmp[w];
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* tmp) {
+  for (int d = 16; d > 0; d >>= 1) {
+    unsigned long long o = __shfl_down_sync(0xFFFFFFFFu, x, d);
+    x = o > x ? o : x;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = x;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (threadIdx.x == 0)
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) r = tmp[w] > r ? tmp[w] : r;
+  __syncthreads();
+  return r;
+}
+
+enum { L_NEXT = 0, L_SMALL, L_LARGE, L_COPY, L_FALLBACK, L_N };
+
+__global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
+  uint32_t pi = blockIdx.x;
+  const Item& it = a.items[pi];
+  Plan& pl = a.plans[pi];
+  __shared__ uint32_t wtmp[32];
+  __shared__ unsigned long long ltmp[32];
+  __shared__ unsigned long long s_base[L_N];
+  __shared__ int s_noprog;
+  __shared__ uint32_t s_tot;
+  uint32_t level = it.level;
+  uint32_t cl = level + 1 < LS_MAX_LEVELS ? level + 1 : LS_MAX_LEVELS - 1;
+  DevLevelStats* ls = a.stats + (level < LS_MAX_LEVELS ? level : LS_MAX_LEVELS - 1);
+  DevLevelStats* cs = a.stats + cl;
+  uint8_t dest = it.buf ^ 1;
+  // Homogeneity check (Sec. 2.2): an all-equal item is already sorted.
+  if (pl.minv == pl.maxv) {
+    if (threadIdx.x == 0) {
+      pl.flags |= FLAG_SKIP_SCATTER | FLAG_HOMOGENEOUS;
+      atomicAdd(&ls->homogeneous, 1ull);
+      if (it.buf == 1) {
+        uint64_t np = (it.n + kCopyPiece - 1) / kCopyPiece;
+        unsigned long long b = atomicAdd(&a.ctr->n_copy, (unsigned long long)np);
+        if (b + np > a.copy_cap) {
+          atomicExch(&a.ctr->overflow, 1ull);
+        } else {
+          for (uint64_t q = 0; q < np; ++q) {
+            uint64_t off = q * kCopyPiece;
+            uint64_t len = it.n - off < kCopyPiece ? it.n - off : kCopyPiece;
+            a.copy[b + q] = Span{it.lo + off, (uint32_t)len, 1u};
+          }
+        }
+      }
+    }
+    return;
+  }
+  uint32_t nb = pl.nb;
+  const unsigned long long* cnt = a.counts + pl.cnt_off;
+  bool eq = pl.decision == LS_DEC_SPLITTER_EQ;
+  bool learned = pl.decision == LS_DEC_LEARNED;
+  const uint64_t* T = a.pivots + pl.tab_off;
+  bool has_T = pl.cls != CLS_DIRECT;
+  uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+  uint32_t b0 = threadIdx.x * per;
+  uint32_t b1 = b0 + per < nb ? b0 + per : nb;
+  // exclusive scan of counts -> bucket starts (uint32 is enough per item up
+  // to 2^32 keys; items are smaller than that on one GPU)
+  uint64_t locsum = 0;
+  for (uint32_t b = b0; b < b1; ++b) locsum += cnt[b];
+  if (threadIdx.x == 0) s_noprog = 0;
+  uint32_t excl32 = block_excl_scan((uint32_t)locsum, wtmp, &s_tot);
+  uint64_t run = excl32;
+  unsigned long long mxc = 0, sq = 0, eqk = 0, bk = 0, bki = 0, fbk = 0, fbi = 0;
+  uint32_t nl[L_N] = {0, 0, 0, 0, 0};
+  for (uint32_t b = b0; b < b1; ++b) {
+    uint64_t sz = cnt[b];
+    mxc = sz > mxc ? sz : mxc;
+    sq += sz * sz;
+    if (sz == it.n && !(eq && (b & 1))) s_noprog = 1;
+  }
+  __syncthreads();
+  bool noprog = s_noprog != 0;
+  // level statistics of this item
+  unsigned long long tmax = block_max_u64(mxc, ltmp);
+  unsigned long long tsq = block_sum_u64(sq, ltmp);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ls->items, 1ull);
+    atomicAdd(&ls->keys, (unsigned long long)it.n);
+    if (learned) atomicAdd(&ls->learned, 1ull);
+    else if (eq) atomicAdd(&ls->splitter_eq, 1ull);
+    else atomicAdd(&ls->splitter, 1ull);
+    atomicMax(&ls->max_child, tmax);
+    atomicAdd(&ls->sumsq_child, tsq);
+  }
+  if (noprog) {
+    // no-progress guard: redo the same range at the next level with the
+    // splitter tree (keys stay where they are).
+    if (threadIdx.x == 0) {
+      pl.flags |= FLAG_SKIP_SCATTER | FLAG_NOPROGRESS;
+      atomicAdd(&ls->noprogress, 1ull);
+      uint32_t bb = 0;
+      for (uint32_t b = 0; b < nb; ++b)
+        if (cnt[b] == it.n) bb = b;
+      if (level + 1 > rp.max_depth) {
+        atomicAdd(&cs->fallback_items, 1ull);
+        atomicAdd(&cs->fallback_keys, (unsigned long long)it.n);
+        unsigned long long q = atomicAdd(&a.ctr->n_fallback, 1ull);
+        if (q < a.fallback_cap) a.fallback[q] = Span{it.lo, (uint32_t)it.n, it.buf};
+        else atomicExch(&a.ctr->overflow, 1ull);
+      } else {
+        Item ch = it;
+        ch.level = (uint16_t)(level + 1);
+        ch.gidx = it.gidx * nb + bb;
+        ch.kind = KIND_FORCE_SPLITTER;
+        ch.model = -1;
+        ch.mk = 0;
+        ch.mg = 0;
+        if (has_T) {
+          if (bb >= 1) ch.ord_lo = T[bb] > it.ord_lo ? T[bb] : it.ord_lo;
+          if (bb < pl.kmax) ch.ord_hi = T[bb + 1] - 1;
+        }
+        unsigned long long q = atomicAdd(&a.ctr->n_next, 1ull);
+        if (q < a.next_cap) a.next[q] = ch;
+        else atomicExch(&a.ctr->overflow, 1ull);
+      }
+    }
+    return;
+  }
+  // write cursors: absolute positions in the destination buffer
+  {
+    uint64_t r = run;
+    for (uint32_t b = b0; b < b1; ++b) {
+      a.cursors[pl.cnt_off + b] = it.lo + r;
+      r += cnt[b];
+    }
+  }
+  // classify children and count list entries
+  for (uint32_t b = b0; b < b1; ++b) {
+    uint64_t sz = cnt[b];
+    if (eq && (b & 1)) {
+      eqk += sz;
+      if (sz && dest == 1) nl[L_COPY] += (uint32_t)((sz + kCopyPiece - 1) / kCopyPiece);
+      continue;
+    }
+    if (sz == 0) continue;
+    if (sz == 1) {
+      if (dest == 1) nl[L_COPY] += 1;
+      continue;
+    }
+    if (sz <= rp.T) {
+      if (sz <= kWarpSortMax) nl[L_SMALL]++;
+      else nl[L_LARGE]++;
+      bki++;
+      bk += sz;
+    } else if (level + 1 > rp.max_depth) {
+      nl[L_FALLBACK]++;
+      fbi++;
+      fbk += sz;
+    } else {
+      nl[L_NEXT]++;
+    }
+  }
+  uint32_t pos[L_N];
+  for (int q = 0; q < L_N; ++q) {
+    uint32_t tot;
+    pos[q] = block_excl_scan(nl[q], wtmp, &tot);
+    if (threadIdx.x == 0) {
+      unsigned long long* ctr = (q == L_NEXT)    ? &a.ctr->n_next
+                                : (q == L_SMALL) ? &a.ctr->n_base_small
+                                : (q == L_LARGE) ? &a.ctr->n_base_large
+                                : (q == L_COPY)  ? &a.ctr->n_copy
+                                                 : &a.ctr->n_fallback;
+      s_base[q] = tot ? atomicAdd(ctr, (unsigned long long)tot) : 0ull;
+    }
+  }
+  unsigned long long s_eqk = block_sum_u64(eqk, ltmp);
+  unsigned long long s_bk = block_sum_u64(bk, ltmp);
+  unsigned long long s_bki = block_sum_u64(bki, ltmp);
+  unsigned long long s_fbk = block_sum_u64(fbk, ltmp);
+  unsigned long long s_fbi = block_sum_u64(fbi, ltmp);
+  if (threadIdx.x == 0) {
+    if (s_eqk) atomicAdd(&ls->eq_keys, s_eqk);
+    if (s_bki) {
+      atomicAdd(&cs->base_items, s_bki);
+      atomicAdd(&cs->base_keys, s_bk);
+    }
+    if (s_fbi) {
+      atomicAdd(&cs->fallback_items, s_fbi);
+      atomicAdd(&cs->fallback_keys, s_fbk);
+    }
+  }
+  __syncthreads();
+  unsigned long long wp[L_N];
+  for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + pos[q];
+  const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.large_cap, a.copy_cap, a.fallback_cap};
+  bool ovf = false;
+  uint64_t r = run;
+  uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
+  uint64_t mg = (it.kind == KIND_REFINE) ? it.mg : 0;
+  for (uint32_t b = b0; b < b1; ++b) {
+    uint64_t sz = cnt[b];
+    uint64_t clo = it.lo + r;
+    r += sz;
+    if (eq && (b & 1)) {
+      if (sz && dest == 1) {
+        for (uint64_t off = 0; off < sz; off += kCopyPiece) {
+          uint64_t len = sz - off < kCopyPiece ? sz - off : kCopyPiece;
+          if (wp[L_COPY] < caps[L_COPY]) a.copy[wp[L_COPY]] = Span{clo + off, (uint32_t)len, 1u};
+          else ovf = true;
+          wp[L_COPY]++;
+        }
+      }
+      continue;
+    }
+    if (sz == 0) continue;
+    if (sz == 1) {
+      if (dest == 1) {
+        if (wp[L_COPY] < caps[L_COPY]) a.copy[wp[L_COPY]] = Span{clo, 1u, 1u};
+        else ovf = true;
+        wp[L_COPY]++;
+      }
+      continue;
+    }
+    if (sz <= rp.T) {
+      int q = sz <= kWarpSortMax ? L_SMALL : L_LARGE;
+      Span* lst = q == L_SMALL ? a.base_small : a.base_large;
+      if (wp[q] < caps[q]) lst[wp[q]] = Span{clo, (uint32_t)sz, dest};
+      else ovf = true;
+      wp[q]++;
+    } else if (level + 1 > rp.max_depth) {
+      if (wp[L_FALLBACK] < caps[L_FALLBACK]) a.fallback[wp[L_FALLBACK]] = Span{clo, (uint32_t)sz, dest};
+      else ovf = true;
+      wp[L_FALLBACK]++;
+    } else {
+      Item ch;
+      ch.lo = clo;
+      ch.n = sz;
+      ch.gidx = it.gidx * nb + b;
+      ch.segment = it.segment;
+      ch.level = (uint16_t)(level + 1);
+      ch.buf = dest;
+      ch.pad = 0;
+      ch.ord_lo = it.ord_lo;
+      ch.ord_hi = it.ord_hi;
+      if (has_T) {
+        if (b >= 1) ch.ord_lo = T[b] > it.ord_lo ? T[b] : it.ord_lo;
+        if (b < pl.kmax) ch.ord_hi = T[b + 1] - 1;
+      }
+      if (learned && rp.recurse == LS_RECURSE_REFINE_GLOBAL) {
+        ch.kind = KIND_REFINE;
+        ch.model = pl.model;
+        ch.mk = (uint16_t)(mk + 1);
+        ch.mg = mg * rp.B + b;
+      } else {
+        ch.kind = KIND_FRESH;
+        ch.model = -1;
+        ch.mk = 0;
+        ch.mg = 0;
+      }
+      if (wp[L_NEXT] < caps[L_NEXT]) a.next[wp[L_NEXT]] = ch;
+      else ovf = true;
+      wp[L_NEXT]++;
+    }
+  }
+  if (ovf) atomicExch(&a.ctr->overflow, 1ull);
+}
+
+// ------------------------------------------------------------- base case
+
+// Warp bitonic sort of up to 32*E keys held E per lane (element index
+// lane*E + r); padding is ~0 (largest ord).
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[E]) {
+  const unsigned lane = threadIdx.x & 31;
+  constexpr uint32_t P = 32 * E;
+#pragma unroll
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= (uint32_t)E) {
+        const int lm = (int)(j / E);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          uint32_t i = lane * E + r;
+          uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v[r], lm);
+          bool up = (i & k) == 0;
+          bool lower = (i & j) == 0;
+          uint64_t mn = v[r] < o ? v[r] : o;
+          uint64_t mx = v[r] < o ? o : v[r];
+          v[r] = (lower == up) ? mn : mx;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if ((r & (int)j) == 0) {
+            uint32_t i = lane * E + r;
+            bool up = (i & k) == 0;
+            uint64_t x = v[r], y = v[r ^ j];
+            if ((x > y) == up) {
+              v[r] = y;
+              v[r ^ j] = x;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_span(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t* src = s.buf ? Bbuf : A;
+  uint64_t v[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    uint32_t i = lane * E + r;
+    v[r] = i < s.n ? ord_of(src[s.lo + i], dt) : ~0ull;
+  }
+  warp_bitonic<E>(v);
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    uint32_t i = lane * E + r;
+    if (i < s.n) A[s.lo + i] = unord(v[r], dt);
+  }
+}
+
+__global__ void __launch_bounds__(kTPB) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
+                                                     int dt) {
+  uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
+  for (; w < n; w += nw) {
+    Span s = spans[w];
+    if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
+    else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
+    else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
+    else warp_sort_span<8>(s, A, Bbuf, dt);
+  }
+}
+
+__device__ void block_bitonic_smem(uint64_t* sm, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          uint64_t x = sm[i], y = sm[ixj];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            sm[i] = y;
+            sm[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_base_large(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
+                                                     int dt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    Span s = spans[w];
+    const uint64_t* src = s.buf ? Bbuf : A;
+    uint32_t P = 2;
+    while (P < s.n) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sm[i] = i < s.n ? ord_of(src[s.lo + i], dt) : ~0ull;
+    __syncthreads();
+    block_bitonic_smem(sm, P);
+    for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) A[s.lo + i] = unord(sm[i], dt);
+    __syncthreads();
+  }
+}
+
+__global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf) {
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    Span s = spans[w];
+    for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) A[s.lo + i] = Bbuf[s.lo + i];
+  }
+}
+
+// Fallback for spans past max_depth: one block merge-sorts the span through
+// the other buffer (bitonic runs of 2048 in shared memory, then merge-path
+// passes), leaving the result in A.
+__global__ void __launch_bounds__(1024) k_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
+                                                   int dt) {
+  __shared__ uint64_t sm[kSortChunk];
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    Span s = spans[w];
+    uint64_t* src = s.buf ? Bbuf : A;
+    uint64_t* oth = s.buf ? A : Bbuf;
+    // runs of 2048 sorted by ord, written to `oth`
+    for (uint64_t r0 = 0; r0 < s.n; r0 += kSortChunk) {
+      uint32_t len = (uint32_t)(s.n - r0 < kSortChunk ? s.n - r0 : kSortChunk);
+      for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x)
+        sm[i] = i < len ? ord_of(src[s.lo + r0 + i], dt) : ~0ull;
+      __syncthreads();
+      block_bitonic_smem(sm, kSortChunk);
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) oth[s.lo + r0 + i] = sm[i];
+      __syncthreads();
+    }
+    uint64_t* cur = oth;
+    uint64_t* nxt = src;
+    for (uint64_t wd = kSortChunk; wd < s.n; wd *= 2) {
+      for (uint64_t o = (uint64_t)threadIdx.x * 8; o < s.n; o += (uint64_t)blockDim.x * 8) {
+        uint64_t a0 = (o / (2 * wd)) * (2 * wd);
+        uint64_t a1 = a0 + wd < s.n ? a0 + wd : s.n;
+        uint64_t b1 = a0 + 2 * wd < s.n ? a0 + 2 * wd : s.n;
+        uint64_t na = a1 - a0, nbb = b1 - a1;
+        const uint64_t* X = cur + s.lo + a0;
+        const uint64_t* Y = cur + s.lo + a1;
+        uint64_t diag = o - a0;
+        uint64_t lo = diag > nbb ? diag - nbb : 0, hi = diag < na ? diag : na;
+        while (lo < hi) {
+          uint64_t mid = (lo + hi) >> 1;
+          if (X[mid] <= Y[diag - 1 - mid]) lo = mid + 1;
+          else hi = mid;
+        }
+        uint64_t i = lo, j = diag - lo;
+        uint64_t lim = b1 - o < 8 ? b1 - o : 8;
+        for (uint64_t k = 0; k < lim; ++k) {
+          bool takeX = (j >= nbb) || (i < na && X[i] <= Y[j]);
+          nxt[s.lo + o + k] = takeX ? X[i++] : Y[j++];
+        }
+      }
+      __syncthreads();
+      uint64_t* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    // cur holds ord values; write keys to A
+    for (uint64_t i = threadIdx.x; i < s.n; i += blockDim.x) A[s.lo + i] = unord(cur[s.lo + i], dt);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------- ls_classify kernels
+
+__global__ void k_direct_classify(const DModel* mp, const Leaf* leaves, const uint64_t* __restrict__ keys, uint64_t n,
+                                  int dt, double P, double Bg, uint32_t B, uint32_t* ids,
+                                  unsigned long long* hist) {
+  DModel m = *mp;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t b = refine_id(m, leaves + m.leaf_off, key_value(keys[i], dt), P, Bg, B);
+    if (ids) ids[i] = b;
+    if (hist) atomicAdd(&hist[b], 1ull);
+  }
+}
+
+__global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs,
+                                 const uint64_t* __restrict__ keys, uint64_t n, int dt, uint32_t* ids,
+                                 unsigned long long* hist, uint32_t nb_pad, uint32_t cells) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* sH = reinterpret_cast<uint32_t*>(sT + nb_pad);
+  uint16_t* sD = reinterpret_cast<uint16_t*>(sH + nb_pad);
+  Plan pl = *plan;
+  for (uint32_t j = threadIdx.x; j < nb_pad; j += blockDim.x) {
+    sT[j] = pivots[pl.tab_off + j];
+    sH[j] = 0;
+  }
+  if (pl.cls == CLS_DIR)
+    for (uint32_t j = threadIdx.x; j <= cells; j += blockDim.x) sD[j] = dirs[pl.dir_off + j];
+  __syncthreads();
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t nround = (n + stride - 1) / stride;
+  for (uint64_t rd = 0; rd < nround; ++rd) {
+    uint64_t i = rd * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint32_t b = 0xFFFFFFFFu;
+    if (i < n) {
+      uint64_t u = ord_of(keys[i], dt);
+      b = (pl.cls == CLS_DIR) ? pivot_count_dir(sT, sD, pl.dir_lo, pl.dir_hi, pl.dir_shift, pl.kmax, u)
+                              : pivot_count(sT, nb_pad, u);
+      b = b < pl.kmax ? b : pl.kmax;
+      if (ids) ids[i] = b;
+    }
+    agg_inc(sH, b);
+  }
+  __syncthreads();
+  if (hist)
+    for (uint32_t j = threadIdx.x; j < nb_pad; j += blockDim.x)
+      if (sH[j]) atomicAdd(&hist[j], (unsigned long long)sH[j]);
+}
+
+// ------------------------------------------------------------------ scan
+
+__global__ void k_scan_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, size_t n,
+                             uint64_t* __restrict__ bsum) {
+  __shared__ uint64_t w[32];
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  uint64_t x = i < n ? in[i] : 0;
+  unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t incl = x;
+  for (int d = 1; d < 32; d <<= 1) {
+    uint64_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl += o;
+  }
+  if (lane == 31) w[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t v = lane < (blockDim.x >> 5) ? w[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      uint64_t o = __shfl_up_sync(0xFFFFFFFFu, v, d);
+      if (lane >= (unsigned)d) v += o;
+    }
+    w[lane] = v;
+  }
+  __syncthreads();
+  uint64_t excl = incl - x + (wid > 0 ? w[wid - 1] : 0);
+  if (i < n) out[i] = excl;
+  if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = w[(blockDim.x >> 5) - 1];
+}
+
+__global__ void k_scan_add(uint64_t* __restrict__ out, size_t n, const uint64_t* __restrict__ boff) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+__global__ void k_scan_total(uint64_t* out, size_t n, const uint64_t* in) {
+  // out[n] = out[n-1] + in[n-1]
+  if (n == 0) out[0] = 0;
+  else out[n] = out[n - 1] + in[n - 1];
+}
+
+__global__ void k_fill_u64(uint64_t* p, uint64_t v, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+constexpr int kScanTPB = 1024;
+
+}  // namespace
+
+// ===================================================== host launchers
+
+size_t scan_tmp_elems(size_t n) {
+  size_t t = 0;
+  while (n > 1) {
+    n = (n + kScanTPB - 1) / kScanTPB;
+    t += 2 * n + 2;
+  }
+  return t + 4;
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n) (out[n] = total).
+void launch_scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, uint64_t* tmp, size_t tmp_elems,
+                               cudaStream_t st) {
+  (void)tmp_elems;
+  if (n == 0) {
+    k_scan_total<<<1, 1, 0, st>>>(out, 0, in);
+    return;
+  }
+  size_t nb = (n + kScanTPB - 1) / kScanTPB;
+  uint64_t* bsum = tmp;
+  uint64_t* boff = tmp + nb + 1;
+  k_scan_block<<<(unsigned)nb, kScanTPB, 0, st>>>(in, out, n, bsum);
+  if (nb > 1) {
+    launch_scan_exclusive_u64(bsum, boff, nb, tmp + 2 * nb + 2, 0, st);
+    k_scan_add<<<(unsigned)nb, kScanTPB, 0, st>>>(out, n, boff);
+  }
+  k_scan_total<<<1, 1, 0, st>>>(out, n, in);
+}
+
+void launch_fill_u64(uint64_t* p, uint64_t v, size_t n, cudaStream_t st) {
+  if (n) k_fill_u64<<<grid_for(n), kTPB, 0, st>>>(p, v, n);
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+static size_t k1_smem(const PassArgs& a) {
+  return a.nb_pad_max * (8 + 4) + (a.dir_cells_max + 1) * 2 + 16;
+}
+static size_t k3_smem(const PassArgs& a) {
+  return a.nb_pad_max * (8 + 8 + 4 + 4 + 2 * (kTPB / 32)) + kTile * (8 + 2) + (a.dir_cells_max + 1) * 2 + 16;
+}
+
+void launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (!a.nchunks) return;
+  size_t sm = k1_smem(a);
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_classify_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_classify_hist, kTPB, sm);
+  if (per < 1) per = 1;
+  uint64_t grid = (uint64_t)sm_count() * per;
+  if (grid > a.nchunks) grid = a.nchunks;
+  k_classify_hist<<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+}
+
+void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (!a.nchunks) return;
+  size_t sm = k3_smem(a);
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter, kTPB, sm);
+  if (per < 1) per = 1;
+  uint64_t grid = (uint64_t)sm_count() * per;
+  if (grid > a.nchunks) grid = a.nchunks;
+  cudaMemsetAsync(a.chunk_ctr, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(a.incl, 0, a.nchunks * a.nb_pad_max * sizeof(unsigned long long), st);
+  k_scatter<<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+}
+
+void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (!a.nitems) return;
+  k_children<<<a.nitems, 1024, 0, st>>>(a, rp);
+}
+
+void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, int dt, cudaStream_t st) {
+  if (!n) return;
+  uint64_t warps = n;
+  uint64_t blocks = (warps * 32 + kTPB - 1) / kTPB;
+  uint64_t cap = (uint64_t)sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  k_base_small<<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, dt);
+}
+
+void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, int dt,
+                       cudaStream_t st) {
+  if (!n) return;
+  uint32_t P = 2;
+  while (P < max_len) P <<= 1;
+  size_t sm = (size_t)P * 8;
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_base_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
+  uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
+  k_base_large<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, dt);
+}
+
+void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, cudaStream_t st) {
+  if (!n) return;
+  uint64_t grid = n < (uint64_t)sm_count() * 16 ? n : (uint64_t)sm_count() * 16;
+  k_copy_spans<<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf);
+}
+
+void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, int dt, cudaStream_t st) {
+  if (!n) return;
+  uint64_t grid = n < (uint64_t)sm_count() * 2 ? n : (uint64_t)sm_count() * 2;
+  k_fallback<<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, dt);
+}
+
+void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,
+                            double Bg, uint32_t B, uint32_t* ids, unsigned long long* hist, cudaStream_t st) {
+  if (!n) return;
+  uint64_t grid = grid_for(n);
+  uint64_t cap = (uint64_t)sm_count() * 8;
+  if (grid > cap) grid = cap;
+  k_direct_classify<<<(unsigned)grid, kTPB, 0, st>>>(m, leaves, keys, n, dt, P, Bg, B, ids, hist);
+}
+
+void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs, const uint64_t* keys,
+                           uint64_t n, int dt, uint32_t* ids, unsigned long long* hist, uint32_t nb_pad,
+                           uint32_t cells, cudaStream_t st) {
+  if (!n) return;
+  size_t sm = (size_t)nb_pad * 12 + (cells + 1) * 2 + 16;
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_table_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  uint64_t grid = grid_for(n);
+  uint64_t cap = (uint64_t)sm_count() * 4;
+  if (grid > cap) grid = cap;
+  k_table_classify<<<(unsigned)grid, kTPB, sm, st>>>(plan, pivots, dirs, keys, n, dt, ids, hist, nb_pad, cells);
+}
+
+}  // namespace lsg
