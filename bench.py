@@ -1,0 +1,378 @@
+"""Benchmark: full sorts of 1e8 float64 keys on one GB300, learned vs splitter.
+
+A step sorts six 1e8-key float64 arrays, one per synthetic distribution of
+the paper's suite (normal, lognormal, exponential, chi-squared, mixture of 5
+Gaussians, uniform on [0, 1e6)), each through ls_sort on the device, with the
+partitioner Alg. 5 picks (the RMI for all six).  The same arrays are then
+sorted with the splitter tree forced, on the same kernels.  Every sort
+starts from the unsorted input: a device-to-device restore copy runs before
+each sort, outside its CUDA-event pair.  The inputs (800 MB each) are larger
+than L2 (129 MB), so no flush is needed.
+
+Printed on rank 0: one JSON line (metric keys/s).  `--impl reference` times
+the CPU oracle instead (single thread, bounded samples).  Under torchrun every
+rank sorts its own six arrays (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+METRIC = "keys/s and % HBM roofline at 1e8 f64 keys, learned vs splitter partition, 1 GB300"
+DISTS = datagen.F64_DISTS
+FALLBACK_HBM_GBS = 6800.0
+SCATTER_BYTES_PER_KEY = 16  # K3 reads each key once and writes it once
+CLASSIFY_BYTES_PER_KEY = 8  # K1 reads each key once
+BASECASE_T = 256            # buckets of <= 256 keys go to the warp-register base case
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=float, default=1e8)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-splitter", action="store_true")
+    ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per key of the scatter kernel from the committed ncu summary,
+    only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "scatter_traffic.json")
+    src = os.path.join(ROOT, "paper_2307_08637_gb300", "csrc", "ls_partition.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("source_sha256") != sha:
+            return None
+        return float(d["dram_bytes_per_key"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{dev}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gen_inputs(n: int, seed: int, dists=DISTS):
+    return [(d, datagen.generate(d, n, seed)) for d in dists]
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    n = int(args.n)
+    sample_n = min(n, 10_000_000)
+    inputs = gen_inputs(sample_n, args.seed)
+    p = oracle.params()
+    times = []
+    for step in range(args.warmup + args.steps):
+        d, x = inputs[step % len(inputs)]
+        t0 = time.perf_counter()
+        out, rc, tr, _, _ = oracle.sort(x, p)
+        dt = time.perf_counter() - t0
+        assert rc == 0
+        if step >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample_n * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C2 sample: 1e7-key prefix of each 1e8 float64 distribution, one per step",
+                   "distributions": list(DISTS), "keys_per_step": sample_n},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_n} keys per step, distributions cycled"},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_sorts(lsg, ctx, work, pristine, p, torch, stream):
+    """Sort every array once from its pristine copy; returns (ms list, stats list)."""
+    ms, sts = [], []
+    for w, src in zip(work, pristine):
+        w.copy_(src)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = lsg.ls_sort(ctx, w, p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        sts.append(st)
+    return ms, sts
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    import paper_2307_08637_gb300 as lsg
+
+    n = int(args.n)
+    stream = torch.cuda.current_stream()
+    ctx = lsg.Context(dev)
+    dists = tuple(d for d in args.dists.split(",") if d)
+    inputs = gen_inputs(n, args.seed + 1000 * rank, dists)
+    pristine = [torch.from_numpy(x).to(f"cuda:{dev}") for _, x in inputs]
+    work = [torch.empty_like(t) for t in pristine]
+    p_learned = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, basecase_threshold=BASECASE_T)
+    p_split = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, partitioner=lsg.LS_PART_SPLITTER,
+                                    basecase_threshold=BASECASE_T)
+    ctx.workspace(n, 1, lsg.LS_F64, p_split)  # allocate once, before timing
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        time_sorts(lsg, ctx, work, pristine, p_learned, torch, stream)
+    barrier()
+    ms_learned, sts_learned = [], []
+    with Clocks(dev) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            ms, sts = time_sorts(lsg, ctx, work, pristine, p_learned, torch, stream)
+            ms_learned.append(sum(ms))
+            sts_learned += sts
+        barrier()
+        wall = time.perf_counter() - wall0
+    # correctness guard on the last sorted array of the timed region
+    last = work[-1]
+    sord = last.view(torch.int64)
+    sord = sord ^ ((sord >> 63) & 0x7FFFFFFFFFFFFFFF)
+    assert bool((sord[1:] >= sord[:-1]).all()), "bench output not sorted"
+    step_ms = sum(ms_learned) / len(ms_learned)
+    if world > 1:
+        t = torch.tensor([step_ms], device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    keys_per_step = n * len(inputs)
+    value = world * keys_per_step / (step_ms / 1e3)
+
+    # per-pass device time (all timed learned sorts)
+    passes = {}
+    for st in sts_learned:
+        for k, v in st.passes().items():
+            a = passes.setdefault(k, {"ms": 0.0, "launches": 0, "keys": 0})
+            a["ms"] += v["ms"]
+            a["launches"] += v["launches"]
+            a["keys"] += v["keys"]
+    peak, peak_kind = measured_peak()
+    sc = passes["scatter"]
+    achieved = SCATTER_BYTES_PER_KEY * sc["keys"] / (sc["ms"] / 1e3) / 1e9 if sc["ms"] > 0 else None
+    k1 = passes["classify"]
+    k1_gbs = CLASSIFY_BYTES_PER_KEY * k1["keys"] / (k1["ms"] / 1e3) / 1e9 if k1["ms"] > 0 else None
+    tr = ncu_traffic()
+    roofline = {
+        "kernel": "k_scatter (K3 stable partition scatter)",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+        "bytes_per_key": SCATTER_BYTES_PER_KEY,
+        "keys_per_launch": sc["keys"] / max(sc["launches"], 1),
+        "traffic": (tr * sc["keys"] / max(sc["launches"], 1)) if tr else None,
+        "frac_of_8TBps": achieved / 8000.0 if achieved else None,
+        "classify_k1_gbs": k1_gbs, "classify_k1_frac": (k1_gbs / peak) if k1_gbs else None,
+    }
+    # per-distribution details of the timed learned sorts
+    per_dist = {}
+    for i, (d, _) in enumerate(inputs):
+        tms = [st.ms_total for st in sts_learned[i::len(inputs)]]
+        per_dist[d] = {"host_ms_mean": sum(tms) / len(tms), "root_decision": int(sts_learned[i].root_decision),
+                       "levels": int(sts_learned[i].levels_used),
+                       "level1_max_bucket": int(sts_learned[i].level[0].max_child),
+                       "level1_bucket_sumsq": int(sts_learned[i].level[0].sumsq_child)}
+
+    split = None
+    if not args.no_splitter:
+        ms_s, sts_s = [], []
+        for _ in range(max(1, args.steps // 2)):
+            ms, sts = time_sorts(lsg, ctx, work, pristine, p_split, torch, stream)
+            ms_s.append(sum(ms))
+            sts_s += sts
+        s_ms = sum(ms_s) / len(ms_s)
+        ps = {}
+        for st in sts_s:
+            for k, v in st.passes().items():
+                a = ps.setdefault(k, {"ms": 0.0, "keys": 0})
+                a["ms"] += v["ms"]
+                a["keys"] += v["keys"]
+        split = {"value": world * keys_per_step / (s_ms / 1e3), "unit": "keys/s", "ms_per_step": s_ms,
+                 "learned_speedup": s_ms / step_ms,
+                 "scatter_gbs": SCATTER_BYTES_PER_KEY * ps["scatter"]["keys"] / (ps["scatter"]["ms"] / 1e3) / 1e9,
+                 "classify_gbs": CLASSIFY_BYTES_PER_KEY * ps["classify"]["keys"] / (ps["classify"]["ms"] / 1e3) / 1e9,
+                 "level1_max_bucket": {d: int(sts_s[i].level[0].max_child) for i, (d, _) in enumerate(inputs)},
+                 "level1_bucket_sumsq": {d: int(sts_s[i].level[0].sumsq_child) for i, (d, _) in enumerate(inputs)}}
+
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(x).pin_memory() for _, x in inputs]
+        host_src = [x.copy() for _, x in inputs]
+        p_plain = lsg.ls_params_default(basecase_threshold=BASECASE_T)
+        lsg.ls_sort_host(ctx, host[0].numpy(), p_plain)  # warm the context's device cache
+        tt = []
+        for _ in range(max(1, min(args.steps, 3))):
+            for h, src in zip(host, host_src):
+                np.copyto(h.numpy(), src)
+            t0 = time.perf_counter()
+            for h in host:
+                lsg.ls_sort_host(ctx, h.numpy(), p_plain)
+            tt.append(time.perf_counter() - t0)
+        e2e = {"value": world * keys_per_step / (sum(tt) / len(tt)), "unit": "keys/s",
+               "h2d_bytes_per_step": 8 * keys_per_step, "d2h_bytes_per_step": 8 * keys_per_step,
+               "ms_per_step": 1e3 * sum(tt) / len(tt), "api": "ls_sort_host (pinned host buffers)"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        import oracle
+
+        oracle.build()
+        x = inputs[0][1]
+        t0 = time.perf_counter()
+        out, rc, _, _, _ = oracle.sort(x, oracle.params())
+        dt = time.perf_counter() - t0
+        assert rc == 0
+        cpu = {"value": x.size / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full {x.size}-key {inputs[0][0]} array (1 of the 6 distributions), single thread",
+               "seconds": dt}
+
+    launches = sum(int(st.kernel_launches) for st in sts_learned)
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C2: six 1e8-key float64 arrays per step (normal, lognormal, exponential, "
+                               "chi-squared, mix of 5 Gaussians, uniform[0,1e6)), full sort each",
+                   "partitioner": "Alg. 5 AUTO (RMI chosen on all six)", "fanout": 1000, "sample_rate": 0.01,
+                   "basecase_threshold": BASECASE_T, "recurse": "REFINE_GLOBAL",
+                   "keys_per_step_per_gpu": keys_per_step, "l2": "inputs 800 MB each, larger than L2; no flush",
+                   "timing": "CUDA events around each ls_sort on the launching stream; D2D input restore outside",
+                   "wall_s_timed_region_incl_restores": wall},
+        "roofline": roofline,
+        "splitter": split,
+        "per_dist": per_dist,
+        "passes_ms_per_step": {k: v["ms"] / args.steps for k, v in passes.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -101,8 +101,14 @@ typedef struct {
   int32_t partitioner;           /* ls_partitioner */
   int32_t recurse_model;         /* ls_recurse */
   int32_t classify_mode;         /* ls_classify_mode (speed only) */
-  uint32_t tile_keys;            /* keys per partition tile, 0 = library default */
+  uint32_t tile_keys;            /* reserved (0): the tile size is fixed at 4096 keys */
+  uint32_t flags;                /* LS_FLAG_* */
 } ls_params;
+
+/* ls_params.flags: record CUDA events around every kernel launch class and
+ * report their device time in ls_stats.pass[] (adds one event pair per
+ * launch; off by default). */
+#define LS_FLAG_TIME_PASSES 1u
 
 /* The trained two-layer RMI (all FP64), as exported by ls_fit. */
 typedef struct {
@@ -131,6 +137,23 @@ typedef struct {
   uint64_t keys, max_child, sumsq_child, eq_keys;
 } ls_level_stats;
 
+/* Kernel classes timed with LS_FLAG_TIME_PASSES. */
+#define LS_PASS_SAMPLE 0    /* sample gather + sample sort + duplicate count */
+#define LS_PASS_FIT 1       /* RMI fit (sums, leaves, monotone clamps) */
+#define LS_PASS_PIVOTS 2    /* exact pivots, imbalance test, decision, splitter tables, directory */
+#define LS_PASS_CLASSIFY 3  /* K1: classify + histogram (reads 8 B/key) */
+#define LS_PASS_CHILDREN 4  /* K2: bucket scan + children */
+#define LS_PASS_SCATTER 5   /* K3: stable scatter (reads and writes 8 B/key) */
+#define LS_PASS_BASE 6      /* base case and depth-limit fallback (8 B/key each way) */
+#define LS_PASS_COPY 7      /* copy of finished buckets back into the keys array */
+#define LS_NPASS 8
+
+typedef struct {
+  double ms;          /* summed device time of the class's launches */
+  uint64_t launches;
+  uint64_t keys;      /* keys the launches processed */
+} ls_pass_time;
+
 typedef struct {
   int32_t status;               /* device status of the call (LS_OK, LS_ENAN, ...) */
   int32_t root_decision;        /* LS_DEC_* of the first array's root */
@@ -142,6 +165,7 @@ typedef struct {
   ls_level_stats level[LS_MAX_LEVELS];
   double ms_total;              /* host-observed time of the call (stats only) */
   uint64_t kernel_launches;     /* kernels this call launched */
+  ls_pass_time pass[LS_NPASS];  /* filled when LS_FLAG_TIME_PASSES is set */
 } ls_stats;
 
 typedef struct ls_ctx ls_ctx;

@@ -140,7 +140,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
   l.mcap = 1024 + n / 65536;
   l.base_cap = n / 2 + 1024;
   l.large_cap = n / (kWarpSortMax + 1) + 1024;
-  l.copy_cap = n / 2 + 64 * 1024;
+  l.copy_cap = n / 2 + l.icap + 64 * 1024;  // <= one run of final buckets per non-final child + item
   l.fb_cap = n / (T + 1) + 1024;
   l.rchunk_cap = l.scap / kChunk + kBatchItems + 8;
   l.lchunk_cap = l.scap / kChunk + (uint64_t)kBatchItems * l.L + 8;
@@ -199,7 +199,58 @@ struct Batch {
   uint64_t ntiles = 0;
 };
 
+// CUDA-event timing of kernel classes (LS_FLAG_TIME_PASSES), recorded on
+// the caller's stream around each launch group.
+struct PassTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    uint64_t keys;
+  };
+  std::vector<Rec> recs;
+  Rec cur{};
+  cudaEvent_t make() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int cls, uint64_t keys) {
+    if (!on) return;
+    cur = Rec{make(), make(), cls, keys};
+    cudaEventRecord(cur.a, st);
+  }
+  void end() {
+    if (!on) return;
+    cudaEventRecord(cur.b, st);
+    recs.push_back(cur);
+  }
+  void collect(ls_stats* s) {
+    if (!on) return;
+    cudaStreamSynchronize(st);
+    for (Rec& r : recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && s) {
+        s->pass[r.cls].ms += ms;
+        s->pass[r.cls].launches += 1;
+        s->pass[r.cls].keys += r.keys;
+      }
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  ~PassTimer() {
+    for (Rec& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+
 struct Sorter {
+  PassTimer timer;
   ls_ctx* ctx;
   const ls_params* p;
   RunParams rp;
@@ -361,10 +412,12 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
     f.keysB = s.Bb;
     uint64_t* samp0 = at<uint64_t>(s.ws, L.o_samp0);
     uint64_t* samp1 = at<uint64_t>(s.ws, L.o_samp1);
+    s.timer.begin(LS_PASS_SAMPLE, samp_prefix.back());
     launch_sample_gather(f, s.rp, samp0, st);
     sorted = segmented_sort_u64(samp0, samp1, d_soff, d_scpre, (uint32_t)fresh.size(), sort_cpre.back(), max_s,
                                 st, &s.launches);
     launch_dups(f, sorted, st);
+    s.timer.end();
     s.launches += 2;
     if (!cand.empty()) {
       FitArgs fa;
@@ -391,22 +444,30 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       fa.leaf_of = at<uint32_t>(s.ws, L.o_leafof);
       fa.leaf_cnt = at<uint32_t>(s.ws, L.o_leafcnt);
       if (fa.total_rchunks > L.rchunk_cap || fa.lchunk_bound > L.lchunk_cap) return LS_ENOMEM;
+      s.timer.begin(LS_PASS_FIT, cand_soff.back());
       launch_fit(fa, s.rp, st, &s.launches);
+      s.timer.end();
+      s.timer.begin(LS_PASS_PIVOTS, 0);
       launch_learned_pivots(d_plans, d_items, d_cand, fa.ncand, pow2ceil(p->fanout), models, leaves, pivots, s.rp,
                             st);
       launch_imbalance(fa, pivots, counts, s.rp, st, &s.launches);
+      s.timer.end();
       s.launches += 1;
     }
+    s.timer.begin(LS_PASS_PIVOTS, 0);
     launch_decide(f, models, s.rp, st);
     launch_splitter_build(f, sorted, pivots, s.rp, st);
+    s.timer.end();
     s.launches += 2;
   }
+  s.timer.begin(LS_PASS_PIVOTS, 0);
   if (!refine_tab.empty()) {
     launch_learned_pivots(d_plans, d_items, d_reftab, (uint32_t)refine_tab.size(), pow2ceil(p->fanout), models,
                           leaves, pivots, s.rp, st);
     s.launches += 1;
   }
   launch_dir_build(d_plans, nitems, L.cells, pivots, dirs, st);
+  s.timer.end();
   s.launches += 1;
 
   // ---- partition passes
@@ -433,7 +494,13 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.check_nan = check_nan && s.dt == LS_F64;
   pa.nb_pad_max = L.nbc;
   pa.dir_cells_max = L.cells;
+  uint64_t batch_keys = 0;
+  for (uint32_t i = 0; i < nitems; ++i) batch_keys += its[i].n;
+  CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(pa.incl, 0, tiles * L.nbc * sizeof(unsigned long long), st));
+  s.timer.begin(LS_PASS_CLASSIFY, batch_keys);
   launch_classify_hist(pa, s.rp, st);
+  s.timer.end();
 
   ChildArgs ca;
   ca.items = d_items;
@@ -454,8 +521,12 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   ca.fallback_cap = L.fb_cap;
   ca.ctr = at<LevelCounters>(s.ws, L.o_ctr);
   ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
+  s.timer.begin(LS_PASS_CHILDREN, 0);
   launch_children(ca, s.rp, st);
+  s.timer.end();
+  s.timer.begin(LS_PASS_SCATTER, batch_keys);
   launch_scatter(pa, s.rp, st);
+  s.timer.end();
   s.launches += 3;
   CK(cudaGetLastError());
 
@@ -491,11 +562,19 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
 // Sort / copy the finished spans of one level.
 ls_status finish_spans(Sorter& s, const LevelCounters& c) {
   Layout& L = s.lay;
-  if (c.n_base_small) launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.dt, s.st);
-  if (c.n_base_large)
-    launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.dt, s.st);
-  if (c.n_copy) launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.st);
-  if (c.n_fallback) launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.dt, s.st);
+  if (c.n_base_small || c.n_base_large || c.n_fallback) {
+    s.timer.begin(LS_PASS_BASE, 0);
+    if (c.n_base_small) launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.dt, s.st);
+    if (c.n_base_large)
+      launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.dt, s.st);
+    if (c.n_fallback) launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.dt, s.st);
+    s.timer.end();
+  }
+  if (c.n_copy) {
+    s.timer.begin(LS_PASS_COPY, 0);
+    launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.st);
+    s.timer.end();
+  }
   s.launches += (c.n_base_small > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
   CK(cudaGetLastError());
   return LS_OK;
@@ -537,6 +616,8 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   s.Bb = at<uint64_t>(ws, lay.o_buf);
   s.seg_decision = seg_dec;
   s.nseg = nseg;
+  s.timer.on = (p->flags & LS_FLAG_TIME_PASSES) != 0;
+  s.timer.st = st;
   for (int m = (int)lay.mcap - 1; m >= 0; --m) s.model_free.push_back(m);
 
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), st));
@@ -658,6 +739,9 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     if (q.items || q.base_items || q.homogeneous || q.fallback_items) used = l + 1;
   }
   stats->levels_used = used;
+  s.timer.collect(stats);
+  for (uint32_t l = 0; l < LS_MAX_LEVELS; ++l)
+    stats->pass[LS_PASS_BASE].keys += stats->level[l].base_keys + stats->level[l].fallback_keys;
   stats->status = result;
   stats->kernel_launches = s.launches;
   ctx->launches += s.launches;

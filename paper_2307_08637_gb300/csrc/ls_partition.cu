@@ -497,25 +497,36 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
     }
     return;
   }
-  // write cursors: absolute positions in the destination buffer
+  // bucket starts (item-relative) and "final" flags in shared memory:
+  // a bucket is final when it is an equality bucket or holds <= 1 key.
+  extern __shared__ __align__(16) unsigned char k2smem[];
+  uint64_t* s_start = reinterpret_cast<uint64_t*>(k2smem);      // nb + 1
+  uint8_t* s_fin = reinterpret_cast<uint8_t*>(s_start + nb + 1);  // nb
   {
     uint64_t r = run;
     for (uint32_t b = b0; b < b1; ++b) {
-      a.cursors[pl.cnt_off + b] = it.lo + r;
-      r += cnt[b];
+      s_start[b] = r;
+      a.cursors[pl.cnt_off + b] = it.lo + r;  // destination of the bucket's first key
+      uint64_t sz = cnt[b];
+      s_fin[b] = (uint8_t)((eq && (b & 1)) || sz <= 1);
+      r += sz;
     }
+    if (threadIdx.x == 0) s_start[nb] = it.n;
   }
-  // classify children and count list entries
+  __syncthreads();
+  // count list entries: base case / fallback / next level per non-final
+  // bucket; one copy run per maximal run of final buckets (only when the
+  // destination is the workspace buffer)
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
-    if (eq && (b & 1)) {
-      eqk += sz;
-      if (sz && dest == 1) nl[L_COPY] += (uint32_t)((sz + kCopyPiece - 1) / kCopyPiece);
-      continue;
-    }
-    if (sz == 0) continue;
-    if (sz == 1) {
-      if (dest == 1) nl[L_COPY] += 1;
+    if (eq && (b & 1)) eqk += sz;
+    if (s_fin[b]) {
+      if (dest == 1 && (b == 0 || !s_fin[b - 1])) {
+        uint32_t e = b + 1;
+        while (e < nb && s_fin[e]) ++e;
+        uint64_t len = s_start[e] - s_start[b];
+        nl[L_COPY] += (uint32_t)((len + kCopyPiece - 1) / kCopyPiece);
+      }
       continue;
     }
     if (sz <= rp.T) {
@@ -565,30 +576,22 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
   for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + pos[q];
   const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.large_cap, a.copy_cap, a.fallback_cap};
   bool ovf = false;
-  uint64_t r = run;
   uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
   uint64_t mg = (it.kind == KIND_REFINE) ? it.mg : 0;
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
-    uint64_t clo = it.lo + r;
-    r += sz;
-    if (eq && (b & 1)) {
-      if (sz && dest == 1) {
-        for (uint64_t off = 0; off < sz; off += kCopyPiece) {
-          uint64_t len = sz - off < kCopyPiece ? sz - off : kCopyPiece;
-          if (wp[L_COPY] < caps[L_COPY]) a.copy[wp[L_COPY]] = Span{clo + off, (uint32_t)len, 1u};
+    uint64_t clo = it.lo + s_start[b];
+    if (s_fin[b]) {
+      if (dest == 1 && (b == 0 || !s_fin[b - 1])) {
+        uint32_t e = b + 1;
+        while (e < nb && s_fin[e]) ++e;
+        uint64_t len = s_start[e] - s_start[b];
+        for (uint64_t off = 0; off < len; off += kCopyPiece) {
+          uint64_t pl_len = len - off < kCopyPiece ? len - off : kCopyPiece;
+          if (wp[L_COPY] < caps[L_COPY]) a.copy[wp[L_COPY]] = Span{clo + off, (uint32_t)pl_len, 1u};
           else ovf = true;
           wp[L_COPY]++;
         }
-      }
-      continue;
-    }
-    if (sz == 0) continue;
-    if (sz == 1) {
-      if (dest == 1) {
-        if (wp[L_COPY] < caps[L_COPY]) a.copy[wp[L_COPY]] = Span{clo, 1u, 1u};
-        else ovf = true;
-        wp[L_COPY]++;
       }
       continue;
     }
@@ -985,14 +988,18 @@ void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  cudaMemsetAsync(a.chunk_ctr, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(a.incl, 0, a.nchunks * a.nb_pad_max * sizeof(unsigned long long), st);
   k_scatter<<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
 }
 
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   if (!a.nitems) return;
-  k_children<<<a.nitems, 1024, 0, st>>>(a, rp);
+  size_t sm = (size_t)(LS_MAX_FANOUT + 1) * 8 + LS_MAX_FANOUT + 16;
+  static bool set = false;
+  if (!set) {
+    cudaFuncSetAttribute(k_children, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = true;
+  }
+  k_children<<<a.nitems, 1024, sm, st>>>(a, rp);
 }
 
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, int dt, cudaStream_t st) {

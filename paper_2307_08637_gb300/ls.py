@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("recurse_model", C.c_int32),
         ("classify_mode", C.c_int32),
         ("tile_keys", C.c_uint32),
+        ("flags", C.c_uint32),
     ]
 
 
@@ -109,6 +110,14 @@ class LevelStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in _LEVEL_FIELDS]
 
 
+LS_FLAG_TIME_PASSES = 1
+PASS_NAMES = ("sample", "fit", "pivots", "classify", "children", "scatter", "base", "copy")
+
+
+class PassTime(C.Structure):
+    _fields_ = [("ms", C.c_double), ("launches", C.c_uint64), ("keys", C.c_uint64)]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("status", C.c_int32),
@@ -121,7 +130,12 @@ class Stats(C.Structure):
         ("level", LevelStats * LS_MAX_LEVELS),
         ("ms_total", C.c_double),
         ("kernel_launches", C.c_uint64),
+        ("pass_", PassTime * len(PASS_NAMES)),
     ]
+
+    def passes(self) -> dict:
+        return {n: {"ms": self.pass_[i].ms, "launches": int(self.pass_[i].launches), "keys": int(self.pass_[i].keys)}
+                for i, n in enumerate(PASS_NAMES)}
 
     def levels(self) -> list[dict]:
         return [{n: int(getattr(self.level[i], n)) for n in _LEVEL_FIELDS} for i in range(self.levels_used)]
