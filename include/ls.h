@@ -235,6 +235,23 @@ ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_s
                       double* d_pred, double* d_resid, double* d_grad_a, double* d_grad_b, double* d_grad_root,
                       ls_stream_t stream);
 
+/* ls_classify without any device allocation (the paper has no counterpart:
+ * this is a deployment variant of ls_classify).  For callers that cannot call
+ * cudaMalloc where they classify -- an application whose own memory pool
+ * owns the device memory, or a path that must not risk cudaMalloc's
+ * device-wide synchronisation.  Same arguments and results as ls_classify,
+ * without a context: it classifies on the current device and stream.
+ * Scratch is one fixed 256 KB device array inside the library (present on
+ * every GPU that loads it, until the process exits); it holds the model and
+ * pivot tables of the last call, is fully rewritten by each call, and is
+ * shared by all calls: calls that overlap on the GPU race, so serialise them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Fanouts up to LS_MAX_FANOUT fit; a model that needs more scratch than the
+ * array holds is rejected with LS_ENOMEM.  Synchronous on `stream`. */
+ls_status ls_classify_static(const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype, uint32_t k,
+                             uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist, ls_stream_t stream);
+
 /* Synchronise `stream` and return the device status word of the last call
  * on this context (LS_OK, LS_ENAN, LS_ETIMEOUT or LS_EDEVICE), then clear it. */
 ls_status ls_last_device_status(ls_ctx* ctx, ls_stream_t stream);

@@ -29,7 +29,7 @@ LS_MAX_LEVELS = 48
 EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
-    "ls_model_import", "ls_status_string",
+    "ls_model_import", "ls_status_string", "ls_classify_static",
 )
 
 
@@ -173,6 +173,8 @@ def lib() -> C.CDLL:
     L.ls_fit.restype = C.c_int
     L.ls_classify.argtypes = [vp, C.POINTER(Model), vp, u64, C.c_int, u32, u64, i32, vp, vp, vp]
     L.ls_classify.restype = C.c_int
+    L.ls_classify_static.argtypes = [C.POINTER(Model), vp, u64, C.c_int, u32, u64, i32, vp, vp, vp]
+    L.ls_classify_static.restype = C.c_int
     L.ls_fit_grad.argtypes = [vp, C.POINTER(Model), vp, u64, C.c_int, vp, vp, vp, vp, vp, vp]
     L.ls_fit_grad.restype = C.c_int
     L.ls_last_device_status.argtypes = [vp, vp]
@@ -344,6 +346,15 @@ def ls_classify(ctx: Context, model: Model, keys, k: int = 0, g: int = 0, mode: 
     _check(lib().ls_classify(ctx.handle, C.byref(model), _ptr(keys), keys.numel(), dt, k, g, mode, _ptr(ids),
                              _ptr(hist), _stream(stream)), "ls_classify")
     return ids, hist
+
+
+def ls_classify_static(model: Model, keys, ids, hist, k: int = 0, g: int = 0, mode: int = LS_CLASSIFY_AUTO,
+                       stream=None) -> None:
+    """ls_classify into caller-provided outputs, with no device allocation
+    anywhere on the path (for callers that cannot allocate: see ls.h)."""
+    dt = _dtype_code(keys)
+    _check(lib().ls_classify_static(C.byref(model), _ptr(keys), keys.numel(), dt, k, g, mode, _ptr(ids),
+                                    _ptr(hist), _stream(stream)), "ls_classify_static")
 
 
 def ls_fit_grad(ctx: Context, model: Model, sorted_sample, stream=None) -> dict:
