@@ -37,7 +37,7 @@ DISTS = datagen.F64_DISTS
 FALLBACK_HBM_GBS = 6800.0
 SCATTER_BYTES_PER_KEY = 16  # K3 reads each key once and writes it once
 CLASSIFY_BYTES_PER_KEY = 8  # K1 reads each key once
-BASECASE_T = 256            # buckets of <= 256 keys go to the warp-register base case
+BASECASE_T = 4096           # buckets of <= 4096 keys go to the shared-memory base case
 
 
 def parse():

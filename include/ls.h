@@ -77,10 +77,12 @@ typedef enum {
 /* Per-key bucket search used by the partition passes.  Every mode gives
  * identical bucket ids; they differ only in speed. */
 typedef enum {
-  LS_CLASSIFY_AUTO = 0,      /* learned: directory; splitter: tree search */
+  LS_CLASSIFY_AUTO = 0,      /* learned: FP32 guess; splitter: tree search */
   LS_CLASSIFY_DIRECTORY = 1, /* radix directory over the pivots + <=k compares */
   LS_CLASSIFY_TREE = 2,      /* branchless binary search over the pivots */
-  LS_CLASSIFY_DIRECT = 3     /* learned only: FP64 RMI per key (diagnostic) */
+  LS_CLASSIFY_DIRECT = 3,    /* learned only: FP64 RMI per key (diagnostic) */
+  LS_CLASSIFY_GUESS = 4      /* learned only: FP32 image of the RMI guesses the
+                                bucket, exact pivots correct it */
 } ls_classify_mode;
 
 #define LS_MAX_FANOUT 4096

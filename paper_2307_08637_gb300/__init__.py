@@ -15,7 +15,7 @@ from .ls import (  # noqa: F401
     ls_sort_segmented, ls_workspace_size, status_string,
     LS_OK, LS_EINVAL, LS_ENOMEM, LS_ENAN, LS_ETIMEOUT, LS_ECUDA, LS_ENOTIMPL, LS_EDEVICE,
     LS_F64, LS_U64, LS_PART_AUTO, LS_PART_LEARNED, LS_PART_SPLITTER, LS_RECURSE_REFINE_GLOBAL,
-    LS_RECURSE_RETRAIN, LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT,
+    LS_RECURSE_RETRAIN, LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT, LS_CLASSIFY_GUESS,
     LS_FLAG_TIME_PASSES, PASS_NAMES, PassTime,
     LS_DEC_NONE, LS_DEC_LEARNED, LS_DEC_SPLITTER, LS_DEC_SPLITTER_EQ, LS_DEC_HOMOGENEOUS, LS_MAX_FANOUT,
 )

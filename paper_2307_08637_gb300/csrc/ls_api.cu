@@ -68,7 +68,7 @@ ls_status validate_params(const ls_params* p) {
   if (!(p->sample_rate >= 0.0) || !(p->dup_frac >= 0.0) || !(p->imbalance_tau > 0.0)) return LS_EINVAL;
   if (p->partitioner < 0 || p->partitioner > 2) return LS_EINVAL;
   if (p->recurse_model < 0 || p->recurse_model > 1) return LS_EINVAL;
-  if (p->classify_mode < 0 || p->classify_mode > 3) return LS_EINVAL;
+  if (p->classify_mode < 0 || p->classify_mode > 4) return LS_EINVAL;
   return LS_OK;
 }
 
@@ -121,7 +121,7 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_incl, o_chunkctr;
+      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_incl, o_chunkctr, o_fmodels, o_fleaves, o_ids;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
@@ -153,6 +153,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
     return r;
   };
   l.o_buf = take(n * 8);
+  l.o_ids = take(n * 2);
   l.o_cur = take(l.icap * sizeof(Item));
   l.o_next = take(l.icap * sizeof(Item));
   l.o_plans = take(kBatchItems * sizeof(Plan));
@@ -167,6 +168,8 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
   l.o_models = take(l.mcap * sizeof(DModel));
   l.o_leaves = take(l.mcap * l.L * sizeof(Leaf));
   l.o_leafcnt = take(l.mcap * l.L * 4);
+  l.o_fmodels = take(l.mcap * sizeof(FModel));
+  l.o_fleaves = take(l.mcap * l.L * sizeof(FLeaf));
   l.o_samp0 = take(l.scap * 8);
   l.o_samp1 = take(l.scap * 8);
   l.o_rpart = take(8 * l.rchunk_cap * 8);
@@ -328,7 +331,10 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
         pl.nb_pad = pow2ceil(p->fanout);
         pl.kmax = p->fanout - 1;
         bool direct = p->classify_mode == LS_CLASSIFY_DIRECT || it.n < 4ull * p->fanout;
-        pl.cls = direct ? CLS_DIRECT : (p->classify_mode == LS_CLASSIFY_TREE ? CLS_TREE : CLS_DIR);
+        pl.cls = direct                                        ? CLS_DIRECT
+                 : p->classify_mode == LS_CLASSIFY_TREE        ? CLS_TREE
+                 : p->classify_mode == LS_CLASSIFY_DIRECTORY   ? CLS_DIR
+                                                               : CLS_GUESS;
         if (!direct) refine_tab.push_back(i);
       }
     }
@@ -443,6 +449,8 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       fa.lpart = at<double>(s.ws, L.o_lpart);
       fa.leaf_of = at<uint32_t>(s.ws, L.o_leafof);
       fa.leaf_cnt = at<uint32_t>(s.ws, L.o_leafcnt);
+      fa.fmodels = at<FModel>(s.ws, L.o_fmodels);
+      fa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
       if (fa.total_rchunks > L.rchunk_cap || fa.lchunk_bound > L.lchunk_cap) return LS_ENOMEM;
       s.timer.begin(LS_PASS_FIT, cand_soff.back());
       launch_fit(fa, s.rp, st, &s.launches);
@@ -466,9 +474,34 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
                           leaves, pivots, s.rp, st);
     s.launches += 1;
   }
-  launch_dir_build(d_plans, nitems, L.cells, pivots, dirs, st);
+  if (p->classify_mode == LS_CLASSIFY_DIRECTORY) {
+    launch_dir_build(d_plans, nitems, L.cells, pivots, dirs, st);
+    s.launches += 1;
+  }
   s.timer.end();
-  s.launches += 1;
+  // shared memory of the passes is sized by what this batch really uses;
+  // fresh items are decided on the device, so read their plans back
+  uint32_t nbp_max = 2;
+  bool any_dir = false, any_guess = false;
+  if (!fresh.empty()) {
+    std::vector<Plan> hp(nitems);
+    CK(cudaMemcpyAsync(hp.data(), d_plans, nitems * sizeof(Plan), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (const Plan& q : hp) {
+      nbp_max = std::max(nbp_max, q.nb_pad);
+      any_dir |= q.cls == CLS_DIR;
+      any_guess |= q.cls == CLS_GUESS;
+    }
+  } else {
+    for (const Plan& q : plans) {
+      nbp_max = std::max(nbp_max, q.nb_pad);
+      any_dir |= q.cls == CLS_DIR;
+      any_guess |= q.cls == CLS_GUESS;
+    }
+  }
+  uint32_t aux = 16;
+  if (any_dir) aux = std::max<uint32_t>(aux, ((L.cells + 1) * 2 + 15) & ~15u);
+  if (any_guess) aux = std::max<uint32_t>(aux, L.L * (uint32_t)sizeof(FLeaf));
 
   // ---- partition passes
   PassArgs pa;
@@ -492,8 +525,12 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.cursors = cursors;
   pa.status = s.ctx->d_status;
   pa.check_nan = check_nan && s.dt == LS_F64;
-  pa.nb_pad_max = L.nbc;
+  pa.nb_pad_max = nbp_max;
   pa.dir_cells_max = L.cells;
+  pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
+  pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
+  pa.aux_bytes = aux;
+  pa.ids = at<uint16_t>(s.ws, L.o_ids);
   uint64_t batch_keys = 0;
   for (uint32_t i = 0; i < nitems; ++i) batch_keys += its[i].n;
   CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
@@ -971,6 +1008,8 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
   fa.lpart = at<double>(ws, lay.o_lpart);
   fa.leaf_of = at<uint32_t>(ws, lay.o_leafof);
   fa.leaf_cnt = at<uint32_t>(ws, lay.o_leafcnt);
+  fa.fmodels = at<FModel>(ws, lay.o_fmodels);
+  fa.fleaves = at<FLeaf>(ws, lay.o_fleaves);
   launch_fit(fa, s.rp, st, &s.launches);
   uint64_t* pivots = at<uint64_t>(ws, lay.o_pivots);
   unsigned long long* counts = at<unsigned long long>(ws, lay.o_counts);
@@ -1030,7 +1069,7 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
 ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype, uint32_t k,
                       uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist, ls_stream_t stream) {
   if (!ctx || !model || (!d_keys && n) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
-  if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < 0 || mode > 3) return LS_EINVAL;
+  if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < 0 || mode > 4) return LS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
   uint32_t B = model->L;
@@ -1040,7 +1079,7 @@ ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, ui
   uint32_t nbp = pow2ceil(B);
   uint32_t cells = 1u << kDirBits;
   size_t need = up(sizeof(DModel)) + up(B * sizeof(Leaf)) + up(sizeof(Item)) + up(sizeof(Plan)) + up(nbp * 8) +
-                up((cells + 1) * 2) + up(8);
+                up((cells + 1) * 2) + up(8) + up(sizeof(FModel)) + up(B * sizeof(FLeaf)) + up(8);
   ls_status r = ensure_cache(ctx, need + kAlign);
   if (r != LS_OK) return r;
   char* b = static_cast<char*>(ctx->d_cache);
@@ -1057,6 +1096,12 @@ ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, ui
   uint16_t* d_dir = reinterpret_cast<uint16_t*>(b);
   b += up((cells + 1) * 2);
   uint32_t* d_list = reinterpret_cast<uint32_t*>(b);
+  b += up(8);
+  FModel* d_fm = reinterpret_cast<FModel*>(b);
+  b += up(sizeof(FModel));
+  FLeaf* d_fl = reinterpret_cast<FLeaf*>(b);
+  b += up(B * sizeof(FLeaf));
+  int32_t* d_slot = reinterpret_cast<int32_t*>(b);
   DModel dm;
   std::vector<Leaf> lv;
   model_to_device_layout(model, &dm, lv);
@@ -1083,19 +1128,21 @@ ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, ui
   pl.nb = B;
   pl.nb_pad = nbp;
   pl.decision = LS_DEC_LEARNED;
-  pl.cls = (mode == LS_CLASSIFY_TREE) ? CLS_TREE : CLS_DIR;
+  pl.cls = (mode == LS_CLASSIFY_TREE) ? CLS_TREE : (mode == LS_CLASSIFY_GUESS) ? CLS_GUESS : CLS_DIR;
   uint32_t zero = 0;
   CK(cudaMemcpyAsync(d_it, &it, sizeof it, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_pl, &pl, sizeof pl, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_list, &zero, 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_slot, &zero, 4, cudaMemcpyHostToDevice, st));
   RunParams rp;
   memset(&rp, 0, sizeof rp);
   rp.B = B;
   rp.dt = dtype;
   launch_learned_pivots(d_pl, d_it, d_list, 1, nbp, d_m, d_l, d_piv, rp, st);
   launch_dir_build(d_pl, 1, cells, d_piv, d_dir, st);
+  if (mode == LS_CLASSIFY_GUESS) launch_fmodel(d_m, d_l, d_slot, 1, B, d_fm, d_fl, st);
   launch_table_classify(d_pl, d_piv, d_dir, static_cast<const uint64_t*>(d_keys), n, dtype, d_ids,
-                        reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st);
+                        reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st, d_fm, d_fl);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   return LS_OK;

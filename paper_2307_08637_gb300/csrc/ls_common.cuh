@@ -29,7 +29,7 @@ constexpr uint64_t kChunkKeys = (uint64_t)kTileKeys * kChunkTiles;
 constexpr unsigned long long kReady = 1ull << 63;     // inclusive-prefix flag of a chunk
 
 enum : uint8_t { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2 };
-enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2 };
+enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2, CLS_GUESS = 3 };
 enum : uint8_t { FLAG_SKIP_SCATTER = 1, FLAG_HOMOGENEOUS = 2, FLAG_NOPROGRESS = 4 };
 
 // One RMI leaf f2^(i)(x) = a (x - x0) + b, clamped to [lo, hi] (Sec. 4).
@@ -46,6 +46,16 @@ struct DModel {
   uint32_t ok;         // 1 if every parameter is finite
   uint32_t pad;
 };
+
+// FP32 image of a model, used only to guess a bucket that exact pivots then
+// correct: root r = raL (xf - rx0f) + rbL gives the leaf, leaf i is
+// F ~ a_i (xf - x0_i) + b_i (FLeaf = {x0, a, b, unused}).
+struct FModel {
+  float xminf, xmaxf, rx0f, raL, rbL;
+  uint32_t L;
+  uint64_t leaf_off;  // offset into the FLeaf pool (same as the FP64 leaves)
+};
+typedef float4 FLeaf;
 
 // A range of keys still to be partitioned (a bucket of the previous level).
 struct Item {
@@ -229,6 +239,73 @@ __device__ __forceinline__ uint32_t pivot_count_dir(const uint64_t* __restrict__
     else e = mid - 1;
   }
   while (b < e && T[b + 1] <= u) ++b;
+  return b;
+}
+
+// Key -> float by bit manipulation (round toward zero), no FP64 or
+// conversion-pipe instruction: doubles outside the float range saturate to
+// +-0 / +-inf, u64 keys keep their top 24 significant bits.  Monotone in
+// the key order; only used for guesses.
+__device__ __forceinline__ float key_to_float(uint64_t bits, int dt) {
+  if (dt) {
+    if (bits == 0) return 0.0f;
+    uint32_t lz = __clzll((long long)bits);
+    uint32_t e = 63 - lz;
+    uint32_t mant = (uint32_t)((bits << lz) >> 40) & 0x7FFFFFu;
+    return __uint_as_float(((e + 127u) << 23) | mant);
+  }
+  uint32_t hi = (uint32_t)(bits >> 32);
+  uint32_t sign = hi & 0x80000000u;
+  int32_t e = (int32_t)((hi >> 20) & 0x7FF) - 1023 + 127;
+  uint32_t mant = (uint32_t)((bits >> 29) & 0x7FFFFFu);
+  uint32_t f;
+  if (e <= 0) f = sign;                       // zero, subnormal, underflow
+  else if (e >= 255) f = sign | 0x7F800000u;  // inf or overflow
+  else f = sign | ((uint32_t)e << 23) | mant;
+  return __uint_as_float(f);
+}
+
+// Bucket guess from the FP32 model image (leaves in shared memory), for
+// refinement scale P and offset Bg; clamped to [0, kmax].
+__device__ __forceinline__ uint32_t guess_bucket(const FModel& m, const FLeaf* __restrict__ fl, float Pf, float Bgf,
+                                                 uint32_t kmax, uint64_t bits, int dt) {
+  float x = key_to_float(bits, dt);
+  x = fminf(fmaxf(x, m.xminf), m.xmaxf);
+  float r = __fmaf_rn(m.raL, x - m.rx0f, m.rbL);
+  int li = (int)fminf(fmaxf(floorf(r), 0.0f), (float)(m.L - 1));
+  FLeaf l = fl[li];
+  float F = __fmaf_rn(l.y, x - l.x, l.z);
+  float t = floorf(__fmaf_rn(F, Pf, -Bgf));
+  t = fminf(fmaxf(t, 0.0f), (float)kmax);  // NaN-free inputs: the model image is finite
+  return (uint32_t)t;
+}
+
+// Exact bucket #{j <= kmax : T[j] <= u} from a guess: two steps either way,
+// then the full branchless search.  T[0] <= every key of the item.
+__device__ __forceinline__ uint32_t fix_bucket(const uint64_t* __restrict__ T, uint32_t nb_pad, uint32_t kmax,
+                                               uint32_t g, uint64_t u) {
+  uint32_t b = g;
+  if (T[b] > u) {
+    --b;
+    if (T[b] > u) {
+      --b;
+      if (T[b] > u) {
+        b = pivot_count(T, nb_pad, u);
+        return b < kmax ? b : kmax;
+      }
+    }
+    return b;
+  }
+  if (b < kmax && T[b + 1] <= u) {
+    ++b;
+    if (b < kmax && T[b + 1] <= u) {
+      ++b;
+      if (b < kmax && T[b + 1] <= u) {
+        b = pivot_count(T, nb_pad, u);
+        return b < kmax ? b : kmax;
+      }
+    }
+  }
   return b;
 }
 

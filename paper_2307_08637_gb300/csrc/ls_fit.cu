@@ -439,8 +439,9 @@ __device__ __forceinline__ double refine_value(const DModel& m, const Leaf* lv, 
 }
 
 // Smallest u in [lo, hi] with v(u) >= t, given v(lo) < t <= v(hi).  v is
-// monotone in u, so any bracketing search is exact; interpolation steps are
-// interleaved with bisection so at most ~3*64 evaluations are needed.
+// monotone in u, so any bracketing search is exact.  Interpolation steps
+// (with a bisection every fourth step) also test the neighbour of the
+// estimate, so an estimate within one ord of the pivot closes the bracket.
 __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64_t lo, uint64_t hi, double t,
                                  double P, double vlo, double vhi) {
   uint64_t L = lo, H = hi;
@@ -448,7 +449,8 @@ __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64
   for (int it = 0; it < 256 && H - L > 1; ++it) {
     uint64_t span = H - L;
     uint64_t mid;
-    if ((it % 3) != 2 && vH > vL) {
+    bool interp = (it & 3) != 3 && vH > vL;
+    if (interp) {
       double frac = (t - vL) / (vH - vL);
       double off = frac * (double)span;
       uint64_t o;
@@ -463,12 +465,40 @@ __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64
     if (vm >= t) {
       H = mid;
       vH = vm;
+      if (interp && mid - 1 > L) {
+        double v2 = refine_value(m, lv, mid - 1, P, dt);
+        if (v2 >= t) {
+          H = mid - 1;
+          vH = v2;
+        } else {
+          L = mid - 1;
+          vL = v2;
+        }
+      }
     } else {
       L = mid;
       vL = vm;
+      if (interp && mid + 1 < H) {
+        double v2 = refine_value(m, lv, mid + 1, P, dt);
+        if (v2 >= t) {
+          H = mid + 1;
+          vH = v2;
+        } else {
+          L = mid + 1;
+          vL = v2;
+        }
+      }
     }
   }
   return H;
+}
+
+// The bucket a refinement value v maps to: clamp(floor(v) - Bg, 0, B-1)
+// (the same arithmetic as refine_id after its multiplication by P).
+__device__ __forceinline__ uint32_t bucket_of_value(double v, double Bg, uint32_t B) {
+  double t = floor(v);
+  t = __dsub_rn(t, Bg);
+  return clamp_index(t, B - 1);
 }
 
 __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
@@ -480,23 +510,25 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
   uint32_t pi = list[li];
   Plan& pl = plans[pi];
   const Item& it = items[pi];
+  uint64_t* T = pivots + pl.tab_off;
+  uint32_t B = rp.B;
+  if (j >= B) {
+    T[j] = ~0ull;
+    return;
+  }
   DModel m = models[pl.model];
   const Leaf* lv = leaves + m.leaf_off;
-  uint32_t B = rp.B;
   double P = pl.P, Bg = pl.Bg;
   uint64_t lo = it.ord_lo, hi = it.ord_hi;
-  uint64_t* T = pivots + pl.tab_off;
-  uint32_t kmin = refine_id(m, lv, ord_value(lo, rp.dt), P, Bg, B);
-  uint32_t kmax = refine_id(m, lv, ord_value(hi, rp.dt), P, Bg, B);
+  double vlo = refine_value(m, lv, lo, P, rp.dt);
+  double vhi = refine_value(m, lv, hi, P, rp.dt);
+  uint32_t kmin = bucket_of_value(vlo, Bg, B);
+  uint32_t kmax = bucket_of_value(vhi, Bg, B);
   if (j == 0) {
     T[0] = lo;
     pl.kmax = kmax;
     pl.nb = B;
     pl.nb_pad = nb_pad;
-    return;
-  }
-  if (j >= B) {
-    T[j] = ~0ull;
     return;
   }
   if (j <= kmin) {
@@ -508,9 +540,64 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
     return;
   }
   double t = __dadd_rn((double)j, Bg);
-  double vlo = refine_value(m, lv, lo, P, rp.dt);
-  double vhi = refine_value(m, lv, hi, P, rp.dt);
-  T[j] = search_pivot(m, lv, rp.dt, lo, hi, t, P, vlo, vhi);
+  // Analytic guess inside the leaf whose F-range reaches the target: the
+  // leaf model is linear, so x* = x0 + (t/P - b)/a lands within a few ord
+  // of the pivot; two evaluations confirm it, otherwise the bracket the
+  // evaluations leave is searched.
+  uint64_t L = lo, H = hi;
+  double vL = vlo, vH = vhi;
+  {
+    double xlo = ord_value(lo, rp.dt), xhi = ord_value(hi, rp.dt);
+    double xcl = dmin(dmax(xlo, m.xmin), m.xmax), xch = dmin(dmax(xhi, m.xmin), m.xmax);
+    uint32_t l0 = root_leaf(m, xcl), l1 = root_leaf(m, xch);
+    double tF = t / P;
+    while (l0 < l1) {  // first leaf whose clamp maximum reaches tF
+      uint32_t mid = (l0 + l1) >> 1;
+      if (lv[mid].hi < tF) l0 = mid + 1;
+      else l1 = mid;
+    }
+    Leaf lf = lv[l0];
+    if (lf.a > 0.0) {
+      double xs = lf.x0 + (tF - lf.b) / lf.a;
+      if (xs >= xlo && xs <= xhi) {
+        uint64_t u;
+        if (rp.dt) {
+          u = xs >= 18446744073709549568.0 ? ~0ull : (uint64_t)xs;
+        } else {
+          u = ord_of((uint64_t)__double_as_longlong(xs), 0);
+        }
+        if (u > L && u < H) {
+          double vu = refine_value(m, lv, u, P, rp.dt);
+          if (vu >= t) {
+            H = u;
+            vH = vu;
+            double v2 = refine_value(m, lv, u - 1, P, rp.dt);
+            if (v2 < t) {
+              T[j] = u;
+              return;
+            }
+            if (u - 1 > L) {
+              H = u - 1;
+              vH = v2;
+            }
+          } else {
+            L = u;
+            vL = vu;
+            double v2 = refine_value(m, lv, u + 1, P, rp.dt);
+            if (v2 >= t) {
+              T[j] = u + 1;
+              return;
+            }
+            if (u + 1 < H) {
+              L = u + 1;
+              vL = v2;
+            }
+          }
+        }
+      }
+    }
+  }
+  T[j] = search_pivot(m, lv, rp.dt, L, H, t, P, vL, vH);
 }
 
 // Classify the candidates' own samples with their learned pivots (sample
@@ -584,9 +671,10 @@ __global__ void k_decide(FreshArgs f, const DModel* models, RunParams rp) {
   }
   if (learned) {
     pl.decision = LS_DEC_LEARNED;
-    pl.cls = (rp.classify_mode == LS_CLASSIFY_TREE) ? CLS_TREE
-             : (rp.classify_mode == LS_CLASSIFY_DIRECT) ? CLS_DIRECT
-                                                         : CLS_DIR;
+    pl.cls = (rp.classify_mode == LS_CLASSIFY_TREE)        ? CLS_TREE
+             : (rp.classify_mode == LS_CLASSIFY_DIRECT)    ? CLS_DIRECT
+             : (rp.classify_mode == LS_CLASSIFY_DIRECTORY) ? CLS_DIR
+                                                           : CLS_GUESS;
   } else {
     pl.decision = LS_DEC_SPLITTER;  // refined to SPLITTER_EQ by the table build
     pl.model = -1;
@@ -876,6 +964,41 @@ __global__ void k_grad_root_finish(uint64_t S, uint64_t nch, GradScratch g, doub
   }
 }
 
+// FP32 image of model slot `slot`: thread per leaf, one extra for the root.
+__device__ __forceinline__ void fmodel_one(const DModel* models, const Leaf* leaves, int32_t slot, uint32_t i,
+                                           uint32_t L, FModel* fm, FLeaf* fl) {
+  const DModel& m = models[slot];
+  if (i < L) {
+    Leaf l = leaves[m.leaf_off + i];
+    fl[m.leaf_off + i] = make_float4(__double2float_rn(l.x0), __double2float_rn(l.a), __double2float_rn(l.b), 0.0f);
+  } else if (i == L) {
+    FModel f;
+    f.xminf = __double2float_rn(m.xmin);
+    f.xmaxf = __double2float_rn(m.xmax);
+    f.rx0f = __double2float_rn(m.rx0);
+    f.raL = __double2float_rn(__dmul_rn(m.ra, (double)m.L));
+    f.rbL = __double2float_rn(__dmul_rn(m.rb, (double)m.L));
+    f.L = m.L;
+    f.leaf_off = m.leaf_off;
+    fm[slot] = f;
+  }
+}
+
+__global__ void k_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots,
+                         uint32_t L, FModel* fm, FLeaf* fl) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)nslots * (L + 1)) return;
+  uint32_t c = (uint32_t)(g / (L + 1)), i = (uint32_t)(g % (L + 1));
+  fmodel_one(models, leaves, slots[c], i, L, fm, fl);
+}
+
+__global__ void k_fmodel_fit(FitArgs a) {
+  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)a.ncand * (a.L + 1)) return;
+  uint32_t c = (uint32_t)(g / (a.L + 1)), i = (uint32_t)(g % (a.L + 1));
+  fmodel_one(a.models, a.leaves, a.plans[a.cand[c]].model, i, a.L, a.fmodels, a.fleaves);
+}
+
 }  // namespace
 
 // ===================================================== host launchers
@@ -921,7 +1044,14 @@ void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t
   k_fit_leaf_partials<<<grid_for(a.lchunk_bound, 128), 128, 0, st>>>(a, rp);
   k_fit_leaf_finish<<<grid_for(tot, 128), 128, 0, st>>>(a, rp, a.leaf_cnt);
   k_fit_monotone<<<a.ncand, 1024, 0, st>>>(a, a.leaf_cnt);
-  *launches += 12;
+  k_fmodel_fit<<<grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st>>>(a);
+  *launches += 13;
+}
+
+void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
+                   FModel* fm, FLeaf* fl, cudaStream_t st) {
+  if (!nslots) return;
+  k_fmodel<<<grid_for((uint64_t)nslots * (L + 1)), kTPB, 0, st>>>(models, leaves, slots, nslots, L, fm, fl);
 }
 
 void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,

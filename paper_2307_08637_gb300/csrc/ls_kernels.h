@@ -82,8 +82,15 @@ struct FitArgs {
   double* lpart;               // 4 * lchunk_bound
   uint32_t* leaf_of;           // total_cand_samples
   uint32_t* leaf_cnt;          // per model slot * L (sample points per leaf)
+  FModel* fmodels;             // per model slot: FP32 image header
+  FLeaf* fleaves;              // per model slot * L: FP32 image leaves
 };
 void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches);
+
+// FP32 images of the models of one slot list (used for bucket guesses).
+void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
+                   FModel* fm, FLeaf* fl, cudaStream_t st);
+void launch_fmodel_for_fit(const FitArgs& a, cudaStream_t st);
 
 // Exact learned pivots for items whose plan has decision candidate LEARNED:
 // list of plan indices; thread per (item, j < nb_pad).
@@ -121,6 +128,10 @@ struct PassArgs {
   const uint16_t* dirs;
   const DModel* models;
   const Leaf* leaves;
+  const FModel* fmodels;
+  const FLeaf* fleaves;
+  uint32_t aux_bytes;           // shared-memory bytes for a directory or FP32 leaves
+  uint16_t* ids;                // per key (same offsets as the keys): bucket id written by K1, read by K3
   unsigned long long* counts;   // per plan: nb counts
   unsigned long long* cursors;  // per plan: nb bucket bases in the destination
   uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
@@ -167,6 +178,6 @@ void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t*
                             double Bg, uint32_t B, uint32_t* ids, unsigned long long* hist, cudaStream_t st);
 void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs, const uint64_t* keys,
                            uint64_t n, int dt, uint32_t* ids, unsigned long long* hist, uint32_t nb_pad,
-                           uint32_t cells, cudaStream_t st);
+                           uint32_t cells, cudaStream_t st, const FModel* fm = nullptr, const FLeaf* fl = nullptr);
 
 }  // namespace lsg

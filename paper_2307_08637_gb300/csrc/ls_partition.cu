@@ -52,25 +52,33 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t* h, uint32_t b) {
 struct Cls {
   uint64_t dir_lo, dir_hi;
   double P, Bg;
+  FModel fm;
+  float Pf, Bgf;
   uint32_t nb_pad, kmax, shift, B;
   int32_t model;
   uint8_t cls;
+  uint8_t agg;  // warp-aggregate histogram increments (splitters: duplicates collide)
 };
 
-__device__ __forceinline__ uint32_t classify_key(uint64_t bits, const Cls& c, const uint64_t* sT, const uint16_t* sD,
+__device__ __forceinline__ uint32_t classify_key(uint64_t bits, const Cls& c, const uint64_t* sT, const void* sAux,
                                                  const DModel* models, const Leaf* leaves, int dt) {
   if (c.cls == CLS_DIRECT) {
     const DModel& m = models[c.model];
     return refine_id(m, leaves + m.leaf_off, key_value(bits, dt), c.P, c.Bg, c.B);
   }
   uint64_t u = ord_of(bits, dt);
-  uint32_t b = (c.cls == CLS_DIR) ? pivot_count_dir(sT, sD, c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
-                                  : pivot_count(sT, c.nb_pad, u);
+  if (c.cls == CLS_GUESS) {
+    uint32_t gb = guess_bucket(c.fm, static_cast<const FLeaf*>(sAux), c.Pf, c.Bgf, c.kmax, bits, dt);
+    return fix_bucket(sT, c.nb_pad, c.kmax, gb, u);
+  }
+  uint32_t b = (c.cls == CLS_DIR)
+                   ? pivot_count_dir(sT, static_cast<const uint16_t*>(sAux), c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
+                   : pivot_count(sT, c.nb_pad, u);
   return b < c.kmax ? b : c.kmax;
 }
 
 // Load item pi's classifier into shared memory (all threads).
-__device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, uint16_t* sD) {
+__device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, void* sAux) {
   const Plan& pl = a.plans[pi];
   c.cls = pl.cls;
   c.nb_pad = pl.nb_pad;
@@ -80,8 +88,11 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
   c.shift = pl.dir_shift;
   c.P = pl.P;
   c.Bg = pl.Bg;
+  c.Pf = (float)pl.P;
+  c.Bgf = (float)pl.Bg;
   c.B = rp.B;
   c.model = pl.model;
+  c.agg = pl.decision != LS_DEC_LEARNED;
   if (c.cls == CLS_DIRECT) {
     c.kmax = rp.B - 1;
     return;
@@ -90,7 +101,13 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
   for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) sT[j] = T[j];
   if (c.cls == CLS_DIR) {
     const uint16_t* D = a.dirs + pl.dir_off;
+    uint16_t* sD = static_cast<uint16_t*>(sAux);
     for (uint32_t j = threadIdx.x; j <= pl.dir_cells; j += blockDim.x) sD[j] = D[j];
+  } else if (c.cls == CLS_GUESS) {
+    c.fm = a.fmodels[pl.model];
+    const FLeaf* F = a.fleaves + c.fm.leaf_off;
+    FLeaf* sF = static_cast<FLeaf*>(sAux);
+    for (uint32_t j = threadIdx.x; j < c.fm.L; j += blockDim.x) sF[j] = F[j];
   }
 }
 
@@ -99,11 +116,11 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
 // Classify every key of every chunk, histogram per chunk in shared memory;
 // write the chunk's bucket counts (dense row, used by K3's lookback), add
 // them to the item's totals, and track the item's min / max ord.
-__global__ void __launch_bounds__(kTPB) k_classify_hist(PassArgs a, RunParams rp) {
+__global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* sH = reinterpret_cast<uint32_t*>(sT + a.nb_pad_max);
-  uint16_t* sD = reinterpret_cast<uint16_t*>(sH + a.nb_pad_max);
+  void* sD = sT + a.nb_pad_max;  // directory or FP32 leaves (aux_bytes, 16-byte aligned)
+  uint32_t* sH = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(sD) + a.aux_bytes);
   for (uint32_t j = threadIdx.x; j < a.nb_pad_max; j += blockDim.x) sH[j] = 0;
   uint32_t cur = 0xFFFFFFFFu;
   Cls c;
@@ -121,6 +138,7 @@ __global__ void __launch_bounds__(kTPB) k_classify_hist(PassArgs a, RunParams rp
     uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
     uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
+    uint16_t* idout = a.ids + it.lo + c0;
     unsigned long long mn = ~0ull, mx = 0;
     for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
       uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
@@ -143,8 +161,10 @@ __global__ void __launch_bounds__(kTPB) k_classify_hist(PassArgs a, RunParams rp
           mn = u < mn ? u : mn;
           mx = u > mx ? u : mx;
           b = classify_key(bits, c, sT, sD, a.models, a.leaves, rp.dt);
+          idout[t0 + idx] = (uint16_t)b;
         }
-        agg_inc(sH, b);
+        if (c.agg) agg_inc(sH, b);
+        else if (b != 0xFFFFFFFFu) atomicAdd(&sH[b], 1u);
       }
     }
     __syncthreads();
@@ -183,24 +203,20 @@ __global__ void __launch_bounds__(kTPB) k_classify_hist(PassArgs a, RunParams rp
 // consecutive keys and ranks them in order with warp-private counters, so
 // every key keeps its relative order within its bucket (the stable counting
 // sort of the partitioning step).
-__global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
+__global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kWarps = kTPB / 32;
   const uint32_t nbp = a.nb_pad_max;
-  uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* sRun = sT + nbp;                              // next destination per bucket
+  uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);     // next destination per bucket
   uint64_t* stage = sRun + nbp;                           // kTile keys
   uint32_t* sLs = reinterpret_cast<uint32_t*>(stage + kTile);  // tile-local start per bucket
   uint32_t* sCnt = sLs + nbp;                             // tile count per bucket
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(sCnt + nbp);  // [kWarps][nbp]
   uint16_t* sid = wcnt + kWarps * nbp;                    // kTile bucket ids
-  uint16_t* sD = sid + kTile;
   __shared__ uint32_t wsum[kWarps];
   __shared__ unsigned long long s_chunk;
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (uint32_t j = threadIdx.x; j < kWarps * nbp; j += blockDim.x) wcnt[j] = 0;
-  uint32_t cur = 0xFFFFFFFFu;
-  Cls c;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_chunk = atomicAdd(a.chunk_ctr, 1ull);
@@ -210,12 +226,8 @@ __global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
     uint32_t pi = find_plan(a.plans, a.nitems, ch);
     const Plan& pl = a.plans[pi];
     if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
-    if (pi != cur) {
-      load_cls(a, rp, pi, c, sT, sD);
-      cur = pi;
-    }
     const Item& it = a.items[pi];
-    const uint32_t nbk = c.nb_pad;
+    const uint32_t nbk = pl.nb_pad;
     // lookback: destination of this chunk's first key of each bucket
     const uint64_t cfirst = pl.chunk_begin;
     const uint32_t* aggrow = a.agg + ch * nbp;
@@ -237,6 +249,7 @@ __global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
     uint64_t c0 = (ch - cfirst) * kChunkKeys;
     uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
+    const uint16_t* idin = a.ids + it.lo + c0;
     uint64_t* dst = it.buf ? a.outA : a.outB;
     bool oob = false;
     for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
@@ -249,11 +262,11 @@ __global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
       for (int k = 0; k < kKPT; ++k) {
         uint32_t pos = wid * (32 * kKPT) + k * 32 + lane;
         v[k] = pos < len ? src[t0 + pos] : 0;
+        bk[k] = pos < len ? (uint32_t)idin[t0 + pos] : 0xFFFFFFFFu;
       }
 #pragma unroll
       for (int k = 0; k < kKPT; ++k) {
-        uint32_t pos = wid * (32 * kKPT) + k * 32 + lane;
-        uint32_t b = pos < len ? classify_key(v[k], c, sT, sD, a.models, a.leaves, rp.dt) : 0xFFFFFFFFu;
+        uint32_t b = bk[k];
         unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
         int leader = __ffs(peers) - 1;
         uint32_t old = 0;
@@ -327,6 +340,8 @@ __global__ void __launch_bounds__(kTPB) k_scatter(PassArgs a, RunParams rp) {
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) wcnt[w * nbp + b] = 0;
       }
+      // the next tile's ranking writes the counters this loop clears
+      __syncthreads();
     }
     if (oob) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
   }
@@ -825,18 +840,26 @@ __global__ void k_direct_classify(const DModel* mp, const Leaf* leaves, const ui
 
 __global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs,
                                  const uint64_t* __restrict__ keys, uint64_t n, int dt, uint32_t* ids,
-                                 unsigned long long* hist, uint32_t nb_pad, uint32_t cells) {
+                                 unsigned long long* hist, uint32_t nb_pad, uint32_t cells, const FModel* fmp,
+                                 const FLeaf* flp, uint32_t aux_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* sH = reinterpret_cast<uint32_t*>(sT + nb_pad);
-  uint16_t* sD = reinterpret_cast<uint16_t*>(sH + nb_pad);
+  void* sAux = sT + nb_pad;
+  uint32_t* sH = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(sAux) + aux_bytes);
+  uint16_t* sD = static_cast<uint16_t*>(sAux);
+  FLeaf* sF = static_cast<FLeaf*>(sAux);
   Plan pl = *plan;
+  FModel fm;
+  if (pl.cls == CLS_GUESS) fm = *fmp;
   for (uint32_t j = threadIdx.x; j < nb_pad; j += blockDim.x) {
     sT[j] = pivots[pl.tab_off + j];
     sH[j] = 0;
   }
   if (pl.cls == CLS_DIR)
     for (uint32_t j = threadIdx.x; j <= cells; j += blockDim.x) sD[j] = dirs[pl.dir_off + j];
+  if (pl.cls == CLS_GUESS)
+    for (uint32_t j = threadIdx.x; j < fm.L; j += blockDim.x) sF[j] = flp[fm.leaf_off + j];
+  const float Pf = (float)pl.P, Bgf = (float)pl.Bg;
   __syncthreads();
   uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t nround = (n + stride - 1) / stride;
@@ -844,10 +867,15 @@ __global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const
     uint64_t i = rd * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     uint32_t b = 0xFFFFFFFFu;
     if (i < n) {
-      uint64_t u = ord_of(keys[i], dt);
-      b = (pl.cls == CLS_DIR) ? pivot_count_dir(sT, sD, pl.dir_lo, pl.dir_hi, pl.dir_shift, pl.kmax, u)
-                              : pivot_count(sT, nb_pad, u);
-      b = b < pl.kmax ? b : pl.kmax;
+      uint64_t bits = keys[i];
+      uint64_t u = ord_of(bits, dt);
+      if (pl.cls == CLS_GUESS) {
+        b = fix_bucket(sT, nb_pad, pl.kmax, guess_bucket(fm, sF, Pf, Bgf, pl.kmax, bits, dt), u);
+      } else {
+        b = (pl.cls == CLS_DIR) ? pivot_count_dir(sT, sD, pl.dir_lo, pl.dir_hi, pl.dir_shift, pl.kmax, u)
+                                : pivot_count(sT, nb_pad, u);
+        b = b < pl.kmax ? b : pl.kmax;
+      }
       if (ids) ids[i] = b;
     }
     agg_inc(sH, b);
@@ -953,10 +981,10 @@ static int sm_count() {
 }
 
 static size_t k1_smem(const PassArgs& a) {
-  return a.nb_pad_max * (8 + 4) + (a.dir_cells_max + 1) * 2 + 16;
+  return a.nb_pad_max * (8 + 4) + a.aux_bytes + 16;
 }
 static size_t k3_smem(const PassArgs& a) {
-  return a.nb_pad_max * (8 + 8 + 4 + 4 + 2 * (kTPB / 32)) + kTile * (8 + 2) + (a.dir_cells_max + 1) * 2 + 16;
+  return a.nb_pad_max * (8 + 4 + 4 + 2 * (kTPB / 32)) + kTile * (8 + 2) + 16;
 }
 
 void launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
@@ -1050,9 +1078,10 @@ void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t*
 
 void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs, const uint64_t* keys,
                            uint64_t n, int dt, uint32_t* ids, unsigned long long* hist, uint32_t nb_pad,
-                           uint32_t cells, cudaStream_t st) {
+                           uint32_t cells, cudaStream_t st, const FModel* fm, const FLeaf* fl) {
   if (!n) return;
-  size_t sm = (size_t)nb_pad * 12 + (cells + 1) * 2 + 16;
+  uint32_t aux = (uint32_t)((((cells + 1) * 2 > LS_MAX_FANOUT * 16 ? (cells + 1) * 2 : LS_MAX_FANOUT * 16) + 15) & ~15u);
+  size_t sm = (size_t)nb_pad * 12 + aux + 16;
   static size_t set = 0;
   if (sm > set) {
     cudaFuncSetAttribute(k_table_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1061,7 +1090,8 @@ void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint1
   uint64_t grid = grid_for(n);
   uint64_t cap = (uint64_t)sm_count() * 4;
   if (grid > cap) grid = cap;
-  k_table_classify<<<(unsigned)grid, kTPB, sm, st>>>(plan, pivots, dirs, keys, n, dt, ids, hist, nb_pad, cells);
+  k_table_classify<<<(unsigned)grid, kTPB, sm, st>>>(plan, pivots, dirs, keys, n, dt, ids, hist, nb_pad, cells, fm,
+                                                      fl, aux);
 }
 
 }  // namespace lsg

@@ -20,7 +20,7 @@ LS_OK, LS_EINVAL, LS_ENOMEM, LS_ENAN, LS_ETIMEOUT, LS_ECUDA, LS_ENOTIMPL, LS_EDE
 LS_F64, LS_U64 = 0, 1
 LS_PART_AUTO, LS_PART_LEARNED, LS_PART_SPLITTER = 0, 1, 2
 LS_RECURSE_REFINE_GLOBAL, LS_RECURSE_RETRAIN = 0, 1
-LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT = 0, 1, 2, 3
+LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT, LS_CLASSIFY_GUESS = 0, 1, 2, 3, 4
 LS_DEC_NONE, LS_DEC_LEARNED, LS_DEC_SPLITTER, LS_DEC_SPLITTER_EQ, LS_DEC_HOMOGENEOUS = 0, 1, 2, 3, 4
 LS_MAX_FANOUT = 4096
 LS_MAX_LEVELS = 48

@@ -69,7 +69,8 @@ def test_fit_parity(ctx, dist, n, L):
 
 # ------------------------------------------------------------- classify
 
-@pytest.mark.parametrize("mode", [lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY, lsg.LS_CLASSIFY_TREE])
+@pytest.mark.parametrize("mode", [lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY, lsg.LS_CLASSIFY_TREE,
+                                  lsg.LS_CLASSIFY_GUESS])
 @pytest.mark.parametrize("dist", ["uniform01", "normal", "exponential", "skewed_u64"])
 def test_classify_parity(ctx, dist, mode):
     x = datagen.generate(dist, 300_001, 5)
@@ -86,13 +87,26 @@ def test_classify_parity(ctx, dist, mode):
         assert np.array_equal(gh.cpu().numpy().astype(np.uint64), oh)
 
 
+def test_classify_guess_on_shifted_narrow_keys(ctx):
+    """Keys 1000 + 1e-3 x: the FP32 image cannot resolve them, the exact
+    pivots must still give the FP64 buckets."""
+    x = 1000.0 + 1e-3 * datagen.generate("normal", 200_000, 6)
+    s = np.sort(x[:4000])
+    om, ok = oracle.fit(s, 1000)
+    gm = lsg.Model.from_dict(om.to_dict())
+    for k, g in ((0, 0), (1, 433)):
+        oid, oh = oracle.classify(om, x, 1000, k, g)
+        gid, gh = lsg.ls_classify(ctx, gm, to_dev(x), k=k, g=g, mode=lsg.LS_CLASSIFY_GUESS)
+        assert np.array_equal(gid.cpu().numpy().view(np.uint32), oid)
+
+
 def test_classify_special_keys(ctx):
     """+-0, +-inf, subnormals, keys outside the sample range, u64 near 2^64."""
     s = np.sort(datagen.generate("normal", 5000, 3))
     om, _ = oracle.fit(s, 100)
     gm = lsg.Model.from_dict(om.to_dict())
     x = np.array([-np.inf, -1e308, -7.0, -0.0, 0.0, 5e-324, -5e-324, 1e-300, 3.0, 1e308, np.inf] * 3)
-    for mode in (lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY, lsg.LS_CLASSIFY_TREE):
+    for mode in (lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY, lsg.LS_CLASSIFY_TREE, lsg.LS_CLASSIFY_GUESS):
         gid, _ = lsg.ls_classify(ctx, gm, to_dev(x), mode=mode)
         oid, _ = oracle.classify(om, x, 100)
         assert np.array_equal(gid.cpu().numpy().view(np.uint32), oid)
@@ -100,7 +114,7 @@ def test_classify_special_keys(ctx):
     om, _ = oracle.fit(u, 64)
     gm = lsg.Model.from_dict(om.to_dict())
     y = np.array([0, 1, 2**53, 2**53 + 1, 2**63, 2**64 - 2, 2**64 - 1], dtype=np.uint64)
-    for mode in (lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY):
+    for mode in (lsg.LS_CLASSIFY_DIRECT, lsg.LS_CLASSIFY_DIRECTORY, lsg.LS_CLASSIFY_GUESS):
         gid, _ = lsg.ls_classify(ctx, gm, to_dev(y), mode=mode)
         oid, _ = oracle.classify(om, y, 64)
         assert np.array_equal(gid.cpu().numpy().view(np.uint32), oid)
@@ -158,7 +172,8 @@ def test_sort_parity_u64_duplicates(ctx, dist):
                                 dict(partitioner=oracle.PART_LEARNED, fanout=2, basecase_threshold=16),
                                 dict(max_depth=1, basecase_threshold=16),
                                 dict(sample_rate=1.0, partitioner=oracle.PART_LEARNED),
-                                dict(classify_mode=3), dict(classify_mode=1), dict(classify_mode=2)])
+                                dict(classify_mode=3), dict(classify_mode=1), dict(classify_mode=2),
+                                dict(classify_mode=4)])
 def test_sort_parity_options(ctx, kw):
     x = datagen.generate("mix_gauss", 300_000, 4)
     okw = {k: v for k, v in kw.items() if k != "classify_mode"}
