@@ -501,6 +501,61 @@ __device__ __forceinline__ uint32_t bucket_of_value(double v, double Bg, uint32_
   return clamp_index(t, B - 1);
 }
 
+// Leaf the root routes ord u to (the model clamps the key to [xmin, xmax]).
+__device__ __forceinline__ uint32_t leaf_of_ord(const DModel& m, uint64_t u, int dt) {
+  double x = ord_value(u, dt);
+  double xc = dmax(x, m.xmin);
+  xc = dmin(xc, m.xmax);
+  return root_leaf(m, xc);
+}
+
+// Smallest u in (lo, hi] routed to leaf >= l, given leaf_of(lo) < l <= leaf_of(hi):
+// invert the linear root for a guess, gallop to bracket it, bisect.  Root
+// evaluations are a third of a full model evaluation.
+__device__ uint64_t root_boundary(const DModel& m, uint32_t l, int dt, uint64_t lo, uint64_t hi) {
+  uint64_t L = lo, H = hi;  // leaf_of(L) < l <= leaf_of(H)
+  if (m.ra > 0.0) {
+    double xr = m.rx0 + ((double)l / (double)m.L - m.rb) / m.ra;
+    double xl = ord_value(lo, dt), xh = ord_value(hi, dt);
+    if (xr > xl && xr < xh) {
+      uint64_t g;
+      if (dt) g = xr >= 18446744073709549568.0 ? ~0ull : (uint64_t)xr;
+      else g = ord_of((uint64_t)__double_as_longlong(xr), 0);
+      if (g > L && g < H) {
+        if (leaf_of_ord(m, g, dt) >= l) {
+          H = g;
+          for (uint64_t step = 1; step <= (1ull << 20); step <<= 1) {
+            uint64_t c = H - L > step ? H - step : L;
+            if (c == L) break;
+            if (leaf_of_ord(m, c, dt) < l) {
+              L = c;
+              break;
+            }
+            H = c;
+          }
+        } else {
+          L = g;
+          for (uint64_t step = 1; step <= (1ull << 20); step <<= 1) {
+            uint64_t c = H - L > step ? L + step : H;
+            if (c == H) break;
+            if (leaf_of_ord(m, c, dt) >= l) {
+              H = c;
+              break;
+            }
+            L = c;
+          }
+        }
+      }
+    }
+  }
+  for (int it = 0; it < 70 && H - L > 1; ++it) {
+    uint64_t mid = L + ((H - L) >> 1);
+    if (leaf_of_ord(m, mid, dt) >= l) H = mid;
+    else L = mid;
+  }
+  return H;
+}
+
 __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
                                  uint32_t nb_pad, const DModel* models, const Leaf* leaves,
                                  uint64_t* __restrict__ pivots, RunParams rp) {
@@ -557,7 +612,27 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
       else l1 = mid;
     }
     Leaf lf = lv[l0];
-    if (lf.a > 0.0) {
+    uint32_t lstart = root_leaf(m, xcl);
+    if (!(tF > lf.lo) && l0 > lstart) {
+      // the target is at or below this leaf's floor: F jumps over it where
+      // the root starts routing to leaf l0, so that boundary is the pivot
+      uint64_t u = root_boundary(m, l0, rp.dt, lo, hi);
+      if (u > L && u <= H) {
+        double vu = refine_value(m, lv, u, P, rp.dt);
+        double v2 = refine_value(m, lv, u - 1, P, rp.dt);
+        if (vu >= t && v2 < t) {
+          T[j] = u;
+          return;
+        }
+        if (vu >= t) {
+          H = u;
+          vH = vu;
+        } else {
+          L = u;
+          vL = vu;
+        }
+      }
+    } else if (lf.a > 0.0) {
       double xs = lf.x0 + (tF - lf.b) / lf.a;
       if (xs >= xlo && xs <= xhi) {
         uint64_t u;

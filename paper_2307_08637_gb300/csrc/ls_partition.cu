@@ -714,12 +714,115 @@ __device__ __forceinline__ void warp_sort_span(const Span& s, uint64_t* A, const
   }
 }
 
-__global__ void __launch_bounds__(kTPB) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
+// Model-placed base case for one span of <= 256 keys, done by one warp (the
+// GPU form of LearnedSort 2.0's counting sort by predicted position plus an
+// insertion-sort fix, Sec. 2.2): inside a bucket the keys are close to
+// uniform in ord space, so the linear map (ord - min) / (max - min), read as
+// the top 8 bits of (ord - min) << clz(max - min), places them into 256
+// slots; a counting sort by slot and an insertion sort inside each slot give
+// the exact order.  Spans whose largest slot holds more than kMaxSlot keys
+// (clustered data) return false and take the bitonic network instead.
+constexpr uint32_t kSlots = 256;
+constexpr uint32_t kMaxSlot = 24;
+
+__device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
+                                                 uint64_t* sk, uint32_t* sc) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t* src = s.buf ? Bbuf : A;
+  constexpr int R = kWarpSortMax / 32;
+  uint64_t u[R];
+  unsigned long long mn = ~0ull, mx = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    uint32_t i = lane + 32 * r;
+    u[r] = i < s.n ? ord_of(src[s.lo + i], dt) : 0;
+    if (i < s.n) {
+      mn = u[r] < mn ? u[r] : mn;
+      mx = u[r] > mx ? u[r] : mx;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    unsigned long long o1 = __shfl_xor_sync(0xFFFFFFFFu, mn, d);
+    unsigned long long o2 = __shfl_xor_sync(0xFFFFFFFFu, mx, d);
+    mn = o1 < mn ? o1 : mn;
+    mx = o2 > mx ? o2 : mx;
+  }
+  if (mn == mx) {  // all equal: already sorted; bring home if needed
+    if (s.buf)
+      for (uint32_t i = lane; i < s.n; i += 32) A[s.lo + i] = src[s.lo + i];
+    return true;
+  }
+  const uint32_t sh = __clzll((long long)(mx - mn));
+  for (uint32_t d = lane; d <= kSlots; d += 32) sc[d] = 0;
+  __syncwarp();
+  uint32_t dg[R], rk[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    uint32_t i = lane + 32 * r;
+    dg[r] = (uint32_t)(((u[r] - mn) << sh) >> 56);
+    rk[r] = i < s.n ? atomicAdd(&sc[dg[r]], 1u) : 0u;
+  }
+  __syncwarp();
+  // exclusive scan of the 256 slot counts (8 per lane) + largest slot
+  uint32_t c[8], loc = 0, big = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    c[q] = sc[lane * 8 + q];
+    loc += c[q];
+    big = c[q] > big ? c[q] : big;
+  }
+  uint32_t incl = loc;
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl += o;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, big, d);
+    big = o > big ? o : big;
+  }
+  if (big > kMaxSlot) return false;  // uniform across the warp
+  __syncwarp();
+  uint32_t run = incl - loc;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    sc[lane * 8 + q] = run;  // slot start
+    run += c[q];
+  }
+  if (lane == 31) sc[kSlots] = run;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane + 32 * r < s.n) sk[sc[dg[r]] + rk[r]] = u[r];
+  __syncwarp();
+  // insertion sort inside each slot (lane owns 8 consecutive slots)
+  for (int q = 0; q < 8; ++q) {
+    uint32_t a0 = sc[lane * 8 + q], a1 = sc[lane * 8 + q + 1];
+    for (uint32_t x = a0 + 1; x < a1; ++x) {
+      uint64_t v = sk[x];
+      uint32_t y = x;
+      while (y > a0 && sk[y - 1] > v) {
+        sk[y] = sk[y - 1];
+        --y;
+      }
+      sk[y] = v;
+    }
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < s.n; i += 32) A[s.lo + i] = unord(sk[i], dt);
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(kTPB, 3) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
                                                      int dt) {
+  __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
+  __shared__ uint32_t s_cnt[kTPB / 32][kSlots + 1];
+  const unsigned wid = threadIdx.x >> 5;
   uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
   for (; w < n; w += nw) {
     Span s = spans[w];
+    if (s.n >= 16 && warp_placed_sort(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid])) continue;
     if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
     else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
     else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
