@@ -117,11 +117,11 @@ struct Layout {
   uint64_t n = 0;
   uint32_t L = 0, nbc = 0, cells = 0;
   uint64_t icap = 0, scap = 0, mcap = 0, base_cap = 0, large_cap = 0, copy_cap = 0, fb_cap = 0;
-  uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0;
+  uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0, seg_cap = 0;
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_incl, o_chunkctr, o_fmodels, o_fleaves, o_ids;
+      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_chunkctr, o_fmodels, o_fleaves, o_ids;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
@@ -182,7 +182,9 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
   l.o_stats = take(LS_MAX_LEVELS * sizeof(DevLevelStats));
   l.o_ctr = take(sizeof(LevelCounters));
   l.o_agg = take(l.chunk_cap * l.nbc * 4);
-  l.o_incl = take(l.chunk_cap * l.nbc * 8);
+  l.o_excl = take(l.chunk_cap * l.nbc * 8);
+  l.seg_cap = l.chunk_cap / kSegChunks + kBatchItems + 8;
+  l.o_segs = take(l.seg_cap * sizeof(ChunkSeg));
   l.o_chunkctr = take(8);
   l.misc_bytes = 16 * (kBatchItems + 8) * 8;
   l.o_misc = take(l.misc_bytes);
@@ -312,8 +314,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
     pl.cnt_off = (uint64_t)i * L.nbc;
     pl.tab_off = (uint64_t)i * L.nbc;
     pl.dir_off = (uint64_t)i * (L.cells + 1);
-    pl.minv = ~0ull;
-    pl.maxv = 0;
+    pl.mixed = 0;
     pl.model = -1;
     bool is_fresh = it.kind != KIND_REFINE;
     if (it.kind == KIND_REFINE) {
@@ -481,7 +482,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   s.timer.end();
   // shared memory of the passes is sized by what this batch really uses;
   // fresh items are decided on the device, so read their plans back
-  uint32_t nbp_max = 2;
+  uint32_t nbp_max = 2, cls_mask = 0;
   bool any_dir = false, any_guess = false;
   if (!fresh.empty()) {
     std::vector<Plan> hp(nitems);
@@ -491,12 +492,14 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       nbp_max = std::max(nbp_max, q.nb_pad);
       any_dir |= q.cls == CLS_DIR;
       any_guess |= q.cls == CLS_GUESS;
+      cls_mask |= 1u << q.cls;
     }
   } else {
     for (const Plan& q : plans) {
       nbp_max = std::max(nbp_max, q.nb_pad);
       any_dir |= q.cls == CLS_DIR;
       any_guess |= q.cls == CLS_GUESS;
+      cls_mask |= 1u << q.cls;
     }
   }
   uint32_t aux = 16;
@@ -511,7 +514,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.nchunks = tiles;
   if (tiles > L.chunk_cap) return LS_ENOMEM;
   pa.agg = at<uint32_t>(s.ws, L.o_agg);
-  pa.incl = at<unsigned long long>(s.ws, L.o_incl);
+  pa.excl = at<unsigned long long>(s.ws, L.o_excl);
   pa.chunk_ctr = at<unsigned long long>(s.ws, L.o_chunkctr);
   pa.keysA = s.A;
   pa.keysB = s.Bb;
@@ -530,13 +533,13 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
   pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
   pa.aux_bytes = aux;
+  pa.cls_mask = cls_mask;
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
   uint64_t batch_keys = 0;
   for (uint32_t i = 0; i < nitems; ++i) batch_keys += its[i].n;
   CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(pa.incl, 0, tiles * L.nbc * sizeof(unsigned long long), st));
   s.timer.begin(LS_PASS_CLASSIFY, batch_keys);
-  launch_classify_hist(pa, s.rp, st);
+  s.launches += launch_classify_hist(pa, s.rp, st);
   s.timer.end();
 
   ChildArgs ca;
@@ -558,20 +561,42 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   ca.fallback_cap = L.fb_cap;
   ca.ctr = at<LevelCounters>(s.ws, L.o_ctr);
   ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
+  // per-chunk prefixes of the K1 counts, in runs of kSegChunks chunks
+  std::vector<ChunkSeg> segs;
+  bool multi = false;
+  for (uint32_t i = 0; i < nitems; ++i) {
+    uint64_t cb = plans[i].chunk_begin, nc = (its[i].n + kChunkKeys - 1) / kChunkKeys;
+    uint32_t first = (uint32_t)segs.size();
+    multi |= nc > kSegChunks;
+    for (uint64_t c = 0; c < nc; c += kSegChunks) {
+      ChunkSeg g;
+      g.c0 = cb + c;
+      g.nch = (uint32_t)std::min<uint64_t>(kSegChunks, nc - c);
+      g.plan = i;
+      g.first = first;
+      g.pad = 0;
+      segs.push_back(g);
+    }
+  }
+  if (segs.size() > L.seg_cap) return LS_ENOMEM;
+  ChunkSeg* d_segs = at<ChunkSeg>(s.ws, L.o_segs);
+  if (!segs.empty())
+    CK(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(ChunkSeg), cudaMemcpyHostToDevice, st));
   s.timer.begin(LS_PASS_CHILDREN, 0);
+  s.launches += launch_chunk_prefix(d_segs, (uint32_t)segs.size(), multi, d_plans, pa.agg, pa.excl, nbp_max, st);
   launch_children(ca, s.rp, st);
   s.timer.end();
   s.timer.begin(LS_PASS_SCATTER, batch_keys);
   launch_scatter(pa, s.rp, st);
   s.timer.end();
-  s.launches += 3;
+  s.launches += tiles ? 2 : 1;
   CK(cudaGetLastError());
 
   if (record_root && stats) {
     Plan rp0;
     CK(cudaMemcpyAsync(&rp0, d_plans, sizeof(Plan), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (rp0.minv == rp0.maxv) {
+    if (its[0].n > 0 && !rp0.mixed) {
       // homogeneity is checked before any model is built (Sec. 2.2): the
       // sample the device drew speculatively is not part of the decision
       stats->root_decision = LS_DEC_HOMOGENEOUS;
@@ -590,7 +615,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
     CK(cudaStreamSynchronize(st));
     for (uint32_t i = 0; i < nitems; ++i) {
       if (its[i].level != 0 || its[i].segment >= s.nseg) continue;
-      s.seg_decision[its[i].segment] = (hp[i].minv == hp[i].maxv) ? LS_DEC_HOMOGENEOUS : hp[i].decision;
+      s.seg_decision[its[i].segment] = (its[i].n > 0 && !hp[i].mixed) ? LS_DEC_HOMOGENEOUS : hp[i].decision;
     }
   }
   return LS_OK;
@@ -952,7 +977,7 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
   pl.model = 0;
   pl.P = (double)q.fanout;
   pl.nb_pad = pow2ceil(q.fanout);
-  pl.minv = ~0ull;
+  pl.mixed = 0;
   Item* d_items = at<Item>(ws, lay.o_cur);
   Plan* d_plans = at<Plan>(ws, lay.o_plans);
   uint64_t* misc = at<uint64_t>(ws, lay.o_misc);

@@ -26,7 +26,6 @@ constexpr uint32_t kSortChunk = 2048;                 // segmented sample sort c
 constexpr uint32_t kTileKeys = 4096;                  // keys per partition tile (256 threads x 16)
 constexpr uint32_t kChunkTiles = 16;                  // tiles per chunk (one lookback unit)
 constexpr uint64_t kChunkKeys = (uint64_t)kTileKeys * kChunkTiles;
-constexpr unsigned long long kReady = 1ull << 63;     // inclusive-prefix flag of a chunk
 
 enum : uint8_t { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2 };
 enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2, CLS_GUESS = 3 };
@@ -80,7 +79,9 @@ struct Plan {
   uint64_t dir_off;     // offset in the directory pool
   uint64_t dir_lo;      // ord at directory cell 0
   uint64_t dir_hi;      // last pivot; keys >= dir_hi are in bucket kmax
-  unsigned long long minv, maxv;  // K1: smallest / largest ord in the item
+  unsigned int mixed;   // K1: 1 when some key of the item differs from its first key
+  unsigned int pad0;
+  unsigned long long pad1;
   unsigned long long dups;        // fresh: sample duplicates
   unsigned long long imb;         // fresh: largest sample bucket under the RMI
   double P, Bg;         // refine scale B^(k+1) and offset B g

@@ -131,18 +131,34 @@ struct PassArgs {
   const FModel* fmodels;
   const FLeaf* fleaves;
   uint32_t aux_bytes;           // shared-memory bytes for a directory or FP32 leaves
+  uint32_t cls_mask;            // bit c set when some item of the batch uses classifier c
   uint16_t* ids;                // per key (same offsets as the keys): bucket id written by K1, read by K3
   unsigned long long* counts;   // per plan: nb counts
   unsigned long long* cursors;  // per plan: nb bucket bases in the destination
   uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
-  unsigned long long* incl;     // per chunk: inclusive prefixes | kReady (K3)
+  unsigned long long* excl;     // per chunk: keys of each bucket in the item's earlier chunks
   unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
   unsigned int* status;         // device status word
   int check_nan;
   uint32_t nb_pad_max;
   uint32_t dir_cells_max;
 };
-void launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st);
+int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st);  // returns launches
+
+// A run of at most kSegChunks consecutive chunks of one item.
+constexpr uint32_t kSegChunks = 16;
+struct ChunkSeg {
+  uint64_t c0;     // first chunk (global index)
+  uint32_t nch;    // chunks in the run
+  uint32_t plan;   // owning item / plan
+  uint32_t first;  // index of the item's first run
+  uint32_t pad;
+};
+// Per-chunk exclusive prefixes of the K1 counts within each item: one pass
+// per run, then (when some item spans several runs) the runs' carries.
+// Returns launches.
+int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, bool multi, const Plan* plans, uint32_t* agg,
+                        unsigned long long* excl, uint32_t nbp, cudaStream_t st);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
 
 struct ChildArgs {

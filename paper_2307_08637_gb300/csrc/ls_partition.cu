@@ -12,6 +12,8 @@
 //       bitonic sort (<= 8192 keys); fallback merge sort past max_depth.
 #include <cstdio>
 
+#include <type_traits>
+
 #include "ls_kernels.h"
 
 namespace lsg {
@@ -60,23 +62,6 @@ struct Cls {
   uint8_t agg;  // warp-aggregate histogram increments (splitters: duplicates collide)
 };
 
-__device__ __forceinline__ uint32_t classify_key(uint64_t bits, const Cls& c, const uint64_t* sT, const void* sAux,
-                                                 const DModel* models, const Leaf* leaves, int dt) {
-  if (c.cls == CLS_DIRECT) {
-    const DModel& m = models[c.model];
-    return refine_id(m, leaves + m.leaf_off, key_value(bits, dt), c.P, c.Bg, c.B);
-  }
-  uint64_t u = ord_of(bits, dt);
-  if (c.cls == CLS_GUESS) {
-    uint32_t gb = guess_bucket(c.fm, static_cast<const FLeaf*>(sAux), c.Pf, c.Bgf, c.kmax, bits, dt);
-    return fix_bucket(sT, c.nb_pad, c.kmax, gb, u);
-  }
-  uint32_t b = (c.cls == CLS_DIR)
-                   ? pivot_count_dir(sT, static_cast<const uint16_t*>(sAux), c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
-                   : pivot_count(sT, c.nb_pad, u);
-  return b < c.kmax ? b : c.kmax;
-}
-
 // Load item pi's classifier into shared memory (all threads).
 __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, void* sAux) {
   const Plan& pl = a.plans[pi];
@@ -113,9 +98,110 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
 
 // ------------------------------------------------------------------ K1
 
-// Classify every key of every chunk, histogram per chunk in shared memory;
-// write the chunk's bucket counts (dense row, used by K3's lookback), add
-// them to the item's totals, and track the item's min / max ord.
+// Exact bucket #{j <= kmax : T[j] <= u} - 1 from a guess g in [0, kmax]
+// that is usually right or one off: the two table entries around g are read
+// together and decide -1 / 0 / +1; a third read confirms the step, and only
+// a guess two or more off takes the full search.  T[0] <= every key of the
+// item, so a guess can be too high only when g >= 1.
+__device__ __forceinline__ uint32_t fix_guess(const uint64_t* __restrict__ T, uint32_t nb_pad, uint32_t kmax,
+                                              uint32_t g, uint64_t u) {
+  const uint32_t g1 = g < kmax ? g + 1 : kmax;
+  const uint64_t A = T[g], B1 = T[g1];
+  const bool lo = A > u;
+  const bool hi = g < kmax && B1 <= u;
+  const uint32_t g2 = g1 < kmax ? g1 + 1 : kmax;
+  const uint64_t C = T[lo ? (g ? g - 1 : 0) : g2];
+  const bool far = lo ? (g == 0 || C > u) : (hi && g1 < kmax && C <= u);
+  uint32_t b = g - (uint32_t)lo + (uint32_t)hi;
+  if (far) {
+    b = pivot_count(T, nb_pad, u);
+    b = b < kmax ? b : kmax;
+  }
+  return b;
+}
+
+// Bucket of one key for a classifier kind and key type known at compile time.
+template <int CLS, int DT>
+__device__ __forceinline__ uint32_t classify_as(uint64_t bits, const Cls& c, const uint64_t* sT, const void* sAux,
+                                                const DModel* models, const Leaf* leaves) {
+  if (CLS == CLS_DIRECT) {
+    const DModel& m = models[c.model];
+    return refine_id(m, leaves + m.leaf_off, key_value(bits, DT), c.P, c.Bg, c.B);
+  }
+  const uint64_t u = ord_of(bits, DT);
+  if (CLS == CLS_GUESS) {
+    const uint32_t g = guess_bucket(c.fm, static_cast<const FLeaf*>(sAux), c.Pf, c.Bgf, c.kmax, bits, DT);
+    return fix_guess(sT, c.nb_pad, c.kmax, g, u);
+  }
+  const uint32_t b = (CLS == CLS_DIR)
+                         ? pivot_count_dir(sT, static_cast<const uint16_t*>(sAux), c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
+                         : pivot_count(sT, c.nb_pad, u);
+  return b < c.kmax ? b : c.kmax;
+}
+
+// Histogram increment that stays cheap when a warp's keys all share one
+// bucket (duplicates under equality buckets): one add of the lane count.
+__device__ __forceinline__ void hist_add(uint32_t* sH, uint32_t b, bool agg) {
+  if (agg) {
+    const unsigned act = __activemask();
+    const uint32_t lo = __reduce_min_sync(act, b), hi = __reduce_max_sync(act, b);
+    if (lo == hi) {
+      if ((threadIdx.x & 31) == (unsigned)(__ffs(act) - 1) && b != 0xFFFFFFFFu) atomicAdd(&sH[b], (uint32_t)__popc(act));
+      return;
+    }
+  }
+  if (b != 0xFFFFFFFFu) atomicAdd(&sH[b], 1u);
+}
+
+// One chunk of K1: classify, store ids, histogram; OR every key's bits into
+// `diff` against the item's first key (all equal <=> the item is
+// homogeneous) and, when NANCHK, flag NaNs (|bits| above infinity's).
+template <int CLS, int DT, bool NANCHK>
+__device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const uint64_t* sT, const void* sD,
+                                         uint32_t* sH, const uint64_t* src, uint16_t* idout, uint64_t clen,
+                                         uint64_t first, uint64_t& diff, bool& nan) {
+  constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
+    const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+    const uint64_t* s = src + t0 + threadIdx.x;
+    uint16_t* d = idout + t0 + threadIdx.x;
+    if (len == kTile) {
+      uint64_t v[kKPT];
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) v[k] = s[k * kTPB];
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) {
+        const uint64_t bits = v[k];
+        if (NANCHK) nan |= (bits & kAbs) > kInf;
+        diff |= bits ^ first;
+        const uint32_t b = classify_as<CLS, DT>(bits, c, sT, sD, a.models, a.leaves);
+        d[k * kTPB] = (uint16_t)b;
+        hist_add(sH, b, c.agg);
+      }
+    } else {
+      for (int k = 0; k < kKPT; ++k) {
+        const uint32_t idx = k * kTPB + threadIdx.x;
+        uint32_t b = 0xFFFFFFFFu;
+        if (idx < len) {
+          const uint64_t bits = s[k * kTPB];
+          if (NANCHK) nan |= (bits & kAbs) > kInf;
+          diff |= bits ^ first;
+          b = classify_as<CLS, DT>(bits, c, sT, sD, a.models, a.leaves);
+          d[k * kTPB] = (uint16_t)b;
+        }
+        hist_add(sH, b, c.agg);
+      }
+    }
+  }
+}
+
+// Classify every key of every chunk whose item uses classifier CLS,
+// histogram per chunk in shared memory; write the chunk's bucket counts
+// (dense row, read by the chunk-prefix kernels), add them to the item's
+// totals, store each key's bucket id, and flag items that are not
+// homogeneous.  One kernel per classifier kind, key type and NaN check keeps
+// each instance's registers and instructions to what it needs.
+template <int CLS, int DT, bool NANCHK>
 __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
@@ -126,7 +212,8 @@ __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams
   Cls c;
   bool nan = false;
   for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
-    uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    const uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    if (a.plans[pi].cls != CLS) continue;  // uniform across the block
     if (pi != cur) {
       __syncthreads();
       load_cls(a, rp, pi, c, sT, sD);
@@ -135,216 +222,302 @@ __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams
     }
     const Item& it = a.items[pi];
     const Plan& pl = a.plans[pi];
-    uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
-    uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
-    const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
-    uint16_t* idout = a.ids + it.lo + c0;
-    unsigned long long mn = ~0ull, mx = 0;
-    for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
-      uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
-      uint64_t v[kKPT];
-#pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
-        uint32_t idx = k * kTPB + threadIdx.x;
-        v[k] = idx < len ? src[t0 + idx] : 0;
-      }
-#pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
-        uint32_t idx = k * kTPB + threadIdx.x;
-        uint32_t b = 0xFFFFFFFFu;
-        if (idx < len) {
-          uint64_t bits = v[k];
-          if (a.check_nan && (bits & 0x7FF0000000000000ull) == 0x7FF0000000000000ull &&
-              (bits & 0x000FFFFFFFFFFFFFull))
-            nan = true;
-          uint64_t u = ord_of(bits, rp.dt);
-          mn = u < mn ? u : mn;
-          mx = u > mx ? u : mx;
-          b = classify_key(bits, c, sT, sD, a.models, a.leaves, rp.dt);
-          idout[t0 + idx] = (uint16_t)b;
-        }
-        if (c.agg) agg_inc(sH, b);
-        else if (b != 0xFFFFFFFFu) atomicAdd(&sH[b], 1u);
-      }
-    }
+    const uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
+    const uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t* keys = it.buf ? a.keysB : a.keysA;
+    uint64_t diff = 0;
+    k1_chunk<CLS, DT, NANCHK>(a, c, sT, sD, sH, keys + it.lo + c0, a.ids + it.lo + c0, clen, keys[it.lo], diff, nan);
     __syncthreads();
     uint32_t* row = a.agg + ch * a.nb_pad_max;
     for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) {
-      uint32_t h = sH[j];
+      const uint32_t h = sH[j];
       row[j] = h;
       if (h) {
         atomicAdd(&a.counts[pl.cnt_off + j], (unsigned long long)h);
         sH[j] = 0;
       }
     }
-    for (int d = 16; d > 0; d >>= 1) {
-      unsigned long long o1 = __shfl_down_sync(0xFFFFFFFFu, mn, d);
-      unsigned long long o2 = __shfl_down_sync(0xFFFFFFFFu, mx, d);
-      mn = o1 < mn ? o1 : mn;
-      mx = o2 > mx ? o2 : mx;
-    }
-    if ((threadIdx.x & 31) == 0) {
-      if (mn != ~0ull) atomicMin(&a.plans[pi].minv, mn);
-      atomicMax(&a.plans[pi].maxv, mx);
-    }
+    if (__any_sync(0xFFFFFFFFu, diff != 0) && (threadIdx.x & 31) == 0 && !a.plans[pi].mixed)
+      atomicExch(&a.plans[pi].mixed, 1u);
     __syncthreads();
   }
-  if (__syncthreads_or(nan ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_ENAN);
+  if (NANCHK && __syncthreads_or(nan ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_ENAN);
 }
 
 // ------------------------------------------------------------------ K3
 
-// Stable scatter.  Chunks are taken in order from a global counter.  A
-// chunk's per-bucket prefix (keys of the same bucket in earlier chunks of
-// the item) comes from a decoupled lookback over the chunk rows: a
-// predecessor's inclusive prefix if it has published one, else its K1
-// count -- K1 counts always exist, so the lookback never waits.  Inside a
-// chunk the tiles are processed in order; inside a tile each warp owns 512
-// consecutive keys and ranks them in order with warp-private counters, so
-// every key keeps its relative order within its bucket (the stable counting
-// sort of the partitioning step).
+constexpr uint32_t kWarps = kTPB / 32;
+constexpr uint32_t kWarpKeys = kTile / kWarps;  // keys of a tile ranked by one warp
+constexpr uint32_t kMaskBuckets = kTile * 8 / (kWarps * 4);  // peer masks fit in the stage buffer
+
+// Rank of this lane's key among the keys of the same id that the warp has
+// seen so far (its earlier steps, then lower lanes of this step), and the
+// advance of the warp's counter for that id.  The lanes holding the same id
+// are found either with a per-warp word per id in shared memory (each lane
+// ORs its bit in, reads the word back and takes its bit out again, so the
+// words are zero between steps; MASK) or with the warp match instruction,
+// whose cost grows with the number of distinct ids in the warp.  FULL: every
+// lane holds a key; otherwise lanes with id 0xFFFF take no part.  Branch
+// free: every lane issues the same shared-memory operations, with operands
+// that change nothing where a lane has nothing to do.
+template <bool MASK, bool FULL>
+__device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t* wm, uint32_t* myc, unsigned lane, uint32_t wsh,
+                                              unsigned lt) {
+  const bool valid = FULL || b != 0xFFFFu;
+  const uint32_t bb = valid ? b : 0u;
+  const unsigned bit = 1u << lane;
+  unsigned p;
+  if constexpr (MASK) {
+    atomicOr(&wm[bb], valid ? bit : 0u);
+    __syncwarp();
+    p = wm[bb];
+    __syncwarp();
+    atomicAnd(&wm[bb], valid ? ~bit : ~0u);
+  } else {
+    p = __match_any_sync(0xFFFFFFFFu, b);
+  }
+  if (!valid) p = 0;
+  const int leader = __ffs(p) - 1;
+  // every lane adds (zero where it is not the leader): no divergent branch
+  const uint32_t old = atomicAdd(&myc[bb], (int)lane == leader ? (uint32_t)__popc(p) << wsh : 0u);
+  return ((__shfl_sync(0xFFFFFFFFu, old, leader & 31) >> wsh) & 0xFFFFu) + __popc(p & lt);
+}
+
+// Stable scatter, one tile of kTile keys at a time.  Chunks are taken in
+// order from a global counter; a chunk's per-bucket start comes from the
+// chunk-prefix kernels (bucket cursor + keys of the bucket in the item's
+// earlier chunks).  Inside a tile each warp owns kWarpKeys consecutive keys
+// and ranks them in order with warp-private counters; a per-bucket prefix
+// over the warps and a scan over the buckets place every key in a staging
+// buffer grouped by bucket, which is written out with runs of consecutive
+// destinations.  Keys keep their relative order within a bucket (the stable
+// counting sort of the partitioning step).  Counters of warps 2i and 2i+1
+// share a word, 16 bits each (a warp ranks at most kWarpKeys keys).
+template <bool MASK>
 __global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int kWarps = kTPB / 32;
   const uint32_t nbp = a.nb_pad_max;
-  uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);     // next destination per bucket
-  uint64_t* stage = sRun + nbp;                           // kTile keys
+  uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);          // next destination per bucket
+  uint64_t* stage = sRun + nbp;                                // kTile keys; warp peer masks while ranking
   uint32_t* sLs = reinterpret_cast<uint32_t*>(stage + kTile);  // tile-local start per bucket
-  uint32_t* sCnt = sLs + nbp;                             // tile count per bucket
-  uint16_t* wcnt = reinterpret_cast<uint16_t*>(sCnt + nbp);  // [kWarps][nbp]
-  uint16_t* sid = wcnt + kWarps * nbp;                    // kTile bucket ids
-  __shared__ uint32_t wsum[kWarps];
-  __shared__ unsigned long long s_chunk;
+  uint32_t* sCnt = sLs + nbp;                                  // tile count per bucket
+  uint32_t* wcnt = sCnt + nbp;                                 // [kWarps/2][nbp] packed warp counters
+  uint16_t* sid = reinterpret_cast<uint16_t*>(wcnt + (kWarps / 2) * nbp);  // bucket of each staged key
+  __shared__ uint32_t wsum[kWarps * 16];
+  __shared__ unsigned long long s_chunk[2];
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint32_t j = threadIdx.x; j < kWarps * nbp; j += blockDim.x) wcnt[j] = 0;
-  for (;;) {
+  const uint32_t wsh = 16 * (wid & 1);
+  uint32_t* myc = wcnt + (wid >> 1) * nbp;
+  uint32_t* wm = reinterpret_cast<uint32_t*>(stage) + wid * nbp;
+  const unsigned lt = (1u << lane) - 1u;
+  for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp; j += kTPB) wcnt[j] = 0;
+  for (uint32_t j = threadIdx.x; j < kTile * 2; j += kTPB) reinterpret_cast<uint32_t*>(stage)[j] = 0;
+  bool oob = false;
+  for (int par = 0;; par ^= 1) {
+    if (threadIdx.x == 0) s_chunk[par] = atomicAdd(a.chunk_ctr, 1ull);
     __syncthreads();
-    if (threadIdx.x == 0) s_chunk = atomicAdd(a.chunk_ctr, 1ull);
-    __syncthreads();
-    uint64_t ch = s_chunk;
+    const uint64_t ch = s_chunk[par];
     if (ch >= a.nchunks) break;
-    uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    const uint32_t pi = find_plan(a.plans, a.nitems, ch);
     const Plan& pl = a.plans[pi];
     if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
     const Item& it = a.items[pi];
     const uint32_t nbk = pl.nb_pad;
-    // lookback: destination of this chunk's first key of each bucket
-    const uint64_t cfirst = pl.chunk_begin;
-    const uint32_t* aggrow = a.agg + ch * nbp;
-    for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-      unsigned long long sum = 0;
-      for (uint64_t c2 = ch; c2-- > cfirst;) {
-        unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(&a.incl[c2 * nbp + b]);
-        if (v & kReady) {
-          sum += v & ~kReady;
-          break;
-        }
-        sum += a.agg[c2 * nbp + b];
-      }
-      a.incl[ch * nbp + b] = kReady | (sum + aggrow[b]);
-      sRun[b] = a.cursors[pl.cnt_off + b] + sum;
+    const unsigned long long* ex = a.excl + ch * nbp;
+    for (uint32_t b = threadIdx.x; b < nbk; b += kTPB) {
+      sRun[b] = a.cursors[pl.cnt_off + b] + ex[b];
+      sCnt[b] = 0;
+      sLs[b] = 0;
     }
-    __threadfence();
-    __syncthreads();
-    uint64_t c0 = (ch - cfirst) * kChunkKeys;
-    uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
+    const uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
     const uint16_t* idin = a.ids + it.lo + c0;
     uint64_t* dst = it.buf ? a.outA : a.outB;
-    bool oob = false;
-    for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
-      uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
-      uint64_t v[kKPT];
-      uint32_t bk[kKPT];
-      uint32_t rk[kKPT];
-      uint16_t* myc = wcnt + wid * nbp;
+    const uint64_t lo = it.lo, n = it.n;
+    const uint32_t Q = (nbk + kTPB - 1) / kTPB;  // bucket ranges of kTPB (at most 16)
+    uint64_t v[kKPT];
+    uint32_t bk[kKPT];
+    auto load_tile = [&](uint64_t t0) {
+      const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+      const uint64_t* s = src + t0 + wid * kWarpKeys + lane;
+      const uint16_t* d = idin + t0 + wid * kWarpKeys + lane;
+      if (len == kTile) {
 #pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
-        uint32_t pos = wid * (32 * kKPT) + k * 32 + lane;
-        v[k] = pos < len ? src[t0 + pos] : 0;
-        bk[k] = pos < len ? (uint32_t)idin[t0 + pos] : 0xFFFFFFFFu;
-      }
-#pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
-        uint32_t b = bk[k];
-        unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
-        int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if ((int)lane == leader && b != 0xFFFFFFFFu) {
-          old = myc[b];
-          myc[b] = (uint16_t)(old + __popc(peers));
+        for (int k = 0; k < kKPT; ++k) {
+          v[k] = s[k * 32];
+          bk[k] = d[k * 32];
         }
-        old = __shfl_sync(0xFFFFFFFFu, old, leader);
-        rk[k] = old + __popc(peers & ((1u << lane) - 1u));
-        bk[k] = b;
-        __syncwarp();
-      }
-      __syncthreads();
-      // per bucket: exclusive prefix over warps (in place) and tile count
-      for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-        uint32_t t = 0;
+      } else {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-          uint32_t x = wcnt[w * nbp + b];
-          wcnt[w * nbp + b] = (uint16_t)t;
-          t += x;
+        for (int k = 0; k < kKPT; ++k) {
+          const uint32_t pos = wid * kWarpKeys + k * 32 + lane;
+          v[k] = pos < len ? s[k * 32] : 0;
+          bk[k] = pos < len ? (uint32_t)d[k * 32] : 0xFFFFu;
         }
-        sCnt[b] = t;
       }
+    };
+    load_tile(0);
+    auto tile = [&](uint64_t t0, uint32_t len, auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      // rank: bk[k] becomes id | (rank among the warp's keys of that id) << 16
+#pragma unroll
+      for (int k = 0; k < kKPT; ++k) bk[k] |= rank_step<MASK, FULL>(bk[k], wm, myc, lane, wsh, lt) << 16;
       __syncthreads();
-      // exclusive scan of tile counts over buckets -> tile-local starts
-      uint32_t per = (nbk + kTPB - 1) / kTPB;
-      uint32_t j0 = threadIdx.x * per;
-      uint32_t loc = 0;
-      for (uint32_t j = j0; j < j0 + per && j < nbk; ++j) loc += sCnt[j];
-      uint32_t incl = loc;
+      // per bucket b = q*kTPB + tid: advance the run by the previous tile's
+      // count, prefix over the warps (in place), tile count; then one scan
+      // over all buckets (ranges q-major, then warps, then lanes)
+      constexpr uint32_t QMAX = MASK ? kMaskBuckets / kTPB : 16;  // bucket ranges of kTPB
+      uint32_t cnt[QMAX];
+#pragma unroll
+      for (uint32_t q = 0; q < QMAX; ++q) {
+        const uint32_t b = q * kTPB + threadIdx.x;
+        cnt[q] = 0;
+        if (q < Q && b < nbk) {
+          sRun[b] += sLs[b] + sCnt[b];  // undo the previous tile's offset, advance past its keys
+          uint32_t t = 0;
+#pragma unroll
+          for (uint32_t w2 = 0; w2 < kWarps / 2; ++w2) {
+            const uint32_t x = wcnt[w2 * nbp + b];
+            const uint32_t t1 = t + (x & 0xFFFFu);
+            wcnt[w2 * nbp + b] = t | (t1 << 16);
+            t = t1 + (x >> 16);
+          }
+          sCnt[b] = t;
+          cnt[q] = t;
+        }
+      }
+      uint32_t inc[QMAX];
+#pragma unroll
+      for (uint32_t q = 0; q < QMAX; ++q) inc[q] = cnt[q];
+#pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= (unsigned)d) incl += o;
-      }
-      if (lane == 31) wsum[wid] = incl;
-      __syncthreads();
-      if (wid == 0) {
-        uint32_t w = lane < (unsigned)kWarps ? wsum[lane] : 0;
-        for (int d = 1; d < 32; d <<= 1) {
-          uint32_t o = __shfl_up_sync(0xFFFFFFFFu, w, d);
-          if (lane >= (unsigned)d) w += o;
+#pragma unroll
+        for (uint32_t q = 0; q < QMAX; ++q) {
+          if (q < Q) {  // uniform
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc[q], d);
+            if (lane >= (unsigned)d) inc[q] += o;
+          }
         }
-        if (lane < (unsigned)kWarps) wsum[lane] = w;
+      }
+#pragma unroll
+      for (uint32_t q = 0; q < QMAX; ++q) {
+        const uint32_t b = q * kTPB + threadIdx.x;
+        if (q < Q) {
+          if (lane == 31) wsum[q * kWarps + wid] = inc[q];
+          if (b < nbk) sLs[b] = inc[q] - cnt[q];  // exclusive within the warp's 32 buckets
+        }
       }
       __syncthreads();
-      uint32_t run = incl - loc + (wid > 0 ? wsum[wid - 1] : 0);
-      for (uint32_t j = j0; j < j0 + per && j < nbk; ++j) {
-        sLs[j] = run;
-        run += sCnt[j];
+      if (wid == 0) {  // scan the Q*kWarps warp totals, 4 per lane
+        uint32_t e[4], s4 = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t idx = lane * 4 + i;
+          e[i] = idx < Q * kWarps ? wsum[idx] : 0u;
+          s4 += e[i];
+        }
+        uint32_t x = s4;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+          if (lane >= (unsigned)d) x += o;
+        }
+        uint32_t run = x - s4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t idx = lane * 4 + i;
+          if (idx < Q * kWarps) wsum[idx] = run;
+          run += e[i];
+        }
       }
       __syncthreads();
+      for (uint32_t q = 0; q < Q; ++q) {
+        const uint32_t b = q * kTPB + threadIdx.x;
+        if (b < nbk) {
+          const uint32_t ls = sLs[b] + wsum[q * kWarps + wid];
+          sLs[b] = ls;
+          sRun[b] -= ls;  // destination of staged position p is sRun[b] + p
+        }
+      }
+      __syncthreads();
+      // stage grouped by bucket (overwrites the peer masks, all zero now);
+      // in a partial tile the empty lanes write a zero key to the last slot,
+      // which no key of the tile uses
 #pragma unroll
       for (int k = 0; k < kKPT; ++k) {
-        if (bk[k] != 0xFFFFFFFFu) {
-          uint32_t p = sLs[bk[k]] + myc[bk[k]] + rk[k];
-          stage[p] = v[k];
-          sid[p] = (uint16_t)bk[k];
-        }
+        const uint32_t b = bk[k] & 0xFFFFu;
+        const bool valid = FULL || b != 0xFFFFu;
+        const uint32_t bb = valid ? b : 0u;
+        uint32_t p = sLs[bb] + ((myc[bb] >> wsh) & 0xFFFFu) + (bk[k] >> 16);
+        if (!FULL && !valid) p = kTile - 1;
+        stage[p] = v[k];
+        sid[p] = (uint16_t)bb;
       }
+      // prefetch the next tile while the staged one is written out
+      if (t0 + kTile < clen) load_tile(t0 + kTile);
       __syncthreads();
-      for (uint32_t p = threadIdx.x; p < len; p += kTPB) {
-        uint32_t b = sid[p];
-        uint64_t o = sRun[b] + (p - sLs[b]);
-        if (o >= it.lo && o < it.lo + it.n) dst[o] = stage[p];
-        else oob = true;  // K1 and K3 disagree: never write outside the item
+      auto put = [&](uint32_t p) {
+        const uint64_t o = sRun[sid[p]] + p;
+        const uint64_t x = stage[p];
+        stage[p] = 0;  // peer masks of the next tile start from zero
+        const bool ok = o - lo < n;  // K1 and K3 disagree: never write outside the item
+        if (ok) dst[o] = x;
+        oob |= !ok;
+      };
+      if constexpr (FULL) {
+#pragma unroll 4
+        for (uint32_t p = threadIdx.x; p < kTile; p += kTPB) put(p);
+      } else {
+        for (uint32_t p = threadIdx.x; p < len; p += kTPB) put(p);
       }
+      for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp / 4; j += kTPB)
+        reinterpret_cast<uint4*>(wcnt)[j] = make_uint4(0, 0, 0, 0);
       __syncthreads();
-      for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-        sRun[b] += sCnt[b];
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) wcnt[w * nbp + b] = 0;
-      }
-      // the next tile's ranking writes the counters this loop clears
-      __syncthreads();
+    };
+    for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
+      const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+      if (len == kTile) tile(t0, len, std::true_type{});
+      else tile(t0, len, std::false_type{});
     }
-    if (oob) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
   }
+  if (__syncthreads_or(oob ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
+}
+
+// ------------------------------------------------------------------ chunk prefixes
+
+// Run pass: for each bucket column, the exclusive running sum of the K1
+// counts over the run's chunks; the run's total replaces the count in the
+// run's first row when the item has several runs (that row is read only by
+// the thread that owns the column, before it is written).
+__global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans, uint32_t* agg,
+                               unsigned long long* __restrict__ excl, uint32_t nbp) {
+  const ChunkSeg sg = segs[blockIdx.x];
+  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= plans[sg.plan].nb_pad) return;
+  uint32_t v[kSegChunks];
+#pragma unroll
+  for (uint32_t j = 0; j < kSegChunks; ++j) v[j] = j < sg.nch ? agg[(sg.c0 + j) * nbp + b] : 0u;
+  unsigned long long run = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kSegChunks; ++j) {
+    if (j < sg.nch) excl[(sg.c0 + j) * nbp + b] = run;
+    run += v[j];
+  }
+  agg[sg.c0 * nbp + b] = (uint32_t)run;  // at most kSegChunks * kChunkKeys
+}
+
+// Carry pass: add the totals of the item's earlier runs.
+__global__ void k_chunk_carry(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans,
+                              const uint32_t* __restrict__ agg, unsigned long long* __restrict__ excl, uint32_t nbp) {
+  const ChunkSeg sg = segs[blockIdx.x];
+  if (blockIdx.x == sg.first) return;
+  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= plans[sg.plan].nb_pad) return;
+  const uint64_t cf = segs[sg.first].c0;
+  unsigned long long carry = 0;
+  for (uint32_t r = sg.first; r < blockIdx.x; ++r) carry += agg[(cf + (uint64_t)(r - sg.first) * kSegChunks) * nbp + b];
+  for (uint32_t j = 0; j < sg.nch; ++j) excl[(sg.c0 + j) * nbp + b] += carry;
 }
 
 // ------------------------------------------------------------------ K2
@@ -420,7 +593,7 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
   DevLevelStats* cs = a.stats + cl;
   uint8_t dest = it.buf ^ 1;
   // Homogeneity check (Sec. 2.2): an all-equal item is already sorted.
-  if (pl.minv == pl.maxv) {
+  if (it.n > 0 && !pl.mixed) {
     if (threadIdx.x == 0) {
       pl.flags |= FLAG_SKIP_SCATTER | FLAG_HOMOGENEOUS;
       atomicAdd(&ls->homogeneous, 1ull);
@@ -722,81 +895,100 @@ __device__ __forceinline__ void warp_sort_span(const Span& s, uint64_t* A, const
 // slots; a counting sort by slot and an insertion sort inside each slot give
 // the exact order.  Spans whose largest slot holds more than kMaxSlot keys
 // (clustered data) return false and take the bitonic network instead.
-constexpr uint32_t kSlots = 256;
+constexpr uint32_t kSlots = 256;  // slots of the largest size class (32 per key register)
 constexpr uint32_t kMaxSlot = 24;
 
+// Exact warp-wide minimum / maximum of one u64 per lane from 32-bit
+// reductions: high words first, then the low words of the lanes that hold
+// the extreme high word.
+__device__ __forceinline__ void warp_minmax_u64(unsigned long long lmin, unsigned long long lmax,
+                                                unsigned long long& mn, unsigned long long& mx) {
+  const uint32_t hmin = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(lmin >> 32));
+  const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)(lmax >> 32));
+  const uint32_t lo_min = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(lmin >> 32) == hmin ? (uint32_t)lmin : ~0u);
+  const uint32_t lo_max = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)(lmax >> 32) == hmax ? (uint32_t)lmax : 0u);
+  mn = ((unsigned long long)hmin << 32) | lo_min;
+  mx = ((unsigned long long)hmax << 32) | lo_max;
+}
+
+// Model-placed counting sort of one span of at most 32*R keys by one warp:
+// each key goes to slot floor((u - min) / (max - min + 1) * 32R) (a linear
+// CDF between the span's extremes), slots are laid out by an exclusive scan
+// of their counts, and an insertion sort inside each slot finishes the job.
+// Returns false (nothing written) when some slot holds more than kMaxSlot
+// keys; the caller then sorts the span with a bitonic network.
+template <int R>
 __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
                                                  uint64_t* sk, uint32_t* sc) {
+  constexpr uint32_t NS = 32 * R, LG = (R == 1 ? 5 : R == 2 ? 6 : R == 4 ? 7 : 8);
+  static_assert((1u << LG) == NS, "slot count");
   const unsigned lane = threadIdx.x & 31;
   const uint64_t* src = s.buf ? Bbuf : A;
-  constexpr int R = kWarpSortMax / 32;
   uint64_t u[R];
-  unsigned long long mn = ~0ull, mx = 0;
+  unsigned long long lmin = ~0ull, lmax = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     uint32_t i = lane + 32 * r;
     u[r] = i < s.n ? ord_of(src[s.lo + i], dt) : 0;
     if (i < s.n) {
-      mn = u[r] < mn ? u[r] : mn;
-      mx = u[r] > mx ? u[r] : mx;
+      lmin = u[r] < lmin ? u[r] : lmin;
+      lmax = u[r] > lmax ? u[r] : lmax;
     }
   }
-  for (int d = 16; d > 0; d >>= 1) {
-    unsigned long long o1 = __shfl_xor_sync(0xFFFFFFFFu, mn, d);
-    unsigned long long o2 = __shfl_xor_sync(0xFFFFFFFFu, mx, d);
-    mn = o1 < mn ? o1 : mn;
-    mx = o2 > mx ? o2 : mx;
-  }
+  unsigned long long mn, mx;
+  warp_minmax_u64(lmin, lmax, mn, mx);
   if (mn == mx) {  // all equal: already sorted; bring home if needed
     if (s.buf)
       for (uint32_t i = lane; i < s.n; i += 32) A[s.lo + i] = src[s.lo + i];
     return true;
   }
   const uint32_t sh = __clzll((long long)(mx - mn));
-  for (uint32_t d = lane; d <= kSlots; d += 32) sc[d] = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) sc[lane + 32 * r] = 0;
   __syncwarp();
   uint32_t dg[R], rk[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     uint32_t i = lane + 32 * r;
-    dg[r] = (uint32_t)(((u[r] - mn) << sh) >> 56);
+    dg[r] = (uint32_t)(((u[r] - mn) << sh) >> (64 - LG));
     rk[r] = i < s.n ? atomicAdd(&sc[dg[r]], 1u) : 0u;
   }
   __syncwarp();
-  // exclusive scan of the 256 slot counts (8 per lane) + largest slot
-  uint32_t c[8], loc = 0, big = 0;
+  // exclusive scan of the slot counts (R consecutive slots per lane) and the
+  // largest slot
+  uint32_t c[R], loc = 0, big = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    c[q] = sc[lane * 8 + q];
+  for (int q = 0; q < R; ++q) {
+    c[q] = sc[lane * R + q];
     loc += c[q];
     big = c[q] > big ? c[q] : big;
   }
   uint32_t incl = loc;
+#pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
     if (lane >= (unsigned)d) incl += o;
   }
-  for (int d = 16; d > 0; d >>= 1) {
-    uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, big, d);
-    big = o > big ? o : big;
-  }
+  big = __reduce_max_sync(0xFFFFFFFFu, big);
   if (big > kMaxSlot) return false;  // uniform across the warp
   __syncwarp();
   uint32_t run = incl - loc;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    sc[lane * 8 + q] = run;  // slot start
+  for (int q = 0; q < R; ++q) {
+    sc[lane * R + q] = run;  // slot start
     run += c[q];
   }
-  if (lane == 31) sc[kSlots] = run;
+  if (lane == 31) sc[NS] = run;
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (lane + 32 * r < s.n) sk[sc[dg[r]] + rk[r]] = u[r];
   __syncwarp();
-  // insertion sort inside each slot (lane owns 8 consecutive slots)
-  for (int q = 0; q < 8; ++q) {
-    uint32_t a0 = sc[lane * 8 + q], a1 = sc[lane * 8 + q + 1];
+  // insertion sort inside each slot (a lane owns R consecutive slots)
+  uint32_t a0 = sc[lane * R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const uint32_t a1 = a0 + c[q];
     for (uint32_t x = a0 + 1; x < a1; ++x) {
       uint64_t v = sk[x];
       uint32_t y = x;
@@ -806,9 +998,14 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
       }
       sk[y] = v;
     }
+    a0 = a1;
   }
   __syncwarp();
-  for (uint32_t i = lane; i < s.n; i += 32) A[s.lo + i] = unord(sk[i], dt);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    uint32_t i = lane + 32 * r;
+    if (i < s.n) A[s.lo + i] = unord(sk[i], dt);
+  }
   __syncwarp();
   return true;
 }
@@ -822,7 +1019,14 @@ __global__ void __launch_bounds__(kTPB, 3) k_base_small(const Span* spans, uint6
   uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
   for (; w < n; w += nw) {
     Span s = spans[w];
-    if (s.n >= 16 && warp_placed_sort(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid])) continue;
+    bool done = false;
+    if (s.n >= 16) {
+      if (s.n <= 32) done = warp_placed_sort<1>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
+      else if (s.n <= 64) done = warp_placed_sort<2>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
+      else if (s.n <= 128) done = warp_placed_sort<4>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
+      else done = warp_placed_sort<8>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
+    }
+    if (done) continue;
     if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
     else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
     else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
@@ -1083,53 +1287,89 @@ static int sm_count() {
   return sms;
 }
 
+// Raise a kernel's dynamic shared memory limit once per device.
+template <typename F>
+static void allow_smem(F* f, size_t sm, size_t* set) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (sm > set[dev]) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set[dev] = sm;
+  }
+}
+
 static size_t k1_smem(const PassArgs& a) {
   return a.nb_pad_max * (8 + 4) + a.aux_bytes + 16;
 }
 static size_t k3_smem(const PassArgs& a) {
-  return a.nb_pad_max * (8 + 4 + 4 + 2 * (kTPB / 32)) + kTile * (8 + 2) + 16;
+  return a.nb_pad_max * (8 + 4 + 4 + 2 * kWarps) + kTile * (8 + 2) + 16;
 }
 
-void launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
-  if (!a.nchunks) return;
+template <int CLS, int DT, bool NANCHK>
+static void launch_k1(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  static size_t set[64] = {};
   size_t sm = k1_smem(a);
-  static size_t set = 0;
-  if (sm > set) {
-    cudaFuncSetAttribute(k_classify_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = sm;
-  }
+  allow_smem(k_classify_hist<CLS, DT, NANCHK>, sm, set);
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_classify_hist, kTPB, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_classify_hist<CLS, DT, NANCHK>, kTPB, sm);
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_classify_hist<<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  k_classify_hist<CLS, DT, NANCHK><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+}
+
+template <int CLS>
+static void launch_k1_cls(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (rp.dt == LS_U64) launch_k1<CLS, LS_U64, false>(a, rp, st);
+  else if (a.check_nan) launch_k1<CLS, LS_F64, true>(a, rp, st);
+  else launch_k1<CLS, LS_F64, false>(a, rp, st);
+}
+
+int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (!a.nchunks) return 0;
+  int n = 0;
+  if (a.cls_mask & (1u << CLS_GUESS)) launch_k1_cls<CLS_GUESS>(a, rp, st), ++n;
+  if (a.cls_mask & (1u << CLS_TREE)) launch_k1_cls<CLS_TREE>(a, rp, st), ++n;
+  if (a.cls_mask & (1u << CLS_DIR)) launch_k1_cls<CLS_DIR>(a, rp, st), ++n;
+  if (a.cls_mask & (1u << CLS_DIRECT)) launch_k1_cls<CLS_DIRECT>(a, rp, st), ++n;
+  return n;
+}
+
+int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, bool multi, const Plan* plans, uint32_t* agg,
+                        unsigned long long* excl, uint32_t nbp, cudaStream_t st) {
+  if (!nsegs) return 0;
+  dim3 grid(nsegs, (nbp + kTPB - 1) / kTPB);
+  k_chunk_prefix<<<grid, kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  if (!multi) return 1;
+  k_chunk_carry<<<grid, kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  return 2;
+}
+
+template <bool MASK>
+static void launch_k3(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  size_t sm = k3_smem(a);
+  static size_t set[64] = {};
+  allow_smem(k_scatter<MASK>, sm, set);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MASK>, kTPB, sm);
+  if (per < 1) per = 1;
+  uint64_t grid = (uint64_t)sm_count() * per;
+  if (grid > a.nchunks) grid = a.nchunks;
+  k_scatter<MASK><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
 }
 
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (!a.nchunks) return;
-  size_t sm = k3_smem(a);
-  static size_t set = 0;
-  if (sm > set) {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = sm;
-  }
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter, kTPB, sm);
-  if (per < 1) per = 1;
-  uint64_t grid = (uint64_t)sm_count() * per;
-  if (grid > a.nchunks) grid = a.nchunks;
-  k_scatter<<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  if (a.nb_pad_max <= kMaskBuckets) launch_k3<true>(a, rp, st);
+  else launch_k3<false>(a, rp, st);
 }
 
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   if (!a.nitems) return;
   size_t sm = (size_t)(LS_MAX_FANOUT + 1) * 8 + LS_MAX_FANOUT + 16;
-  static bool set = false;
-  if (!set) {
-    cudaFuncSetAttribute(k_children, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = true;
-  }
+  static size_t set[64] = {};
+  allow_smem(k_children, sm, set);
   k_children<<<a.nitems, 1024, sm, st>>>(a, rp);
 }
 
@@ -1148,11 +1388,8 @@ void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t
   uint32_t P = 2;
   while (P < max_len) P <<= 1;
   size_t sm = (size_t)P * 8;
-  static size_t set = 0;
-  if (sm > set) {
-    cudaFuncSetAttribute(k_base_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = sm;
-  }
+  static size_t set[64] = {};
+  allow_smem(k_base_large, sm, set);
   uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
   uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
   k_base_large<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, dt);
@@ -1185,11 +1422,8 @@ void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint1
   if (!n) return;
   uint32_t aux = (uint32_t)((((cells + 1) * 2 > LS_MAX_FANOUT * 16 ? (cells + 1) * 2 : LS_MAX_FANOUT * 16) + 15) & ~15u);
   size_t sm = (size_t)nb_pad * 12 + aux + 16;
-  static size_t set = 0;
-  if (sm > set) {
-    cudaFuncSetAttribute(k_table_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = sm;
-  }
+  static size_t set[64] = {};
+  allow_smem(k_table_classify, sm, set);
   uint64_t grid = grid_for(n);
   uint64_t cap = (uint64_t)sm_count() * 4;
   if (grid > cap) grid = cap;
