@@ -451,12 +451,14 @@ __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64
     uint64_t mid;
     bool interp = (it & 3) != 3 && vH > vL;
     if (interp) {
-      double frac = (t - vL) / (vH - vL);
-      double off = frac * (double)span;
-      uint64_t o;
-      if (!(off >= 1.0)) o = 1;
-      else if (off >= (double)(span - 1)) o = span - 1;
-      else o = (uint64_t)off;
+      // the estimate only steers the search (every probe is evaluated
+      // exactly), so the fraction is formed in FP32 and applied in fixed
+      // point: o = span * frac with frac in [0, 1) as a 32-bit fraction
+      const float frac = fminf(fmaxf((float)__dsub_rn(t, vL) / (float)__dsub_rn(vH, vL), 0.0f), 0.99999994f);
+      const uint64_t f32 = (uint64_t)(frac * 4294967296.0f);
+      uint64_t o = (span >> 32) * f32 + (((span & 0xFFFFFFFFull) * f32) >> 32);
+      if (o < 1) o = 1;
+      if (o > span - 1) o = span - 1;
       mid = L + o;
     } else {
       mid = L + (span >> 1);
@@ -556,11 +558,46 @@ __device__ uint64_t root_boundary(const DModel& m, uint32_t l, int dt, uint64_t 
   return H;
 }
 
+// Per-item quantities every pivot of the item needs.
+struct PivotPrep {
+  double vlo, vhi, xlo, xhi, invP;
+  uint32_t kmin, kmax, l0, l1;
+};
+
+__device__ __forceinline__ void pivot_prep(const DModel& m, const Leaf* lv, const Item& it, double P, double Bg,
+                                           uint32_t B, int dt, PivotPrep& q) {
+  q.vlo = refine_value(m, lv, it.ord_lo, P, dt);
+  q.vhi = refine_value(m, lv, it.ord_hi, P, dt);
+  q.kmin = bucket_of_value(q.vlo, Bg, B);
+  q.kmax = bucket_of_value(q.vhi, Bg, B);
+  q.xlo = ord_value(it.ord_lo, dt);
+  q.xhi = ord_value(it.ord_hi, dt);
+  q.l0 = root_leaf(m, dmin(dmax(q.xlo, m.xmin), m.xmax));
+  q.l1 = root_leaf(m, dmin(dmax(q.xhi, m.xmin), m.xmax));
+  q.invP = 1.0 / P;
+}
+
+// One thread per pivot slot j of each listed item.  When a block lies inside
+// one item (nb_pad a multiple of the block size) the item's end values are
+// evaluated once per block, else by every thread.
 __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
                                  uint32_t nb_pad, const DModel* models, const Leaf* leaves,
                                  uint64_t* __restrict__ pivots, RunParams rp) {
-  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= (uint64_t)nlist * nb_pad) return;
+  __shared__ PivotPrep s_prep;
+  const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const bool shared_prep = nb_pad % blockDim.x == 0;
+  if (shared_prep) {  // uniform: the whole block is in range and in one item
+    if (g >= (uint64_t)nlist * nb_pad) return;
+    if (threadIdx.x == 0) {
+      const uint32_t pi0 = list[(uint32_t)(g / nb_pad)];
+      const Plan& p0 = plans[pi0];
+      const DModel m0 = models[p0.model];
+      pivot_prep(m0, leaves + m0.leaf_off, items[pi0], p0.P, p0.Bg, rp.B, rp.dt, s_prep);
+    }
+    __syncthreads();
+  } else if (g >= (uint64_t)nlist * nb_pad) {
+    return;
+  }
   uint32_t li = (uint32_t)(g / nb_pad), j = (uint32_t)(g % nb_pad);
   uint32_t pi = list[li];
   Plan& pl = plans[pi];
@@ -575,10 +612,11 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
   const Leaf* lv = leaves + m.leaf_off;
   double P = pl.P, Bg = pl.Bg;
   uint64_t lo = it.ord_lo, hi = it.ord_hi;
-  double vlo = refine_value(m, lv, lo, P, rp.dt);
-  double vhi = refine_value(m, lv, hi, P, rp.dt);
-  uint32_t kmin = bucket_of_value(vlo, Bg, B);
-  uint32_t kmax = bucket_of_value(vhi, Bg, B);
+  PivotPrep q;
+  if (shared_prep) q = s_prep;
+  else pivot_prep(m, lv, it, P, Bg, B, rp.dt, q);
+  const double vlo = q.vlo, vhi = q.vhi;
+  const uint32_t kmin = q.kmin, kmax = q.kmax;
   if (j == 0) {
     T[0] = lo;
     pl.kmax = kmax;
@@ -602,17 +640,18 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
   uint64_t L = lo, H = hi;
   double vL = vlo, vH = vhi;
   {
-    double xlo = ord_value(lo, rp.dt), xhi = ord_value(hi, rp.dt);
-    double xcl = dmin(dmax(xlo, m.xmin), m.xmax), xch = dmin(dmax(xhi, m.xmin), m.xmax);
-    uint32_t l0 = root_leaf(m, xcl), l1 = root_leaf(m, xch);
-    double tF = t / P;
+    const double xlo = q.xlo, xhi = q.xhi;
+    uint32_t l0 = q.l0, l1 = q.l1;
+    // target F; it steers the leaf choice and the analytic guess only, the
+    // pivot itself is confirmed by exact evaluations
+    double tF = __dmul_rn(t, q.invP);
     while (l0 < l1) {  // first leaf whose clamp maximum reaches tF
       uint32_t mid = (l0 + l1) >> 1;
       if (lv[mid].hi < tF) l0 = mid + 1;
       else l1 = mid;
     }
     Leaf lf = lv[l0];
-    uint32_t lstart = root_leaf(m, xcl);
+    const uint32_t lstart = q.l0;
     if (!(tF > lf.lo) && l0 > lstart) {
       // the target is at or below this leaf's floor: F jumps over it where
       // the root starts routing to leaf l0, so that boundary is the pivot
