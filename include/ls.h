@@ -111,6 +111,11 @@ typedef struct {
  * report their device time in ls_stats.pass[] (adds one event pair per
  * launch; off by default). */
 #define LS_FLAG_TIME_PASSES 1u
+/* ls_params.flags: take fanout, sample_rate, basecase_threshold and
+ * recurse_model from the context's autotuner entry for this key type and
+ * floor(log2 n) (of the mean segment length for ls_sort_segmented), when
+ * there is one; ls_workspace_size applies the same substitution. */
+#define LS_FLAG_TUNED 2u
 
 /* The trained two-layer RMI (all FP64), as exported by ls_fit. */
 typedef struct {
@@ -253,6 +258,39 @@ ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_s
  * array holds is rejected with LS_ENOMEM.  Synchronous on `stream`. */
 ls_status ls_classify_static(const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype, uint32_t k,
                              uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist, ls_stream_t stream);
+
+/* Autotuner.  The paper notes that adjusting the sample size improved its
+ * parallel performance (Sec. 5); here the fanout B, the sample rate r, the
+ * base-case threshold T and the recursion mode are chosen by timing ls_sort
+ * on copies of the caller's keys: coordinate descent over the candidate
+ * lists below, starting from *base, each configuration timed as the median
+ * of three sorts after one warm-up sort (CUDA events on `stream`).
+ *   fanout             256, 512, 1000, 1024, 2048
+ *   basecase_threshold 1024, 2048, 4096, 8192
+ *   sample_rate        0.0025, 0.005, 0.01, 0.02
+ *   recurse_model      REFINE_GLOBAL, RETRAIN
+ * The winner is written to *out (the other fields are *base's) and stored in
+ * the context for (dtype, floor(log2 n)), where LS_FLAG_TUNED finds it.
+ * d_keys is not modified.  The tuner allocates its own device scratch (n
+ * keys plus the largest workspace of the candidates) and frees it before
+ * returning.  report (nullable) receives the timings.  Synchronous. */
+typedef struct {
+  uint32_t configs;   /* configurations timed */
+  double base_ms;     /* median sort time with *base */
+  double best_ms;     /* median sort time with *out */
+} ls_tune_report;
+
+ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* base,
+                      ls_params* out, ls_tune_report* report, ls_stream_t stream);
+
+/* The context's tuning table as text, one entry per line:
+ *   "<dtype> <log2n> <fanout> <basecase_threshold> <sample_rate> <recurse_model> <ms>\n"
+ * ls_tune_export: *bytes is the buffer size on input and the bytes written
+ * (including the terminating NUL) on output; buf = NULL queries the size.
+ * ls_tune_import adds / replaces entries from such text (NUL-terminated);
+ * malformed lines or out-of-range values give LS_EINVAL and change nothing. */
+ls_status ls_tune_export(ls_ctx* ctx, char* buf, size_t* bytes);
+ls_status ls_tune_import(ls_ctx* ctx, const char* text);
 
 /* Synchronise `stream` and return the device status word of the last call
  * on this context (LS_OK, LS_ENAN, LS_ETIMEOUT or LS_EDEVICE), then clear it. */

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblearnedsort.so")
-SOURCES = ["ls_api.cu", "ls_fit.cu", "ls_partition.cu", "ls_static.cu"]
-HEADERS = ["ls_common.cuh", "ls_kernels.h"]
+SOURCES = ["ls_api.cu", "ls_fit.cu", "ls_partition.cu", "ls_static.cu", "ls_tune.cu"]
+HEADERS = ["ls_common.cuh", "ls_kernels.h", "ls_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no FMA contraction anywhere; the model arithmetic also uses
 # explicit round-to-nearest intrinsics so its results match the FP64

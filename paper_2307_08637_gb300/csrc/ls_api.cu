@@ -22,18 +22,10 @@
 #include <set>
 #include <vector>
 
+#include "ls_ctx.h"
 #include "ls_kernels.h"
 
 using namespace lsg;
-
-struct ls_ctx {
-  int device = 0;
-  unsigned int* d_status = nullptr;
-  // cached device memory for ls_fit / ls_classify / ls_fit_grad / ls_sort_host
-  void* d_cache = nullptr;
-  size_t d_cache_bytes = 0;
-  uint64_t launches = 0;
-};
 
 namespace {
 
@@ -71,6 +63,27 @@ ls_status validate_params(const ls_params* p) {
   if (p->classify_mode < 0 || p->classify_mode > 4) return LS_EINVAL;
   return LS_OK;
 }
+
+}  // namespace
+
+// The parameters a sort really uses: with LS_FLAG_TUNED, the autotuner's
+// entry for the key type and floor(log2) of the (mean segment) length
+// replaces fanout, sample rate, base-case threshold and recursion mode.
+static ls_params effective_params(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dtype, const ls_params& p) {
+  ls_params e = p;
+  if (!(p.flags & LS_FLAG_TUNED) || !ctx) return e;
+  const uint64_t per = nseg ? n / nseg : n;
+  std::lock_guard<std::mutex> lk(ctx->tuned_mu);
+  auto it = ctx->tuned.find(ls_tune_key(dtype, per ? per : 1));
+  if (it == ctx->tuned.end()) return e;
+  e.fanout = it->second.fanout;
+  e.basecase_threshold = it->second.basecase_threshold;
+  e.sample_rate = it->second.sample_rate;
+  e.recurse_model = it->second.recurse_model;
+  return e;
+}
+
+namespace {
 
 uint64_t sample_size(uint64_t n, const ls_params* p) {
   if (n == 0) return 0;
@@ -646,7 +659,9 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
                     const ls_params* p, void* ws, size_t ws_bytes, ls_stats* out_stats, int32_t* seg_dec,
                     cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
-  if (!ctx || (!d_keys && h_off[nseg] > 0) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  if (!ctx || !p || (!d_keys && h_off[nseg] > 0) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  const ls_params eff = effective_params(ctx, h_off[nseg], nseg, dtype, *p);
+  p = &eff;
   ls_status vs = validate_params(p);
   if (vs != LS_OK) return vs;
   for (uint32_t s = 0; s < nseg; ++s)
@@ -891,11 +906,11 @@ void ls_destroy(ls_ctx* ctx) {
 
 ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dtype, const ls_params* p,
                             size_t* bytes) {
-  (void)ctx;
-  if (!bytes || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
-  ls_status vs = validate_params(p);
+  if (!bytes || !p || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  const ls_params eff = effective_params(ctx, n, nseg ? nseg : 1, dtype, *p);
+  ls_status vs = validate_params(&eff);
   if (vs != LS_OK) return vs;
-  *bytes = compute_layout(n, nseg ? nseg : 1, p).total;
+  *bytes = compute_layout(n, nseg ? nseg : 1, &eff).total;
   return LS_OK;
 }
 

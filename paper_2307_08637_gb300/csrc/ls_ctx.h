@@ -1,0 +1,36 @@
+// ls_ctx.h -- the library context (internal).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+
+#include "../../include/ls.h"
+
+// Parameters the autotuner picked for one (key type, floor(log2 n)) class.
+struct ls_tuned_entry {
+  uint32_t fanout = 0;
+  uint32_t basecase_threshold = 0;
+  double sample_rate = 0.0;
+  int32_t recurse_model = 0;
+  double ms = 0.0;  // sort time of the winner when it was tuned
+};
+
+struct ls_ctx {
+  int device = 0;
+  unsigned int* d_status = nullptr;
+  // cached device memory for ls_fit / ls_classify / ls_fit_grad / ls_sort_host
+  void* d_cache = nullptr;
+  size_t d_cache_bytes = 0;
+  uint64_t launches = 0;
+  // autotuner results, keyed by dtype * 64 + floor(log2 n)
+  std::map<int, ls_tuned_entry> tuned;
+  std::mutex tuned_mu;
+};
+
+// Key of the tuning class of n keys of type dt.
+inline int ls_tune_key(int dt, uint64_t n) {
+  int lg = 0;
+  while (lg < 63 && (n >> (lg + 1))) ++lg;
+  return dt * 64 + lg;
+}

@@ -29,7 +29,7 @@ LS_MAX_LEVELS = 48
 EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
-    "ls_model_import", "ls_status_string", "ls_classify_static",
+    "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_tune_export", "ls_tune_import",
 )
 
 
@@ -111,11 +111,16 @@ class LevelStats(C.Structure):
 
 
 LS_FLAG_TIME_PASSES = 1
+LS_FLAG_TUNED = 2
 PASS_NAMES = ("sample", "fit", "pivots", "classify", "children", "scatter", "base", "copy")
 
 
 class PassTime(C.Structure):
     _fields_ = [("ms", C.c_double), ("launches", C.c_uint64), ("keys", C.c_uint64)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("configs", C.c_uint32), ("base_ms", C.c_double), ("best_ms", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -185,6 +190,12 @@ def lib() -> C.CDLL:
     L.ls_model_import.restype = C.c_int
     L.ls_status_string.argtypes = [C.c_int]
     L.ls_status_string.restype = C.c_char_p
+    L.ls_autotune.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Params), C.POINTER(TuneReport), vp]
+    L.ls_autotune.restype = C.c_int
+    L.ls_tune_export.argtypes = [vp, C.c_char_p, C.POINTER(C.c_size_t)]
+    L.ls_tune_export.restype = C.c_int
+    L.ls_tune_import.argtypes = [vp, C.c_char_p]
+    L.ls_tune_import.restype = C.c_int
     _lib = L
     return L
 
@@ -393,3 +404,67 @@ def ls_model_import(data: bytes) -> Model:
     buf = C.create_string_buffer(data, len(data))
     _check(lib().ls_model_import(C.byref(m), buf, len(data)), "ls_model_import")
     return m
+
+
+def ls_autotune(ctx: Context, keys, base: Params | None = None, stream=None) -> tuple[Params, TuneReport]:
+    """Time candidate (fanout, base-case threshold, sample rate, recursion)
+    settings on copies of `keys` (not modified) and return the fastest, which
+    is also stored in the context for LS_FLAG_TUNED."""
+    base = base or ls_params_default()
+    out = Params()
+    rep = TuneReport()
+    rc = lib().ls_autotune(ctx.handle, _ptr(keys), keys.numel(), _dtype_code(keys), C.byref(base), C.byref(out),
+                           C.byref(rep), _stream(stream))
+    _check(rc, "ls_autotune")
+    return out, rep
+
+
+def ls_tune_export(ctx: Context) -> str:
+    """The context's tuning table as text (one entry per line)."""
+    n = C.c_size_t(0)
+    _check(lib().ls_tune_export(ctx.handle, None, C.byref(n)), "ls_tune_export")
+    buf = C.create_string_buffer(n.value)
+    _check(lib().ls_tune_export(ctx.handle, buf, C.byref(n)), "ls_tune_export")
+    return buf.value.decode()
+
+
+def ls_tune_import(ctx: Context, text: str) -> None:
+    """Add / replace tuning entries from ls_tune_export text."""
+    _check(lib().ls_tune_import(ctx.handle, text.encode()), "ls_tune_import")
+
+
+_TUNE_FIELDS = ("dtype", "log2n", "fanout", "basecase_threshold", "sample_rate", "recurse_model", "ms")
+
+
+def tune_text_to_json(text: str) -> list[dict]:
+    """Parse ls_tune_export text into JSON-ready records."""
+    out = []
+    for line in text.splitlines():
+        if not line.strip():
+            continue
+        v = line.split()
+        if len(v) != len(_TUNE_FIELDS):
+            raise ValueError(f"bad tuning line: {line!r}")
+        out.append({"dtype": int(v[0]), "log2n": int(v[1]), "fanout": int(v[2]), "basecase_threshold": int(v[3]),
+                    "sample_rate": float(v[4]), "recurse_model": int(v[5]), "ms": float(v[6])})
+    return out
+
+
+def tune_json_to_text(records: list[dict]) -> str:
+    """Inverse of tune_text_to_json (the text ls_tune_import reads)."""
+    return "".join(f"{int(r['dtype'])} {int(r['log2n'])} {int(r['fanout'])} {int(r['basecase_threshold'])} "
+                   f"{float(r['sample_rate']):.17g} {int(r['recurse_model'])} {float(r['ms']):.6f}\n" for r in records)
+
+
+def save_tuning(ctx: Context, path: str) -> None:
+    """Write the context's tuning table to a JSON file."""
+    import json
+    with open(path, "w") as f:
+        json.dump(tune_text_to_json(ls_tune_export(ctx)), f, indent=1)
+
+
+def load_tuning(ctx: Context, path: str) -> None:
+    """Load a JSON tuning table written by save_tuning into the context."""
+    import json
+    with open(path) as f:
+        ls_tune_import(ctx, tune_json_to_text(json.load(f)))

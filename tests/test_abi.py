@@ -77,3 +77,19 @@ def test_oracle_and_product_share_no_code():
     o = open(os.path.join(ROOT, "oracle", "ls_oracle.c")).read() + open(os.path.join(ROOT, "oracle", "ls_oracle.h")).read()
     for bad in ("paper_2307_08637_gb300", "ls_common", "ls_kernels", "include/ls.h"):
         assert bad not in o, bad
+
+
+def test_tuning_table_text_json_roundtrip():
+    """The autotuner's table format: ls_tune_export text <-> JSON records
+    (pure host code; the GPU tests cover the C side)."""
+    import paper_2307_08637_gb300 as lsg
+    text = "0 20 1000 4096 0.01 0 3.250000\n1 26 512 2048 0.0050000000000000001 1 41.500000\n"
+    recs = lsg.tune_text_to_json(text)
+    assert recs == [
+        {"dtype": 0, "log2n": 20, "fanout": 1000, "basecase_threshold": 4096, "sample_rate": 0.01,
+         "recurse_model": 0, "ms": 3.25},
+        {"dtype": 1, "log2n": 26, "fanout": 512, "basecase_threshold": 2048, "sample_rate": 0.005,
+         "recurse_model": 1, "ms": 41.5}]
+    assert lsg.tune_text_to_json(lsg.tune_json_to_text(recs)) == recs
+    with pytest.raises(ValueError):
+        lsg.tune_text_to_json("0 20 1000\n")
