@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-splitter", action="store_true")
     ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c2: six 1e8-key arrays (the headline); c4: 4096 segments, batched vs one call per array")
+    ap.add_argument("--nseg", type=int, default=4096, help="c4: number of segments")
     return ap.parse_args()
 
 
@@ -367,10 +370,147 @@ def run_ours(args):
     return 0
 
 
+def _oracle_segments(args_tuple):
+    """One oracle sort per segment (worker of the multi-core C4 baseline)."""
+    import oracle
+
+    x, kw = args_tuple
+    out, rc, _, _, _ = oracle.sort(x, oracle.params(**kw))
+    return rc
+
+
+def run_c4(args):
+    """C4: nseg float64 arrays with log-uniform lengths in [1e3, 1e6], each its
+    own distribution with a random affine map; one ls_sort_segmented call
+    (every segment's sample, model and partition handled level by level in
+    shared launches) against one ls_sort call per array, both with the
+    parameters the autotuner picks on a segment of the mean length."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    dev = 0
+    torch.cuda.set_device(dev)
+    import paper_2307_08637_gb300 as lsg
+
+    keys, off, names = datagen.segmented(args.nseg, 4)
+    nseg = off.size - 1
+    lens = np.diff(off).astype(np.int64)
+    n = int(off[-1])
+    stream = torch.cuda.current_stream()
+    ctx = lsg.Context(dev)
+    pristine = torch.from_numpy(keys).to(f"cuda:{dev}")
+    work = torch.empty_like(pristine)
+    mean_len = n / nseg
+    probe = int(np.argmin(np.abs(lens - mean_len)))
+    seg_probe = pristine[int(off[probe]):int(off[probe + 1])].clone()
+    base = lsg.ls_params_default()
+    tuned, rep = lsg.ls_autotune(ctx, seg_probe, base)
+    p = lsg.ls_params_default(fanout=tuned.fanout, basecase_threshold=tuned.basecase_threshold,
+                              sample_rate=tuned.sample_rate, recurse_model=tuned.recurse_model)
+    ctx.workspace(n, nseg, lsg.LS_F64, p)
+
+    def batched():
+        work.copy_(pristine)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, dec = lsg.ls_sort_segmented(ctx, work, off, p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), st
+
+    def looped():
+        work.copy_(pristine)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches = 0
+        for s in range(nseg):
+            st = lsg.ls_sort(ctx, work[int(off[s]):int(off[s + 1])], p, stream=stream)
+            launches += int(st.kernel_launches)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), launches
+
+    for _ in range(args.warmup):
+        batched()
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        bms, bst = [], None
+        for _ in range(args.steps):
+            ms, bst = batched()
+            bms.append(ms)
+    out_b = work.clone()
+    # every segment ascending under ord
+    o = out_b.view(torch.int64)
+    o = o ^ ((o >> 63) & 0x7FFFFFFFFFFFFFFF)
+    ok = (o[1:] >= o[:-1])
+    starts = torch.from_numpy(off[1:-1].astype(np.int64) - 1).to(f"cuda:{dev}")
+    ok[starts[starts >= 0]] = True
+    assert bool(ok.all()), "segmented output not sorted"
+    looped()  # warm-up of the per-array path
+    lms, llaunch = [], 0
+    for _ in range(max(1, min(args.steps, 2))):
+        ms, llaunch = looped()
+        lms.append(ms)
+    assert torch.equal(work, out_b), "batched and per-array results differ"
+    b_ms = sum(bms) / len(bms)
+    l_ms = sum(lms) / len(lms)
+    # oracle: a bounded sample of segments, one thread and all host cores
+    cpu = None
+    if not args.no_cpu:
+        import multiprocessing as mp
+        import oracle
+
+        oracle.build()
+        kw = dict(fanout=p.fanout, basecase_threshold=p.basecase_threshold, sample_rate=p.sample_rate,
+                  recurse_model=p.recurse_model)
+        pick = list(range(0, nseg, max(1, nseg // 48)))[:48]
+        segs = [keys[int(off[s]):int(off[s + 1])] for s in pick]
+        nk = sum(x.size for x in segs)
+        t0 = time.perf_counter()
+        for x in segs:
+            assert _oracle_segments((x, kw)) == 0
+        t1 = time.perf_counter() - t0
+        cores = os.cpu_count() or 1
+        with mp.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            assert all(r == 0 for r in pool.map(_oracle_segments, [(x, kw) for x in segs]))
+            tm = time.perf_counter() - t0
+        cpu = {"value": nk / t1, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(segs)} of the {nseg} segments ({nk} keys), one thread",
+               "all_cores": {"value": nk / tm, "cores": cores, "note": "same segments, spawn pool, one per task"}}
+    line = {
+        "metric": "keys/s, batched segmented sort vs one ls_sort call per array (4096 f64 segments), 1 GB300",
+        "value": n / (b_ms / 1e3), "unit": "keys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": b_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"C4: {nseg} float64 segments, lengths log-uniform in [1e3, 1e6] ({n} keys), "
+                               "distribution per segment from the six of C2, shift U[-1e3,1e3], scale log-U[1e-3,1e3]",
+                   "params": {"fanout": p.fanout, "basecase_threshold": p.basecase_threshold,
+                              "sample_rate": p.sample_rate, "recurse_model": p.recurse_model,
+                              "chosen_by": f"ls_autotune on segment {probe} ({int(lens[probe])} keys, mean "
+                                           f"{mean_len:.0f}); {rep.configs} configurations, "
+                                           f"{rep.base_ms:.3f} -> {rep.best_ms:.3f} ms"},
+                   "l2": "4.7 GB of keys, larger than L2; no flush"},
+        "per_array_calls": {"value": n / (l_ms / 1e3), "unit": "keys/s", "ms_per_step": l_ms,
+                            "gpu_launches": llaunch},
+        "batched_speedup": l_ms / b_ms,
+        "gpu_launches": int(bst.kernel_launches),
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 
