@@ -158,7 +158,9 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
   l.rchunk_cap = l.scap / kChunk + kBatchItems + 8;
   l.lchunk_cap = l.scap / kChunk + (uint64_t)kBatchItems * l.L + 8;
   l.stmp_elems = scan_tmp_elems((size_t)kBatchItems * l.L + 8) + 64;
-  l.chunk_cap = n / kChunkKeys + kBatchItems + nseg + 8;
+  // chunks of a batch: at most n / 64Ki + one partial chunk per item, or
+  // fewer than 2 kChunkSlots + one per item when the chunk size was reduced
+  l.chunk_cap = n / kChunkKeys + kBatchItems + nseg + 8 + 2 * kChunkSlots;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t r = off;
@@ -318,12 +320,20 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   uint64_t tiles = 0;
   uint64_t max_s = 0;
   std::vector<Item> its(items, items + nitems);
+  // Chunk size of the partition passes: 64Ki keys, halved (down to one tile)
+  // while the batch would give fewer than kChunkSlots chunks, so that small
+  // batches (deep levels, few small items) still spread over the GPU.
+  // Every chunk size gives the same partition; only the work split differs.
+  uint64_t batch_keys = 0;
+  for (uint32_t i = 0; i < nitems; ++i) batch_keys += its[i].n;
+  uint64_t ck = kChunkKeys;
+  while (ck > kTileKeys && batch_keys / ck < kChunkSlots) ck >>= 1;
   for (uint32_t i = 0; i < nitems; ++i) {
     Item& it = its[i];
     Plan& pl = plans[i];
     memset(&pl, 0, sizeof pl);
     pl.chunk_begin = tiles;
-    tiles += (it.n + kChunkKeys - 1) / kChunkKeys;
+    tiles += (it.n + ck - 1) / ck;
     pl.cnt_off = (uint64_t)i * L.nbc;
     pl.tab_off = (uint64_t)i * L.nbc;
     pl.dir_off = (uint64_t)i * (L.cells + 1);
@@ -548,8 +558,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.aux_bytes = aux;
   pa.cls_mask = cls_mask;
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
-  uint64_t batch_keys = 0;
-  for (uint32_t i = 0; i < nitems; ++i) batch_keys += its[i].n;
+  pa.chunk_keys = ck;
   CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
   s.timer.begin(LS_PASS_CLASSIFY, batch_keys);
   s.launches += launch_classify_hist(pa, s.rp, st);
@@ -578,7 +587,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   std::vector<ChunkSeg> segs;
   bool multi = false;
   for (uint32_t i = 0; i < nitems; ++i) {
-    uint64_t cb = plans[i].chunk_begin, nc = (its[i].n + kChunkKeys - 1) / kChunkKeys;
+    uint64_t cb = plans[i].chunk_begin, nc = (its[i].n + ck - 1) / ck;
     uint32_t first = (uint32_t)segs.size();
     multi |= nc > kSegChunks;
     for (uint64_t c = 0; c < nc; c += kSegChunks) {

@@ -138,12 +138,17 @@ struct PassArgs {
   uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
   unsigned long long* excl;     // per chunk: keys of each bucket in the item's earlier chunks
   unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
+  uint64_t chunk_keys;          // keys per chunk: a multiple of the tile, at most kChunkKeys
   unsigned int* status;         // device status word
   int check_nan;
   uint32_t nb_pad_max;
   uint32_t dir_cells_max;
 };
 int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st);  // returns launches
+// A batch with fewer chunks than this gets smaller chunks (about two per
+// resident K1/K3 block on a 152-SM part; a constant so that workspace sizes
+// do not depend on the device).
+constexpr uint64_t kChunkSlots = 1024;
 
 // A run of at most kSegChunks consecutive chunks of one item.
 constexpr uint32_t kSegChunks = 16;

@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams
     }
     const Item& it = a.items[pi];
     const Plan& pl = a.plans[pi];
-    const uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
-    const uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t c0 = (ch - pl.chunk_begin) * a.chunk_keys;
+    const uint64_t clen = it.n - c0 < a.chunk_keys ? it.n - c0 : a.chunk_keys;
     const uint64_t* keys = it.buf ? a.keysB : a.keysA;
     uint64_t diff = 0;
     k1_chunk<CLS, DT, NANCHK>(a, c, sT, sD, sH, keys + it.lo + c0, a.ids + it.lo + c0, clen, keys[it.lo], diff, nan);
@@ -293,8 +293,16 @@ __device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t* wm, uint32_t
 // destinations.  Keys keep their relative order within a bucket (the stable
 // counting sort of the partitioning step).  Counters of warps 2i and 2i+1
 // share a word, 16 bits each (a warp ranks at most kWarpKeys keys).
-template <bool MASK>
-__global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
+// How K3 finds the lanes of a warp step that hold the same bucket id.
+enum K3Mode {
+  K3_MATCH = 0,       // warp match instruction (any number of buckets)
+  K3_MASK_STAGE = 1,  // per-warp masks in the staging buffer (nb_pad <= kMaskBuckets)
+  K3_MASK_OWN = 2     // per-warp masks in their own area (nb_pad <= 2 kMaskBuckets)
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter(PassArgs a, RunParams rp) {
+  constexpr bool MASK = MODE != K3_MATCH;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t nbp = a.nb_pad_max;
   uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);          // next destination per bucket
@@ -308,10 +316,14 @@ __global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t wsh = 16 * (wid & 1);
   uint32_t* myc = wcnt + (wid >> 1) * nbp;
-  uint32_t* wm = reinterpret_cast<uint32_t*>(stage) + wid * nbp;
+  uint32_t* const masks =
+      MODE == K3_MASK_OWN ? reinterpret_cast<uint32_t*>(sid + kTile) : reinterpret_cast<uint32_t*>(stage);
+  uint32_t* wm = masks + wid * nbp;
   const unsigned lt = (1u << lane) - 1u;
   for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp; j += kTPB) wcnt[j] = 0;
   for (uint32_t j = threadIdx.x; j < kTile * 2; j += kTPB) reinterpret_cast<uint32_t*>(stage)[j] = 0;
+  if (MODE == K3_MASK_OWN)
+    for (uint32_t j = threadIdx.x; j < kWarps * nbp; j += kTPB) masks[j] = 0;
   bool oob = false;
   for (int par = 0;; par ^= 1) {
     if (threadIdx.x == 0) s_chunk[par] = atomicAdd(a.chunk_ctr, 1ull);
@@ -329,8 +341,8 @@ __global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
       sCnt[b] = 0;
       sLs[b] = 0;
     }
-    const uint64_t c0 = (ch - pl.chunk_begin) * kChunkKeys;
-    const uint64_t clen = it.n - c0 < kChunkKeys ? it.n - c0 : kChunkKeys;
+    const uint64_t c0 = (ch - pl.chunk_begin) * a.chunk_keys;
+    const uint64_t clen = it.n - c0 < a.chunk_keys ? it.n - c0 : a.chunk_keys;
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
     const uint16_t* idin = a.ids + it.lo + c0;
     uint64_t* dst = it.buf ? a.outA : a.outB;
@@ -367,7 +379,8 @@ __global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
       // per bucket b = q*kTPB + tid: advance the run by the previous tile's
       // count, prefix over the warps (in place), tile count; then one scan
       // over all buckets (ranges q-major, then warps, then lanes)
-      constexpr uint32_t QMAX = MASK ? kMaskBuckets / kTPB : 16;  // bucket ranges of kTPB
+      constexpr uint32_t QMAX = MODE == K3_MASK_STAGE ? kMaskBuckets / kTPB
+                                : MODE == K3_MASK_OWN ? 2 * kMaskBuckets / kTPB : 16;  // bucket ranges of kTPB
       uint32_t cnt[QMAX];
 #pragma unroll
       for (uint32_t q = 0; q < QMAX; ++q) {
@@ -460,7 +473,7 @@ __global__ void __launch_bounds__(kTPB, 3) k_scatter(PassArgs a, RunParams rp) {
       auto put = [&](uint32_t p) {
         const uint64_t o = sRun[sid[p]] + p;
         const uint64_t x = stage[p];
-        stage[p] = 0;  // peer masks of the next tile start from zero
+        if (MODE == K3_MASK_STAGE) stage[p] = 0;  // peer masks of the next tile start from zero
         const bool ok = o - lo < n;  // K1 and K3 disagree: never write outside the item
         if (ok) dst[o] = x;
         oob |= !ok;
@@ -1346,23 +1359,24 @@ int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, bool multi, const 
   return 2;
 }
 
-template <bool MASK>
+template <int MODE>
 static void launch_k3(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
-  size_t sm = k3_smem(a);
+  size_t sm = k3_smem(a) + (MODE == K3_MASK_OWN ? (size_t)kWarps * a.nb_pad_max * 4 : 0);
   static size_t set[64] = {};
-  allow_smem(k_scatter<MASK>, sm, set);
+  allow_smem(k_scatter<MODE>, sm, set);
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MASK>, kTPB, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MODE>, kTPB, sm);
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_scatter<MASK><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  k_scatter<MODE><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
 }
 
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (!a.nchunks) return;
-  if (a.nb_pad_max <= kMaskBuckets) launch_k3<true>(a, rp, st);
-  else launch_k3<false>(a, rp, st);
+  if (a.nb_pad_max <= kMaskBuckets) launch_k3<K3_MASK_STAGE>(a, rp, st);
+  else if (a.nb_pad_max <= 2 * kMaskBuckets) launch_k3<K3_MASK_OWN>(a, rp, st);
+  else launch_k3<K3_MATCH>(a, rp, st);
 }
 
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
