@@ -187,30 +187,26 @@ static double tree_sum(double* p, uint64_t m) {
 /* The four least-squares sums over sample positions j in [st, en) of the
  * sorted sample, with X_j = v(s_j) - x0 and y_j = j / S (the empirical CDF
  * of Sec. 2.1: pos = N * P(A <= x)).  Canonical order: consecutive chunks
- * of 256 positions from st, each summed left to right from +0.0; the chunk
- * partials are then combined by tree_sum. */
+ * of 256 positions from st, each summed by tree_sum over its terms; the
+ * chunk partials are then combined by tree_sum again.  (The paper fixes no
+ * summation order; a fixed pairwise tree is deterministic and accurate.) */
 static void ls_sums(const uint64_t* s_ord, int dtype, uint64_t st, uint64_t en, double x0, uint64_t S,
                     double out[4]) {
   uint64_t nch = (en - st + CHUNK - 1) / CHUNK;
   double* part = (double*)malloc(4 * (nch ? nch : 1) * sizeof(double));
+  double t[4][CHUNK];
   uint64_t c = 0;
   for (uint64_t c0 = st; c0 < en; c0 += CHUNK, ++c) {
     uint64_t c1 = (en - c0 > CHUNK) ? c0 + CHUNK : en;
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
     for (uint64_t j = c0; j < c1; ++j) {
       double X = ord_value(s_ord[j], dtype) - x0;
       double y = (double)j / (double)S;
-      double xy = X * y;
-      double xx = X * X;
-      p0 = p0 + X;
-      p1 = p1 + y;
-      p2 = p2 + xy;
-      p3 = p3 + xx;
+      t[0][j - c0] = X;
+      t[1][j - c0] = y;
+      t[2][j - c0] = X * y;
+      t[3][j - c0] = X * X;
     }
-    part[c] = p0;
-    part[nch + c] = p1;
-    part[2 * nch + c] = p2;
-    part[3 * nch + c] = p3;
+    for (int k = 0; k < 4; ++k) part[k * nch + c] = tree_sum(t[k], c1 - c0);
   }
   for (int k = 0; k < 4; ++k) out[k] = tree_sum(part + k * nch, nch);
   free(part);

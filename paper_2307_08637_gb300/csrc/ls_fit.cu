@@ -52,25 +52,41 @@ __device__ __forceinline__ void linfit(double n, double sx, double sy, double sx
   *b = __ddiv_rn(r, n);
 }
 
-// One chunk (<= 256 consecutive positions [j0, j1)) of the least-squares sums:
-// X_j = v(s_j) - x0, y_j = j / S, summed left to right from +0.0.
-__device__ __forceinline__ void chunk_sums(const uint64_t* __restrict__ s, uint64_t j0, uint64_t j1, double x0,
-                                           double Sd, int dt, double out[4]) {
-  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-  for (uint64_t j = j0; j < j1; ++j) {
-    double X = __dsub_rn(ord_value(s[j], dt), x0);
-    double y = __ddiv_rn(__ull2double_rn(j), Sd);
-    double xy = __dmul_rn(X, y);
-    double xx = __dmul_rn(X, X);
-    p0 = __dadd_rn(p0, X);
-    p1 = __dadd_rn(p1, y);
-    p2 = __dadd_rn(p2, xy);
-    p3 = __dadd_rn(p3, xx);
+// The same four sums over one chunk [j0, j1) (at most kChunk = 256
+// positions) by a whole warp, as a fixed pairwise tree: lane l forms the
+// terms of positions j0 + 8l .. j0 + 8l + 7 (+0.0 beyond j1), adds them in
+// pairs, and the lanes combine in pairs (lane 2k takes lane 2k+1's partial,
+// then 4k takes 4k+2's, ...), so lane 0 ends with the complete binary tree
+// over the 256 positions.  Every term is >= +0 (X >= 0 because x0 is the
+// smallest key of the range; y, X y, X X >= 0), so the zero padding changes
+// no addition: this is the tree that halves the list pair by pair and
+// carries an odd last value.  Result valid in lane 0.
+__device__ __forceinline__ void warp_chunk_sums(const uint64_t* __restrict__ s, uint64_t j0, uint64_t j1, double x0,
+                                                double Sd, int dt, double out[4]) {
+  const unsigned lane = threadIdx.x & 31;
+  double t[4][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const uint64_t j = j0 + 8 * lane + e;
+    if (j < j1) {
+      const double X = __dsub_rn(ord_value(s[j], dt), x0);
+      const double y = __ddiv_rn(__ull2double_rn(j), Sd);
+      t[0][e] = X;
+      t[1][e] = y;
+      t[2][e] = __dmul_rn(X, y);
+      t[3][e] = __dmul_rn(X, X);
+    } else {
+      t[0][e] = t[1][e] = t[2][e] = t[3][e] = 0.0;
+    }
   }
-  out[0] = p0;
-  out[1] = p1;
-  out[2] = p2;
-  out[3] = p3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = __dadd_rn(__dadd_rn(__dadd_rn(t[q][0], t[q][1]), __dadd_rn(t[q][2], t[q][3])),
+                         __dadd_rn(__dadd_rn(t[q][4], t[q][5]), __dadd_rn(t[q][6], t[q][7])));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) v = __dadd_rn(v, __shfl_down_sync(0xFFFFFFFFu, v, d));
+    out[q] = v;
+  }
 }
 
 // Fixed pairwise tree over m partials, done by one thread in place:
@@ -213,20 +229,22 @@ __global__ void __launch_bounds__(kTPB) k_merge_pass(const uint64_t* __restrict_
 
 // ---------------------------------------------------------------- fit
 
+// One warp per root chunk of every candidate.
 __global__ void k_fit_root_partials(FitArgs a, RunParams rp) {
-  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= a.total_rchunks) return;
-  uint32_t c = find_seg(a.rchunk_prefix, a.ncand, g);
-  uint64_t k = g - a.rchunk_prefix[c];
+  const uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (g >= a.total_rchunks) return;  // uniform across the warp
+  const uint32_t c = find_seg(a.rchunk_prefix, a.ncand, g);
+  const uint64_t k = g - a.rchunk_prefix[c];
   const Plan& pl = a.plans[a.cand[c]];
-  uint64_t S = pl.S;
+  const uint64_t S = pl.S;
   const uint64_t* s = a.samp + pl.sample_off;
-  double x0 = ord_value(s[0], rp.dt);
-  uint64_t j0 = k * kChunk;
-  uint64_t j1 = j0 + kChunk < S ? j0 + kChunk : S;
+  const double x0 = ord_value(s[0], rp.dt);
+  const uint64_t j0 = k * kChunk;
+  const uint64_t j1 = j0 + kChunk < S ? j0 + kChunk : S;
   double out[4];
-  chunk_sums(s, j0, j1, x0, __ull2double_rn(S), rp.dt, out);
-  for (int q = 0; q < 4; ++q) a.rpart[q * a.total_rchunks + g] = out[q];
+  warp_chunk_sums(s, j0, j1, x0, __ull2double_rn(S), rp.dt, out);
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) a.rpart[q * a.total_rchunks + g] = out[q];
 }
 
 // Per candidate: tree-combine the root chunk partials, fit the root.
@@ -307,26 +325,28 @@ __global__ void k_fit_leaf_chunk_count(FitArgs a) {
   a.lchunk_cnt[g] = (cnt + kChunk - 1) / kChunk;
 }
 
+// One warp per leaf chunk of every candidate.
 __global__ void k_fit_leaf_partials(FitArgs a, RunParams rp) {
-  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  uint32_t tot = a.ncand * a.L;
-  if (g >= a.lchunk_prefix[tot] || g >= a.lchunk_bound) return;
-  uint32_t ci = find_seg(a.lchunk_prefix, tot, g);
-  uint64_t k = g - a.lchunk_prefix[ci];
-  uint32_t c = ci / a.L, i = ci % a.L;
+  const uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint32_t tot = a.ncand * a.L;
+  if (g >= a.lchunk_prefix[tot] || g >= a.lchunk_bound) return;  // uniform across the warp
+  const uint32_t ci = find_seg(a.lchunk_prefix, tot, g);
+  const uint64_t k = g - a.lchunk_prefix[ci];
+  const uint32_t c = ci / a.L, i = ci % a.L;
   const Plan& pl = a.plans[a.cand[c]];
   const uint64_t* s = a.samp + pl.sample_off;
   const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
-  uint64_t S = pl.S;
-  uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
-  uint64_t st = ls[i] < en ? ls[i] : en;
+  const uint64_t S = pl.S;
+  const uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
+  const uint64_t st = ls[i] < en ? ls[i] : en;
   if (st >= en) return;
-  double x0 = ord_value(s[st], rp.dt);
-  uint64_t j0 = st + k * kChunk;
-  uint64_t j1 = j0 + kChunk < en ? j0 + kChunk : en;
+  const double x0 = ord_value(s[st], rp.dt);
+  const uint64_t j0 = st + k * kChunk;
+  const uint64_t j1 = j0 + kChunk < en ? j0 + kChunk : en;
   double out[4];
-  chunk_sums(s, j0, j1, x0, __ull2double_rn((uint64_t)pl.S), rp.dt, out);
-  for (int q = 0; q < 4; ++q) a.lpart[q * a.lchunk_bound + g] = out[q];
+  warp_chunk_sums(s, j0, j1, x0, __ull2double_rn((uint64_t)pl.S), rp.dt, out);
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) a.lpart[q * a.lchunk_bound + g] = out[q];
 }
 
 __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_cnt) {
@@ -1147,7 +1167,7 @@ void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st) {
 
 void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches) {
   if (!a.ncand) return;
-  k_fit_root_partials<<<grid_for(a.total_rchunks, 128), 128, 0, st>>>(a, rp);
+  k_fit_root_partials<<<grid_for(a.total_rchunks * 32, 128), 128, 0, st>>>(a, rp);
   k_fit_root_finish<<<a.ncand, 1024, 0, st>>>(a, rp);
   cudaMemsetAsync(a.leaf_start, 0, (size_t)a.ncand * (a.L + 1) * sizeof(uint32_t), st);
   k_fit_route_leaf<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, rp, a.leaf_of);
@@ -1155,7 +1175,7 @@ void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t
   uint64_t tot = (uint64_t)a.ncand * a.L;
   k_fit_leaf_chunk_count<<<grid_for(tot + 1), kTPB, 0, st>>>(a);
   launch_scan_exclusive_u64(a.lchunk_cnt, a.lchunk_prefix, tot, a.scan_tmp, a.scan_tmp_elems, st);
-  k_fit_leaf_partials<<<grid_for(a.lchunk_bound, 128), 128, 0, st>>>(a, rp);
+  k_fit_leaf_partials<<<grid_for(a.lchunk_bound * 32, 128), 128, 0, st>>>(a, rp);
   k_fit_leaf_finish<<<grid_for(tot, 128), 128, 0, st>>>(a, rp, a.leaf_cnt);
   k_fit_monotone<<<a.ncand, 1024, 0, st>>>(a, a.leaf_cnt);
   k_fmodel_fit<<<grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st>>>(a);

@@ -903,107 +903,116 @@ __device__ __forceinline__ void warp_sort_span(const Span& s, uint64_t* A, const
 // Model-placed base case for one span of <= 256 keys, done by one warp (the
 // GPU form of LearnedSort 2.0's counting sort by predicted position plus an
 // insertion-sort fix, Sec. 2.2): inside a bucket the keys are close to
-// uniform in ord space, so the linear map (ord - min) / (max - min), read as
-// the top 8 bits of (ord - min) << clz(max - min), places them into 256
-// slots; a counting sort by slot and an insertion sort inside each slot give
-// the exact order.  Spans whose largest slot holds more than kMaxSlot keys
-// (clustered data) return false and take the bitonic network instead.
+// uniform in ord space, so a linear map between the span's extremes places
+// them into 32R slots (R = ceil(n / 32) keys per lane); a counting sort by
+// slot and an insertion sort inside each slot give the exact order.  Spans
+// whose largest slot holds more than kMaxSlot keys (clustered data) return
+// false and take the bitonic network instead.
 constexpr uint32_t kSlots = 256;  // slots of the largest size class (32 per key register)
 constexpr uint32_t kMaxSlot = 24;
 
-// Exact warp-wide minimum / maximum of one u64 per lane from 32-bit
-// reductions: high words first, then the low words of the lanes that hold
-// the extreme high word.
-__device__ __forceinline__ void warp_minmax_u64(unsigned long long lmin, unsigned long long lmax,
-                                                unsigned long long& mn, unsigned long long& mx) {
-  const uint32_t hmin = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(lmin >> 32));
-  const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)(lmax >> 32));
-  const uint32_t lo_min = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(lmin >> 32) == hmin ? (uint32_t)lmin : ~0u);
-  const uint32_t lo_max = __reduce_max_sync(0xFFFFFFFFu, (uint32_t)(lmax >> 32) == hmax ? (uint32_t)lmax : 0u);
-  mn = ((unsigned long long)hmin << 32) | lo_min;
-  mx = ((unsigned long long)hmax << 32) | lo_max;
-}
-
-// Model-placed counting sort of one span of at most 32*R keys by one warp:
-// each key goes to slot floor((u - min) / (max - min + 1) * 32R) (a linear
-// CDF between the span's extremes), slots are laid out by an exclusive scan
-// of their counts, and an insertion sort inside each slot finishes the job.
-// Returns false (nothing written) when some slot holds more than kMaxSlot
-// keys; the caller then sorts the span with a bitonic network.
+// Counting sort by predicted slot of one span of n keys, 32(R-1) < n <= 32R.
+// The map: with hmin / hmax the smallest / largest high word of the ords,
+// base = hmin:0 and w = the top 32 bits of (u - base) << clz(hmax - hmin)
+// (or, when every key has the same high word, w = (low - lmin) <<
+// clz(lmax - lmin)); slot = floor(w 32R / 2^32).  Monotone in u, so sorting
+// by slot and then inside slots sorts the span.  Slot s belongs to lane
+// s / R (= w >> 27) and is stored at (s mod R) * 32 + s / R, so the per-lane
+// reads of the scan hit distinct banks.  Counts and starts of a lane's
+// slots stay in registers.
 template <int R>
 __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
                                                  uint64_t* sk, uint32_t* sc) {
-  constexpr uint32_t NS = 32 * R, LG = (R == 1 ? 5 : R == 2 ? 6 : R == 4 ? 7 : 8);
-  static_assert((1u << LG) == NS, "slot count");
+  constexpr uint32_t NS = 32 * R;
   const unsigned lane = threadIdx.x & 31;
-  const uint64_t* src = s.buf ? Bbuf : A;
+  const uint64_t* src = (s.buf ? Bbuf : A) + s.lo;
+  const uint32_t n = s.n;
   uint64_t u[R];
-  unsigned long long lmin = ~0ull, lmax = 0;
+  uint32_t hmin = ~0u, hmax = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    uint32_t i = lane + 32 * r;
-    u[r] = i < s.n ? ord_of(src[s.lo + i], dt) : 0;
-    if (i < s.n) {
-      lmin = u[r] < lmin ? u[r] : lmin;
-      lmax = u[r] > lmax ? u[r] : lmax;
+    const bool ok = r < R - 1 || lane + 32 * r < n;
+    u[r] = ok ? ord_of(src[lane + 32 * r], dt) : 0ull;
+    const uint32_t h = (uint32_t)(u[r] >> 32);
+    if (ok) {
+      hmin = min(hmin, h);
+      hmax = max(hmax, h);
     }
   }
-  unsigned long long mn, mx;
-  warp_minmax_u64(lmin, lmax, mn, mx);
-  if (mn == mx) {  // all equal: already sorted; bring home if needed
-    if (s.buf)
-      for (uint32_t i = lane; i < s.n; i += 32) A[s.lo + i] = src[s.lo + i];
-    return true;
-  }
-  const uint32_t sh = __clzll((long long)(mx - mn));
+  hmin = __reduce_min_sync(0xFFFFFFFFu, hmin);
+  hmax = __reduce_max_sync(0xFFFFFFFFu, hmax);
+  uint32_t w[R];
+  if (hmin == hmax) {  // uniform: one high word, exact low-word extremes
+    uint32_t lmin = ~0u, lmax = 0;
 #pragma unroll
-  for (int r = 0; r < R; ++r) sc[lane + 32 * r] = 0;
+    for (int r = 0; r < R; ++r) {
+      if (r < R - 1 || lane + 32 * r < n) {
+        lmin = min(lmin, (uint32_t)u[r]);
+        lmax = max(lmax, (uint32_t)u[r]);
+      }
+    }
+    lmin = __reduce_min_sync(0xFFFFFFFFu, lmin);
+    lmax = __reduce_max_sync(0xFFFFFFFFu, lmax);
+    if (lmin == lmax) {  // all equal: already sorted; bring home if needed
+      if (s.buf)
+        for (uint32_t i = lane; i < n; i += 32) A[s.lo + i] = src[i];
+      return true;
+    }
+    const uint32_t sh = __clz(lmax - lmin);
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = ((uint32_t)u[r] - lmin) << sh;
+  } else {
+    const uint64_t base = (uint64_t)hmin << 32;
+    const uint32_t sh = __clz(hmax - hmin);
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) sc[q * 32 + lane] = 0;
   __syncwarp();
-  uint32_t dg[R], rk[R];
+  uint32_t at[R], rk[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    uint32_t i = lane + 32 * r;
-    dg[r] = (uint32_t)(((u[r] - mn) << sh) >> (64 - LG));
-    rk[r] = i < s.n ? atomicAdd(&sc[dg[r]], 1u) : 0u;
+    const uint32_t slot = __umulhi(w[r], NS), owner = w[r] >> 27;
+    at[r] = (slot - owner * R) * 32 + owner;
+    rk[r] = (r < R - 1 || lane + 32 * r < n) ? atomicAdd(&sc[at[r]], 1u) : 0u;
   }
   __syncwarp();
-  // exclusive scan of the slot counts (R consecutive slots per lane) and the
-  // largest slot
+  // exclusive scan of the slot counts (slots lane*R .. lane*R+R-1 per lane)
   uint32_t c[R], loc = 0, big = 0;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    c[q] = sc[lane * R + q];
+    c[q] = sc[q * 32 + lane];
     loc += c[q];
-    big = c[q] > big ? c[q] : big;
+    big = max(big, c[q]);
   }
   uint32_t incl = loc;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
     if (lane >= (unsigned)d) incl += o;
   }
-  big = __reduce_max_sync(0xFFFFFFFFu, big);
-  if (big > kMaxSlot) return false;  // uniform across the warp
-  __syncwarp();
+  if (__reduce_max_sync(0xFFFFFFFFu, big) > kMaxSlot) return false;  // uniform across the warp
+  uint32_t st[R];
   uint32_t run = incl - loc;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    sc[lane * R + q] = run;  // slot start
+    st[q] = run;
+    sc[q * 32 + lane] = run;  // slot start
     run += c[q];
   }
-  if (lane == 31) sc[NS] = run;
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (lane + 32 * r < s.n) sk[sc[dg[r]] + rk[r]] = u[r];
+    if (r < R - 1 || lane + 32 * r < n) sk[sc[at[r]] + rk[r]] = u[r];
   __syncwarp();
-  // insertion sort inside each slot (a lane owns R consecutive slots)
-  uint32_t a0 = sc[lane * R];
+  // insertion sort inside the lane's slots that hold two or more keys
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const uint32_t a1 = a0 + c[q];
+    if (c[q] < 2) continue;
+    const uint32_t a0 = st[q], a1 = st[q] + c[q];
     for (uint32_t x = a0 + 1; x < a1; ++x) {
-      uint64_t v = sk[x];
+      const uint64_t v = sk[x];
       uint32_t y = x;
       while (y > a0 && sk[y - 1] > v) {
         sk[y] = sk[y - 1];
@@ -1011,14 +1020,11 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
       }
       sk[y] = v;
     }
-    a0 = a1;
   }
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    uint32_t i = lane + 32 * r;
-    if (i < s.n) A[s.lo + i] = unord(sk[i], dt);
-  }
+  for (int r = 0; r < R; ++r)
+    if (r < R - 1 || lane + 32 * r < n) A[s.lo + lane + 32 * r] = unord(sk[lane + 32 * r], dt);
   __syncwarp();
   return true;
 }
@@ -1026,18 +1032,28 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
 __global__ void __launch_bounds__(kTPB, 3) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
                                                      int dt) {
   __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
-  __shared__ uint32_t s_cnt[kTPB / 32][kSlots + 1];
+  __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
   const unsigned wid = threadIdx.x >> 5;
   uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
   for (; w < n; w += nw) {
-    Span s = spans[w];
-    bool done = false;
-    if (s.n >= 16) {
-      if (s.n <= 32) done = warp_placed_sort<1>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
-      else if (s.n <= 64) done = warp_placed_sort<2>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
-      else if (s.n <= 128) done = warp_placed_sort<4>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
-      else done = warp_placed_sort<8>(s, A, Bbuf, dt, s_keys[wid], s_cnt[wid]);
+    const Span s = spans[w];
+    if (s.n < 2) {  // nothing to order; bring home if needed
+      if (s.n == 1 && s.buf && (threadIdx.x & 31) == 0) A[s.lo] = Bbuf[s.lo];
+      continue;
+    }
+    uint64_t* sk = s_keys[wid];
+    uint32_t* sc = s_cnt[wid];
+    bool done;
+    switch ((s.n + 31) >> 5) {  // uniform across the warp
+      case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
+      case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
+      case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
+      case 4: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
+      case 5: done = warp_placed_sort<5>(s, A, Bbuf, dt, sk, sc); break;
+      case 6: done = warp_placed_sort<6>(s, A, Bbuf, dt, sk, sc); break;
+      case 7: done = warp_placed_sort<7>(s, A, Bbuf, dt, sk, sc); break;
+      default: done = warp_placed_sort<8>(s, A, Bbuf, dt, sk, sc); break;
     }
     if (done) continue;
     if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
