@@ -458,12 +458,38 @@ __device__ __forceinline__ double refine_value(const DModel& m, const Leaf* lv, 
   return __dmul_rn(model_F(m, lv, ord_value(u, dt)), P);
 }
 
+// The same value when the root is known to route u to leaf l (every ord of
+// an item whose two ends route to l does: the root is monotone), so the
+// root's FP64 evaluation is skipped.  Same operations as model_F after the
+// routing, hence the same result.
+__device__ __forceinline__ double refine_value_leaf(const DModel& m, const Leaf& l, uint64_t u, double P, int dt) {
+  double xc = dmax(ord_value(u, dt), m.xmin);
+  xc = dmin(xc, m.xmax);
+  double f = leaf_eval(l, xc);
+  f = dmax(f, l.lo);
+  f = dmin(f, l.hi);
+  return __dmul_rn(f, P);
+}
+
+// Evaluator of v for one item: through the root, or straight in the one
+// leaf all of the item's ords route to.
+struct ItemEval {
+  const DModel& m;
+  const Leaf* lv;
+  Leaf one_leaf;
+  bool one;
+  double P;
+  int dt;
+  __device__ __forceinline__ double operator()(uint64_t u) const {
+    return one ? refine_value_leaf(m, one_leaf, u, P, dt) : refine_value(m, lv, u, P, dt);
+  }
+};
+
 // Smallest u in [lo, hi] with v(u) >= t, given v(lo) < t <= v(hi).  v is
 // monotone in u, so any bracketing search is exact.  Interpolation steps
 // (with a bisection every fourth step) also test the neighbour of the
 // estimate, so an estimate within one ord of the pivot closes the bracket.
-__device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64_t lo, uint64_t hi, double t,
-                                 double P, double vlo, double vhi) {
+__device__ uint64_t search_pivot(const ItemEval& v, uint64_t lo, uint64_t hi, double t, double vlo, double vhi) {
   uint64_t L = lo, H = hi;
   double vL = vlo, vH = vhi;
   for (int it = 0; it < 256 && H - L > 1; ++it) {
@@ -483,12 +509,12 @@ __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64
     } else {
       mid = L + (span >> 1);
     }
-    double vm = refine_value(m, lv, mid, P, dt);
+    double vm = v(mid);
     if (vm >= t) {
       H = mid;
       vH = vm;
       if (interp && mid - 1 > L) {
-        double v2 = refine_value(m, lv, mid - 1, P, dt);
+        double v2 = v(mid - 1);
         if (v2 >= t) {
           H = mid - 1;
           vH = v2;
@@ -501,7 +527,7 @@ __device__ uint64_t search_pivot(const DModel& m, const Leaf* lv, int dt, uint64
       L = mid;
       vL = vm;
       if (interp && mid + 1 < H) {
-        double v2 = refine_value(m, lv, mid + 1, P, dt);
+        double v2 = v(mid + 1);
         if (v2 >= t) {
           H = mid + 1;
           vH = v2;
@@ -637,6 +663,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
   else pivot_prep(m, lv, it, P, Bg, B, rp.dt, q);
   const double vlo = q.vlo, vhi = q.vhi;
   const uint32_t kmin = q.kmin, kmax = q.kmax;
+  const ItemEval ev{m, lv, lv[q.l0], q.l0 == q.l1, P, rp.dt};
   if (j == 0) {
     T[0] = lo;
     pl.kmax = kmax;
@@ -677,8 +704,8 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
       // the root starts routing to leaf l0, so that boundary is the pivot
       uint64_t u = root_boundary(m, l0, rp.dt, lo, hi);
       if (u > L && u <= H) {
-        double vu = refine_value(m, lv, u, P, rp.dt);
-        double v2 = refine_value(m, lv, u - 1, P, rp.dt);
+        double vu = ev(u);
+        double v2 = ev(u - 1);
         if (vu >= t && v2 < t) {
           T[j] = u;
           return;
@@ -701,11 +728,11 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
           u = ord_of((uint64_t)__double_as_longlong(xs), 0);
         }
         if (u > L && u < H) {
-          double vu = refine_value(m, lv, u, P, rp.dt);
+          double vu = ev(u);
           if (vu >= t) {
             H = u;
             vH = vu;
-            double v2 = refine_value(m, lv, u - 1, P, rp.dt);
+            double v2 = ev(u - 1);
             if (v2 < t) {
               T[j] = u;
               return;
@@ -717,7 +744,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
           } else {
             L = u;
             vL = vu;
-            double v2 = refine_value(m, lv, u + 1, P, rp.dt);
+            double v2 = ev(u + 1);
             if (v2 >= t) {
               T[j] = u + 1;
               return;
@@ -731,7 +758,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
       }
     }
   }
-  T[j] = search_pivot(m, lv, rp.dt, L, H, t, P, vL, vH);
+  T[j] = search_pivot(ev, L, H, t, vL, vH);
 }
 
 // Classify the candidates' own samples with their learned pivots (sample
