@@ -138,3 +138,62 @@ def segmented(nseg: int, seed: int, lo: float = 1e3, hi: float = 1e6,
         x = generate(d, int(lens[s]), seed * 1_000_003 + s)
         keys[int(off[s]):int(off[s + 1])] = shift[s] + scale[s] * x
     return keys, off, names
+
+
+def skewed_u64_device(n: int, seed: int, device: str = "cuda:0"):
+    """The skewed u64 workload generated on a GPU (for 2e9 keys, where the
+    numpy generator above would take minutes), as an int64 tensor holding
+    the u64 bit patterns.  Same recipe, not the same bytes:
+      * 64 equal-width pieces of [0, 2^64) with Dirichlet(0.3) masses and a
+        random linear density per piece (slope in [-1, 1]); the offset inside
+        a piece comes from inverting that density in FP32, which fixes its
+        top 24 bits, and the remaining 34 bits are uniform;
+      * each position is, with probability 1/100, a cluster key instead:
+        center + floor(LogN(0, 2)), saturating, 100 uniform u64 centers.
+    Piece masses, slopes and centers are drawn with numpy from `seed`; the
+    per-key draws use a torch generator seeded from it."""
+    import torch
+
+    g = _rng(seed, 3000)
+    masses = g.dirichlet(np.full(64, 0.3))
+    slope_np = g.uniform(-1.0, 1.0, 64)
+    centers_np = g.integers(0, 2 ** 63, size=100, dtype=np.uint64) * np.uint64(2) + \
+        g.integers(0, 2, size=100, dtype=np.uint64)
+    tg = torch.Generator(device=device)
+    tg.manual_seed(int(g.integers(0, 2 ** 62)))
+    cdf = torch.tensor(np.cumsum(masses), dtype=torch.float64, device=device)
+    cdf[-1] = 1.0
+    slope = torch.tensor(slope_np, dtype=torch.float32, device=device)
+    centers = torch.tensor(centers_np.view(np.int64), device=device)
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    step = 1 << 27
+    for a in range(0, n, step):
+        m = min(step, n - a)
+        u_piece = torch.rand(m, generator=tg, device=device, dtype=torch.float64)
+        piece = torch.searchsorted(cdf, u_piece, right=True).clamp_(max=63)
+        del u_piece
+        s = slope[piece]
+        u = torch.rand(m, generator=tg, device=device, dtype=torch.float32)
+        # inverse CDF of f(t) = 1 + s (2t - 1) on [0, 1)
+        disc = torch.sqrt(torch.clamp((1.0 - s) ** 2 + 4.0 * s * u, min=0.0))
+        t = torch.where(s.abs() < 1e-6, u, ((s - 1.0) + disc) / (2.0 * s)).clamp_(0.0, 0.99999994)
+        del s, u, disc
+        top = (t * 16777216.0).to(torch.int64)  # 24 bits
+        low = torch.randint(0, 1 << 34, (m,), generator=tg, device=device, dtype=torch.int64)
+        key = (piece.to(torch.int64) << 58) | (top << 34) | low
+        del t, top, low, piece
+        clu = torch.rand(m, generator=tg, device=device, dtype=torch.float32) < 0.01
+        k = int(clu.sum())
+        if k:
+            c = torch.randint(0, 100, (k,), generator=tg, device=device)
+            z = torch.randn(k, generator=tg, device=device, dtype=torch.float32)
+            off = torch.floor(torch.exp(2.0 * z)).to(torch.int64)
+            base = centers[c]
+            # unsigned saturating add on int64 bit patterns: the sum wrapped
+            # iff it is below the base in unsigned order
+            ssum = base + off
+            mn = -(1 << 63)
+            wrapped = (ssum ^ mn) < (base ^ mn)
+            key[clu] = torch.where(wrapped, torch.full_like(base, -1), ssum)
+        out[a:a + m] = key
+    return out

@@ -265,6 +265,10 @@ class Context:
     def handle(self):
         return self._h
 
+    def free_workspace(self):
+        """Drop the cached workspace tensor (its memory returns to torch's allocator)."""
+        self._ws = None
+
     def workspace(self, n: int, nseg: int, dtype: int, p: Params):
         import torch
         nbytes = ls_workspace_size(self, n, nseg, dtype, p)
