@@ -214,6 +214,18 @@ ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets
  * in the context between calls.  Synchronous. */
 ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, const ls_params* p, ls_stats* out_stats);
 
+/* ls_sort_host for `count` host arrays (array i: h_keys[i], n[i] keys, each
+ * overwritten with its sorted keys).  The copies are pipelined with the
+ * sorts on three context streams: array i + 1 is copied in while array i
+ * is sorted and array i - 1 is copied out (the host link carries both
+ * directions at once).  The overlap needs page-locked host arrays
+ * (cudaMallocHost / cudaHostRegister); pageable arrays are still sorted
+ * correctly.  Device memory (three arrays of the largest size plus one
+ * workspace) is cached in the context.  out_stats (nullable) receives one
+ * ls_stats per array.  Synchronous: returns when every array is back. */
+ls_status ls_sort_host_batch(ls_ctx* ctx, void* const* h_keys, const uint64_t* n, uint32_t count, ls_dtype dtype,
+                             const ls_params* p, ls_stats* out_stats);
+
 /* Train the root model exactly as ls_sort would (sample with the root's
  * seed, sort the sample, fit; Sec. 2.2 / Alg. 5) and copy it to *out_model.
  * Also returns the root decision inputs in *out_stats (nullable).

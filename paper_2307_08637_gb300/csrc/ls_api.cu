@@ -795,13 +795,18 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
       result = (ls_status)dstat;
       break;
     }
-    ls_status r = finish_spans(s, c);
-    if (r != LS_OK) return r;
+    // the next level's items are complete (K2 wrote them): read them back
+    // before the base case is launched, so the host plans the next level
+    // while the GPU sorts this level's finished spans
     if (c.n_next) {
       items.resize(c.n_next);
       CK(cudaMemcpyAsync(items.data(), at<Item>(ws, lay.o_next), c.n_next * sizeof(Item), cudaMemcpyDeviceToHost,
                          st));
       CK(cudaStreamSynchronize(st));
+    }
+    ls_status r = finish_spans(s, c);
+    if (r != LS_OK) return r;
+    if (c.n_next) {
       // keep only models still referenced by refine items
       std::vector<uint8_t> live(lay.mcap, 0);
       for (const Item& it : items)
@@ -910,6 +915,8 @@ void ls_destroy(ls_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_cache) cudaFree(ctx->d_cache);
+  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out})
+    if (s) cudaStreamDestroy(s);
   delete ctx;
 }
 
@@ -941,10 +948,10 @@ ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets
 ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, const ls_params* p,
                        ls_stats* out_stats) {
   if (!ctx || (!h_keys && n)) return LS_EINVAL;
-  ls_status vs = validate_params(p);
+  size_t wsb = 0;
+  ls_status vs = ls_workspace_size(ctx, n, 1, dtype, p, &wsb);  // tuned parameters included
   if (vs != LS_OK) return vs;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
-  size_t wsb = compute_layout(n, 1, p).total;
   size_t keyb = up(n * 8);
   ls_status r = ensure_cache(ctx, keyb + wsb + kAlign);
   if (r != LS_OK) return r;
@@ -956,6 +963,81 @@ ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, co
   if (r != LS_OK) return r;
   if (cudaMemcpy(h_keys, d_keys, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LS_ECUDA;
   return LS_OK;
+}
+
+ls_status ls_sort_host_batch(ls_ctx* ctx, void* const* h_keys, const uint64_t* n, uint32_t count, ls_dtype dtype,
+                             const ls_params* p, ls_stats* out_stats) {
+  if (!ctx || (count && (!h_keys || !n))) return LS_EINVAL;
+  uint64_t nmax = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (!h_keys[i] && n[i]) return LS_EINVAL;
+    nmax = std::max(nmax, n[i]);
+  }
+  size_t wsb = 0;
+  ls_status vs = ls_workspace_size(ctx, nmax, 1, dtype, p, &wsb);  // grows with n: fits every array
+  if (vs != LS_OK) return vs;
+  if (count == 0) return LS_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
+  for (cudaStream_t* s : {&ctx->s_sort, &ctx->s_in, &ctx->s_out})
+    if (!*s && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess) return LS_ECUDA;
+  // three key buffers: array i sorts in slot i % 3 while i + 1 arrives and
+  // i - 1 leaves
+  const uint32_t nb = count < 3 ? count : 3;
+  const size_t keyb = up(nmax * 8);
+  ls_status r = ensure_cache(ctx, nb * keyb + wsb + kAlign);
+  if (r != LS_OK) return r;
+  char* base = static_cast<char*>(ctx->d_cache);
+  void* ws = base + nb * keyb;
+  cudaEvent_t ev[3][3];  // [slot][in, sorted, out]
+  int made = 0;
+  for (uint32_t q = 0; q < nb && r == LS_OK; ++q)
+    for (int k = 0; k < 3 && r == LS_OK; ++k) {
+      if (cudaEventCreateWithFlags(&ev[q][k], cudaEventDisableTiming) != cudaSuccess) r = LS_ECUDA;
+      else ++made;
+    }
+  // big transfers go in pieces, so that the sort's own small per-level
+  // copies (plans, counters) do not queue behind a whole array on the copy
+  // engines
+  static constexpr size_t kPiece = size_t(32) << 20;
+  auto copy = [](void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) -> bool {
+    for (size_t o = 0; o < bytes; o += kPiece)
+      if (cudaMemcpyAsync(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o,
+                          std::min(kPiece, bytes - o), kind, st) != cudaSuccess)
+        return false;
+    return true;
+  };
+  auto h2d = [&](uint32_t i) -> bool {
+    const uint32_t q = i % nb;
+    if (i >= nb && cudaStreamWaitEvent(ctx->s_in, ev[q][2], 0) != cudaSuccess) return false;
+    if (!copy(base + q * keyb, h_keys[i], n[i] * 8, cudaMemcpyHostToDevice, ctx->s_in)) return false;
+    return cudaEventRecord(ev[q][0], ctx->s_in) == cudaSuccess;
+  };
+  if (r == LS_OK && !h2d(0)) r = LS_ECUDA;
+  for (uint32_t i = 0; i < count && r == LS_OK; ++i) {
+    if (i + 1 < count && !h2d(i + 1)) {
+      r = LS_ECUDA;
+      break;
+    }
+    const uint32_t q = i % nb;
+    if (cudaStreamWaitEvent(ctx->s_sort, ev[q][0], 0) != cudaSuccess) {
+      r = LS_ECUDA;
+      break;
+    }
+    r = ls_sort(ctx, base + q * keyb, n[i], dtype, p, ws, wsb, out_stats ? &out_stats[i] : nullptr, ctx->s_sort);
+    if (r != LS_OK) break;
+    if (cudaEventRecord(ev[q][1], ctx->s_sort) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->s_out, ev[q][1], 0) != cudaSuccess ||
+        !copy(h_keys[i], base + q * keyb, n[i] * 8, cudaMemcpyDeviceToHost, ctx->s_out) ||
+        cudaEventRecord(ev[q][2], ctx->s_out) != cudaSuccess)
+      r = LS_ECUDA;
+  }
+  // drain every stream before the buffers can be reused or the call returns
+  for (cudaStream_t s : {ctx->s_in, ctx->s_sort, ctx->s_out})
+    if (cudaStreamSynchronize(s) != cudaSuccess && r == LS_OK) r = LS_ECUDA;
+  for (uint32_t q = 0; q < nb; ++q)
+    for (int k = 0; k < 3; ++k)
+      if (made-- > 0) cudaEventDestroy(ev[q][k]);
+  return r;
 }
 
 ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p,

@@ -5,6 +5,8 @@
 #include <map>
 #include <mutex>
 
+#include <cuda_runtime.h>
+
 #include "../../include/ls.h"
 
 // Parameters the autotuner picked for one (key type, floor(log2 n)) class.
@@ -23,6 +25,9 @@ struct ls_ctx {
   void* d_cache = nullptr;
   size_t d_cache_bytes = 0;
   uint64_t launches = 0;
+  // streams of ls_sort_host_batch (created on first use): sort, host->device,
+  // device->host
+  cudaStream_t s_sort = nullptr, s_in = nullptr, s_out = nullptr;
   // autotuner results, keyed by dtype * 64 + floor(log2 n)
   std::map<int, ls_tuned_entry> tuned;
   std::mutex tuned_mu;

@@ -30,6 +30,7 @@ EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
     "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_tune_export", "ls_tune_import",
+    "ls_sort_host_batch",
 )
 
 
@@ -174,6 +175,9 @@ def lib() -> C.CDLL:
     L.ls_sort_segmented.restype = C.c_int
     L.ls_sort_host.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Stats)]
     L.ls_sort_host.restype = C.c_int
+    L.ls_sort_host_batch.argtypes = [vp, C.POINTER(vp), C.POINTER(u64), u32, C.c_int, C.POINTER(Params),
+                                     C.POINTER(Stats)]
+    L.ls_sort_host_batch.restype = C.c_int
     L.ls_fit.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Model), C.POINTER(Stats), vp, vp]
     L.ls_fit.restype = C.c_int
     L.ls_classify.argtypes = [vp, C.POINTER(Model), vp, u64, C.c_int, u32, u64, i32, vp, vp, vp]
@@ -330,6 +334,28 @@ def ls_sort_host(ctx: Context, keys: np.ndarray, p: Params | None = None) -> Sta
     st = Stats()
     _check(lib().ls_sort_host(ctx.handle, keys.ctypes.data, keys.size, dt, C.byref(p), C.byref(st)), "ls_sort_host")
     return st
+
+
+def ls_sort_host_batch(ctx: Context, arrays, p: Params | None = None, stats: bool = False):
+    """Sort several host numpy arrays (float64 or uint64, one dtype) in place,
+    copies pipelined with the sorts; returns the per-array Stats when asked."""
+    p = p or ls_params_default()
+    arrays = list(arrays)
+    if not arrays:
+        return [] if stats else None
+    kinds = {a.dtype for a in arrays}
+    if len(kinds) != 1 or arrays[0].dtype not in (np.float64, np.uint64):
+        raise TypeError("arrays must all be float64 or all uint64")
+    for a in arrays:
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+    dt = LS_F64 if arrays[0].dtype == np.float64 else LS_U64
+    cnt = len(arrays)
+    ptrs = (C.c_void_p * cnt)(*[a.ctypes.data for a in arrays])
+    ns = (C.c_uint64 * cnt)(*[a.size for a in arrays])
+    st = (Stats * cnt)() if stats else None
+    _check(lib().ls_sort_host_batch(ctx.handle, ptrs, ns, cnt, dt, C.byref(p), st), "ls_sort_host_batch")
+    return list(st) if stats else None
 
 
 def ls_fit(ctx: Context, keys, p: Params | None = None, want_sample: bool = False, stream=None):
