@@ -134,7 +134,7 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_chunkctr, o_fmodels, o_fleaves, o_ids;
+      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
@@ -200,6 +200,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
   l.o_excl = take(l.chunk_cap * l.nbc * 8);
   l.seg_cap = l.chunk_cap / kSegChunks + kBatchItems + 8;
   l.o_segs = take(l.seg_cap * sizeof(ChunkSeg));
+  l.o_multi = take((size_t)kBatchItems * sizeof(uint2));
   l.o_chunkctr = take(8);
   l.misc_bytes = 16 * (kBatchItems + 8) * 8;
   l.o_misc = take(l.misc_bytes);
@@ -455,6 +456,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       fa.items = d_items;
       fa.cand = d_cand;
       fa.cand_soff = d_csoff;
+      fa.nbp_max = pow2ceil(p->fanout);
       fa.rchunk_prefix = d_rcp;
       fa.ncand = (uint32_t)cand.size();
       fa.total_rchunks = rchunk_prefix.back();
@@ -585,11 +587,11 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
   // per-chunk prefixes of the K1 counts, in runs of kSegChunks chunks
   std::vector<ChunkSeg> segs;
-  bool multi = false;
+  std::vector<uint2> multi;  // items with several runs: (first run, runs)
   for (uint32_t i = 0; i < nitems; ++i) {
     uint64_t cb = plans[i].chunk_begin, nc = (its[i].n + ck - 1) / ck;
     uint32_t first = (uint32_t)segs.size();
-    multi |= nc > kSegChunks;
+    if (nc > kSegChunks) multi.push_back(make_uint2(first, (uint32_t)((nc + kSegChunks - 1) / kSegChunks)));
     for (uint64_t c = 0; c < nc; c += kSegChunks) {
       ChunkSeg g;
       g.c0 = cb + c;
@@ -600,12 +602,16 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       segs.push_back(g);
     }
   }
-  if (segs.size() > L.seg_cap) return LS_ENOMEM;
+  if (segs.size() > L.seg_cap || multi.size() > kBatchItems) return LS_ENOMEM;
   ChunkSeg* d_segs = at<ChunkSeg>(s.ws, L.o_segs);
+  uint2* d_multi = at<uint2>(s.ws, L.o_multi);
   if (!segs.empty())
     CK(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(ChunkSeg), cudaMemcpyHostToDevice, st));
+  if (!multi.empty())
+    CK(cudaMemcpyAsync(d_multi, multi.data(), multi.size() * sizeof(uint2), cudaMemcpyHostToDevice, st));
   s.timer.begin(LS_PASS_CHILDREN, 0);
-  s.launches += launch_chunk_prefix(d_segs, (uint32_t)segs.size(), multi, d_plans, pa.agg, pa.excl, nbp_max, st);
+  s.launches += launch_chunk_prefix(d_segs, (uint32_t)segs.size(), d_multi, (uint32_t)multi.size(), d_plans, pa.agg,
+                                    pa.excl, nbp_max, st);
   launch_children(ca, s.rp, st);
   s.timer.end();
   s.timer.begin(LS_PASS_SCATTER, batch_keys);
@@ -1121,6 +1127,7 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
   fa.items = d_items;
   fa.cand = reinterpret_cast<uint32_t*>(misc + 2 * M);
   fa.cand_soff = misc + 3 * M;
+  fa.nbp_max = pow2ceil(q.fanout);
   fa.rchunk_prefix = misc + 4 * M;
   fa.ncand = 1;
   fa.total_rchunks = rcp[1];

@@ -762,19 +762,33 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
 }
 
 // Classify the candidates' own samples with their learned pivots (sample
-// imbalance test) and keep the largest bucket.
+// imbalance test).  Block (x, c) takes a stride of candidate c's samples:
+// the candidate's pivot table and a histogram live in shared memory, and
+// the block adds its histogram to the candidate's counts at the end.
 __global__ void k_imbalance_count(FitArgs a, const uint64_t* __restrict__ pivots,
-                                  unsigned long long* __restrict__ cnt) {
-  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= a.total_cand_samples) return;
-  uint32_t c = find_seg(a.cand_soff, a.ncand, g);
-  uint64_t j = g - a.cand_soff[c];
+                                  unsigned long long* __restrict__ cnt, uint32_t nbp_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* sH = reinterpret_cast<uint32_t*>(sT + nbp_max);
+  const uint32_t c = blockIdx.y;
   const Plan& pl = a.plans[a.cand[c]];
-  if (!a.models[pl.model].ok) return;
-  uint64_t u = a.samp[pl.sample_off + j];
-  uint32_t b = pivot_count(pivots + pl.tab_off, pl.nb_pad, u);
-  b = b < pl.kmax ? b : pl.kmax;
-  atomicAdd(&cnt[pl.cnt_off + b], 1ull);
+  if (!a.models[pl.model].ok) return;  // uniform across the block
+  const uint32_t nbp = pl.nb_pad;
+  for (uint32_t j = threadIdx.x; j < nbp; j += blockDim.x) {
+    sT[j] = pivots[pl.tab_off + j];
+    sH[j] = 0;
+  }
+  __syncthreads();
+  const uint64_t S = a.cand_soff[c + 1] - a.cand_soff[c];
+  const uint64_t* samp = a.samp + pl.sample_off;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < S; j += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t b = pivot_count(sT, nbp, samp[j]);
+    b = b < pl.kmax ? b : pl.kmax;
+    atomicAdd(&sH[b], 1u);
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < nbp; j += blockDim.x)
+    if (sH[j]) atomicAdd(&cnt[pl.cnt_off + j], (unsigned long long)sH[j]);
 }
 
 __global__ void k_imbalance_max(FitArgs a, unsigned long long* __restrict__ cnt) {
@@ -1227,7 +1241,21 @@ void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cn
                       cudaStream_t st, uint64_t* launches) {
   (void)rp;
   if (!a.ncand) return;
-  k_imbalance_count<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, pivots, cnt_pool);
+  // candidates' tables are at most nb_pad_max entries (the learned fanout, padded)
+  const uint32_t nbp_max = a.nbp_max;
+  const size_t sm = (size_t)nbp_max * 12;
+  static size_t set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (sm > set[dev]) {
+    cudaFuncSetAttribute(k_imbalance_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set[dev] = sm;
+  }
+  const uint64_t per = (a.total_cand_samples + a.ncand - 1) / a.ncand;  // mean samples per candidate
+  uint64_t gx = (per + kTPB * 8 - 1) / (kTPB * 8);
+  gx = gx < 1 ? 1 : (gx > 256 ? 256 : gx);
+  k_imbalance_count<<<dim3((unsigned)gx, a.ncand), kTPB, sm, st>>>(a, pivots, cnt_pool, nbp_max);
   k_imbalance_max<<<a.ncand, kTPB, 0, st>>>(a, cnt_pool);
   *launches += 2;
 }

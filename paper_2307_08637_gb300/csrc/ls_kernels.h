@@ -72,6 +72,7 @@ struct FitArgs {
   DModel* models;
   Leaf* leaves;
   uint32_t L;
+  uint32_t nbp_max;            // pivot table length of a learned candidate (L padded to a power of two)
   // scratch
   double* rpart;               // 4 * total_rchunks
   uint32_t* leaf_start;        // ncand * (L+1)
@@ -160,10 +161,11 @@ struct ChunkSeg {
   uint32_t pad;
 };
 // Per-chunk exclusive prefixes of the K1 counts within each item: one pass
-// per run, then (when some item spans several runs) the runs' carries.
+// per run, then, for the items spanning several runs (multi: first run and
+// run count per such item), a scan of the run totals and the carries.
 // Returns launches.
-int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, bool multi, const Plan* plans, uint32_t* agg,
-                        unsigned long long* excl, uint32_t nbp, cudaStream_t st);
+int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
+                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
 
 struct ChildArgs {

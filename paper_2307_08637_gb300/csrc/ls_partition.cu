@@ -520,16 +520,39 @@ __global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __
   agg[sg.c0 * nbp + b] = (uint32_t)run;  // at most kSegChunks * kChunkKeys
 }
 
-// Carry pass: add the totals of the item's earlier runs.
+// Carry scan: for each item with several runs and each bucket column, the
+// exclusive prefix over its runs of the run totals, in place (the total in
+// the run's first row becomes the keys of that bucket in the item's earlier
+// runs).  One thread per column; the loads of eight runs are issued together.
+__global__ void k_run_scan(const uint2* __restrict__ multi, const ChunkSeg* __restrict__ segs,
+                           const Plan* __restrict__ plans, uint32_t* agg, uint32_t nbp) {
+  const uint2 mi = multi[blockIdx.x];  // (first run, number of runs)
+  const ChunkSeg f = segs[mi.x];
+  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (b >= plans[f.plan].nb_pad) return;
+  const uint64_t c0 = f.c0;
+  uint32_t run = 0;
+  for (uint32_t r0 = 0; r0 < mi.y; r0 += 8) {
+    uint32_t t[8];
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k)
+      t[k] = r0 + k < mi.y ? agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k) {
+      if (r0 + k < mi.y) agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] = run;
+      run += t[k];
+    }
+  }
+}
+
+// Carry pass: add each run's carry (from k_run_scan) to its chunks.
 __global__ void k_chunk_carry(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans,
                               const uint32_t* __restrict__ agg, unsigned long long* __restrict__ excl, uint32_t nbp) {
   const ChunkSeg sg = segs[blockIdx.x];
   if (blockIdx.x == sg.first) return;
   const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
   if (b >= plans[sg.plan].nb_pad) return;
-  const uint64_t cf = segs[sg.first].c0;
-  unsigned long long carry = 0;
-  for (uint32_t r = sg.first; r < blockIdx.x; ++r) carry += agg[(cf + (uint64_t)(r - sg.first) * kSegChunks) * nbp + b];
+  const unsigned long long carry = agg[sg.c0 * nbp + b];
   for (uint32_t j = 0; j < sg.nch; ++j) excl[(sg.c0 + j) * nbp + b] += carry;
 }
 
@@ -1365,14 +1388,15 @@ int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st
   return n;
 }
 
-int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, bool multi, const Plan* plans, uint32_t* agg,
-                        unsigned long long* excl, uint32_t nbp, cudaStream_t st) {
+int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
+                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st) {
   if (!nsegs) return 0;
-  dim3 grid(nsegs, (nbp + kTPB - 1) / kTPB);
-  k_chunk_prefix<<<grid, kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
-  if (!multi) return 1;
-  k_chunk_carry<<<grid, kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
-  return 2;
+  const unsigned cols = (nbp + kTPB - 1) / kTPB;
+  k_chunk_prefix<<<dim3(nsegs, cols), kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  if (!nmulti) return 1;
+  k_run_scan<<<dim3(nmulti, cols), kTPB, 0, st>>>(multi, segs, plans, agg, nbp);
+  k_chunk_carry<<<dim3(nsegs, cols), kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  return 3;
 }
 
 template <int MODE>
