@@ -209,6 +209,18 @@ ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets
                             const ls_params* p, void* d_workspace, size_t ws_bytes, ls_stats* out_stats,
                             int32_t* h_seg_decision, ls_stream_t stream);
 
+/* Key-value sort (a payload carried with each key, e.g. row ids of a
+ * database column; argsort when the values are 0..n-1): sorts d_keys[0..n)
+ * ascending by ord exactly as ls_sort does and applies the same permutation
+ * to d_vals[0..n) (val_bytes = 4 or 8 bytes each).  Stable: values of equal
+ * keys keep their input order.  The workspace (ls_workspace_size_pairs)
+ * also holds a ping-pong buffer of the values.  Same conventions as ls_sort. */
+ls_status ls_workspace_size_pairs(ls_ctx* ctx, uint64_t n, uint32_t val_bytes, ls_dtype dtype, const ls_params* p,
+                                  size_t* bytes);
+ls_status ls_sort_pairs(ls_ctx* ctx, void* d_keys, void* d_vals, uint32_t val_bytes, uint64_t n, ls_dtype dtype,
+                        const ls_params* p, void* d_workspace, size_t ws_bytes, ls_stats* out_stats,
+                        ls_stream_t stream);
+
 /* End-to-end sort of a HOST array: copies h_keys to the device, sorts, and
  * copies the result back (h_keys is overwritten).  Device memory is cached
  * in the context between calls.  Synchronous. */

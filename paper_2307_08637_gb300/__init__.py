@@ -12,7 +12,7 @@ been built: there is no CPU or library fallback.
 from .ls import (  # noqa: F401
     EXPORTS, LIB_PATH, Context, LevelStats, LSError, Model, Params, Stats, lib, ls_classify, ls_classify_static, ls_fit, ls_fit_grad,
     ls_last_device_status, ls_model_export, ls_model_import, ls_params_default, ls_sort, ls_sort_host,
-    ls_sort_host_batch,
+    ls_sort_host_batch, ls_sort_pairs, ls_argsort,
     ls_sort_segmented, ls_workspace_size, status_string, ls_autotune, ls_tune_export, ls_tune_import, TuneReport,
     save_tuning, load_tuning, tune_text_to_json, tune_json_to_text,
     LS_OK, LS_EINVAL, LS_ENOMEM, LS_ENAN, LS_ETIMEOUT, LS_ECUDA, LS_ENOTIMPL, LS_EDEVICE,

@@ -134,12 +134,13 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids;
+      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids,
+      o_vbuf;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
 
-Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
+Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb = 0) {
   Layout l;
   l.n = n;
   l.L = p->fanout;
@@ -168,6 +169,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p) {
     return r;
   };
   l.o_buf = take(n * 8);
+  l.o_vbuf = vb ? take(n * vb) : 0;  // key-value sorts: ping-pong buffer of the values
   l.o_ids = take(n * 2);
   l.o_cur = take(l.icap * sizeof(Item));
   l.o_next = take(l.icap * sizeof(Item));
@@ -280,6 +282,9 @@ struct Sorter {
   cudaStream_t st;
   uint64_t* A;
   uint64_t* Bb;
+  void* VA = nullptr;   // key-value sorts: the caller's values ...
+  void* VBb = nullptr;  // ... and their ping-pong buffer
+  uint32_t vb = 0;      // bytes per value (0: keys only)
   int dt;
   std::vector<int> model_free;
   std::vector<uint8_t> model_used;
@@ -559,6 +564,9 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
   pa.aux_bytes = aux;
   pa.cls_mask = cls_mask;
+  pa.valsA = s.VA;
+  pa.valsB = s.VBb;
+  pa.vbytes = s.vb;
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
   pa.chunk_keys = ck;
   CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
@@ -654,15 +662,18 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
   Layout& L = s.lay;
   if (c.n_base_small || c.n_base_large || c.n_fallback) {
     s.timer.begin(LS_PASS_BASE, 0);
-    if (c.n_base_small) launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.dt, s.st);
+    if (c.n_base_small)
+      launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st);
     if (c.n_base_large)
-      launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.dt, s.st);
-    if (c.n_fallback) launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.dt, s.st);
+      launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.VA, s.VBb,
+                        s.vb, s.dt, s.st);
+    if (c.n_fallback)
+      launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st);
     s.timer.end();
   }
   if (c.n_copy) {
     s.timer.begin(LS_PASS_COPY, 0);
-    launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.st);
+    launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.VA, s.VBb, s.vb, s.st);
     s.timer.end();
   }
   s.launches += (c.n_base_small > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
@@ -672,7 +683,7 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
 
 ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32_t nseg, ls_dtype dtype,
                     const ls_params* p, void* ws, size_t ws_bytes, ls_stats* out_stats, int32_t* seg_dec,
-                    cudaStream_t st) {
+                    cudaStream_t st, void* d_vals = nullptr, uint32_t vb = 0) {
   auto t0 = std::chrono::steady_clock::now();
   if (!ctx || !p || (!d_keys && h_off[nseg] > 0) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
   const ls_params eff = effective_params(ctx, h_off[nseg], nseg, dtype, *p);
@@ -684,7 +695,9 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   uint64_t n = h_off[nseg];
   for (uint32_t s = 0; s < nseg; ++s)
     if (h_off[s + 1] - h_off[s] >= (1ull << 32)) return LS_EINVAL;
-  Layout lay = compute_layout(n, nseg, p);
+  if (vb != 0 && vb != 4 && vb != 8) return LS_EINVAL;
+  if (vb && !d_vals && h_off[nseg] > 0) return LS_EINVAL;
+  Layout lay = compute_layout(n, nseg, p, vb);
   if (n > 0 && (!ws || ws_bytes < lay.total)) return LS_ENOMEM;
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LS_EINVAL;
   CK(cudaSetDevice(ctx->device));
@@ -706,6 +719,9 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   s.st = st;
   s.A = d_keys;
   s.Bb = at<uint64_t>(ws, lay.o_buf);
+  s.VA = d_vals;
+  s.VBb = vb ? static_cast<void*>(at<unsigned char>(ws, lay.o_vbuf)) : nullptr;
+  s.vb = vb;
   s.seg_decision = seg_dec;
   s.nseg = nseg;
   s.timer.on = (p->flags & LS_FLAG_TIME_PASSES) != 0;
@@ -949,6 +965,25 @@ ls_status ls_sort_segmented(ls_ctx* ctx, void* d_keys, const uint64_t* h_offsets
   if (!h_offsets || nseg == 0) return LS_EINVAL;
   return sort_impl(ctx, static_cast<uint64_t*>(d_keys), h_offsets, nseg, dtype, p, d_workspace, ws_bytes,
                    out_stats, h_seg_decision, static_cast<cudaStream_t>(stream));
+}
+
+ls_status ls_workspace_size_pairs(ls_ctx* ctx, uint64_t n, uint32_t val_bytes, ls_dtype dtype, const ls_params* p,
+                                  size_t* bytes) {
+  if (!bytes || !p || (dtype != LS_F64 && dtype != LS_U64) || (val_bytes != 4 && val_bytes != 8)) return LS_EINVAL;
+  const ls_params eff = effective_params(ctx, n, 1, dtype, *p);
+  ls_status vs = validate_params(&eff);
+  if (vs != LS_OK) return vs;
+  *bytes = compute_layout(n, 1, &eff, val_bytes).total;
+  return LS_OK;
+}
+
+ls_status ls_sort_pairs(ls_ctx* ctx, void* d_keys, void* d_vals, uint32_t val_bytes, uint64_t n, ls_dtype dtype,
+                        const ls_params* p, void* d_workspace, size_t ws_bytes, ls_stats* out_stats,
+                        ls_stream_t stream) {
+  if (val_bytes != 4 && val_bytes != 8) return LS_EINVAL;
+  uint64_t off[2] = {0, n};
+  return sort_impl(ctx, static_cast<uint64_t*>(d_keys), off, 1, dtype, p, d_workspace, ws_bytes, out_stats, nullptr,
+                   static_cast<cudaStream_t>(stream), d_vals, val_bytes);
 }
 
 ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, const ls_params* p,

@@ -140,6 +140,9 @@ struct PassArgs {
   unsigned long long* excl;     // per chunk: keys of each bucket in the item's earlier chunks
   unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
   uint64_t chunk_keys;          // keys per chunk: a multiple of the tile, at most kChunkKeys
+  void* valsA;                  // key-value sorts: payload of buffer A (caller's values) ...
+  void* valsB;                  // ... and of the ping-pong buffer B
+  uint32_t vbytes;              // bytes per value: 0 (keys only), 4 or 8
   unsigned int* status;         // device status word
   int check_nan;
   uint32_t nb_pad_max;
@@ -190,11 +193,16 @@ struct ChildArgs {
 };
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st);
 
-void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, int dt, cudaStream_t st);
-void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, int dt,
-                       cudaStream_t st);
-void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, cudaStream_t st);
-void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, int dt, cudaStream_t st);
+// Base cases, copies home and the depth-limit fallback.  VA / VBuf / vb:
+// values of a key-value sort (vb = 4 or 8 bytes; 0 for keys only).
+void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
+                       uint32_t vb, int dt, cudaStream_t st);
+void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                       const void* VBuf, uint32_t vb, int dt, cudaStream_t st);
+void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
+                       uint32_t vb, cudaStream_t st);
+void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
+                     int dt, cudaStream_t st);
 
 // ls_classify helpers
 void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,

@@ -300,9 +300,14 @@ enum K3Mode {
   K3_MASK_OWN = 2     // per-warp masks in their own area (nb_pad <= 2 kMaskBuckets)
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter(PassArgs a, RunParams rp) {
+// Payload type of a key-value sort: VB bytes per value (0: keys only).
+template <int VB>
+using ValT = typename std::conditional<VB == 8, uint64_t, uint32_t>::type;
+
+template <int MODE, int VB>
+__global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1) k_scatter(PassArgs a, RunParams rp) {
   constexpr bool MASK = MODE != K3_MATCH;
+  using V = ValT<VB>;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t nbp = a.nb_pad_max;
   uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);          // next destination per bucket
@@ -319,6 +324,9 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
   uint32_t* const masks =
       MODE == K3_MASK_OWN ? reinterpret_cast<uint32_t*>(sid + kTile) : reinterpret_cast<uint32_t*>(stage);
   uint32_t* wm = masks + wid * nbp;
+  // staged values (key-value sorts): after the masks' own area or the ids
+  V* const sv = reinterpret_cast<V*>(MODE == K3_MASK_OWN ? reinterpret_cast<unsigned char*>(masks + kWarps * nbp)
+                                                          : reinterpret_cast<unsigned char*>(sid + kTile));
   const unsigned lt = (1u << lane) - 1u;
   for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp; j += kTPB) wcnt[j] = 0;
   for (uint32_t j = threadIdx.x; j < kTile * 2; j += kTPB) reinterpret_cast<uint32_t*>(stage)[j] = 0;
@@ -346,10 +354,13 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
     const uint16_t* idin = a.ids + it.lo + c0;
     uint64_t* dst = it.buf ? a.outA : a.outB;
+    const V* vsrc = VB ? static_cast<const V*>(it.buf ? a.valsB : a.valsA) + it.lo + c0 : nullptr;
+    V* vdst = VB ? static_cast<V*>(it.buf ? a.valsA : a.valsB) : nullptr;
     const uint64_t lo = it.lo, n = it.n;
     const uint32_t Q = (nbk + kTPB - 1) / kTPB;  // bucket ranges of kTPB (at most 16)
     uint64_t v[kKPT];
     uint32_t bk[kKPT];
+    V vv[VB ? kKPT : 1];
     auto load_tile = [&](uint64_t t0) {
       const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
       const uint64_t* s = src + t0 + wid * kWarpKeys + lane;
@@ -359,6 +370,7 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
         for (int k = 0; k < kKPT; ++k) {
           v[k] = s[k * 32];
           bk[k] = d[k * 32];
+          if constexpr (VB != 0) vv[k] = vsrc[t0 + wid * kWarpKeys + lane + k * 32];
         }
       } else {
 #pragma unroll
@@ -366,6 +378,7 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
           const uint32_t pos = wid * kWarpKeys + k * 32 + lane;
           v[k] = pos < len ? s[k * 32] : 0;
           bk[k] = pos < len ? (uint32_t)d[k * 32] : 0xFFFFu;
+          if constexpr (VB != 0) vv[k] = pos < len ? vsrc[t0 + pos] : V(0);
         }
       }
     };
@@ -466,6 +479,7 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
         if (!FULL && !valid) p = kTile - 1;
         stage[p] = v[k];
         sid[p] = (uint16_t)bb;
+        if constexpr (VB != 0) sv[p] = vv[k];
       }
       // prefetch the next tile while the staged one is written out
       if (t0 + kTile < clen) load_tile(t0 + kTile);
@@ -475,7 +489,10 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? 3 : 1) k_scatter
         const uint64_t x = stage[p];
         if (MODE == K3_MASK_STAGE) stage[p] = 0;  // peer masks of the next tile start from zero
         const bool ok = o - lo < n;  // K1 and K3 disagree: never write outside the item
-        if (ok) dst[o] = x;
+        if (ok) {
+          dst[o] = x;
+          if constexpr (VB != 0) vdst[o] = sv[p];
+        }
         oob |= !ok;
       };
       if constexpr (FULL) {
@@ -923,6 +940,85 @@ __device__ __forceinline__ void warp_sort_span(const Span& s, uint64_t* A, const
   }
 }
 
+// Key-value forms of the base cases: the networks and the slot sort order
+// (ord key, position in the span) pairs, so equal keys keep their input
+// order (a stable sort), and each output position takes the value of the
+// input position it ended with.
+
+// Warp bitonic network over 32E (key, index) pairs held E per lane.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_kv(uint64_t (&v)[E], uint32_t (&ix)[E]) {
+  const unsigned lane = threadIdx.x & 31;
+  constexpr uint32_t P = 32 * E;
+#pragma unroll
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= (uint32_t)E) {
+        const int lm = (int)(j / E);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const uint32_t i = lane * E + r;
+          const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v[r], lm);
+          const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, ix[r], lm);
+          const bool up = (i & k) == 0, lower = (i & j) == 0;
+          const bool mine_less = v[r] < o || (v[r] == o && ix[r] < oi);
+          const bool keep = (lower == up) == mine_less;  // keep the smaller when lower==up
+          v[r] = keep ? v[r] : o;
+          ix[r] = keep ? ix[r] : oi;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if ((r & (int)j) == 0) {
+            const uint32_t i = lane * E + r;
+            const bool up = (i & k) == 0;
+            const uint64_t x = v[r], y = v[r ^ j];
+            const uint32_t xi = ix[r], yi = ix[r ^ j];
+            const bool gt = x > y || (x == y && xi > yi);
+            if (gt == up) {
+              v[r] = y;
+              v[r ^ j] = x;
+              ix[r] = yi;
+              ix[r ^ j] = xi;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int E, int VB>
+__device__ __forceinline__ void warp_sort_span_kv(const Span& s, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                                                  const void* VBuf, int dt) {
+  using V = ValT<VB>;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t* src = s.buf ? Bbuf : A;
+  const V* vsrc = static_cast<const V*>(s.buf ? VBuf : VA) + s.lo;
+  uint64_t v[E];
+  uint32_t ix[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const uint32_t i = lane * E + r;
+    v[r] = i < s.n ? ord_of(src[s.lo + i], dt) : ~0ull;
+    ix[r] = i;
+  }
+  warp_bitonic_kv<E>(v, ix);
+  V val[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) val[r] = lane * E + r < s.n ? vsrc[ix[r]] : V(0);
+  __syncwarp();  // every value is read before any is overwritten (vsrc may be VA)
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const uint32_t i = lane * E + r;
+    if (i < s.n) {
+      A[s.lo + i] = unord(v[r], dt);
+      static_cast<V*>(VA)[s.lo + i] = val[r];
+    }
+  }
+}
+
 // Model-placed base case for one span of <= 256 keys, done by one warp (the
 // GPU form of LearnedSort 2.0's counting sort by predicted position plus an
 // insertion-sort fix, Sec. 2.2): inside a bucket the keys are close to
@@ -1083,6 +1179,339 @@ __global__ void __launch_bounds__(kTPB, 3) k_base_small(const Span* spans, uint6
     else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
     else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
     else warp_sort_span<8>(s, A, Bbuf, dt);
+  }
+}
+
+// warp_placed_sort for a key-value span: the slots order (ord key, index)
+// pairs (si holds each staged key's index in the span), and the values are
+// gathered by index at the end.  Same slot map as the keys-only form.
+template <int R, int VB>
+__device__ __forceinline__ bool warp_placed_sort_kv(const Span& s, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                                                    const void* VBuf, int dt, uint64_t* sk, uint16_t* si,
+                                                    uint32_t* sc) {
+  using V = ValT<VB>;
+  constexpr uint32_t NS = 32 * R;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t* src = (s.buf ? Bbuf : A) + s.lo;
+  const V* vsrc = static_cast<const V*>(s.buf ? VBuf : VA) + s.lo;
+  const uint32_t n = s.n;
+  uint64_t u[R];
+  uint32_t hmin = ~0u, hmax = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const bool ok = r < R - 1 || lane + 32 * r < n;
+    u[r] = ok ? ord_of(src[lane + 32 * r], dt) : 0ull;
+    const uint32_t h = (uint32_t)(u[r] >> 32);
+    if (ok) {
+      hmin = min(hmin, h);
+      hmax = max(hmax, h);
+    }
+  }
+  hmin = __reduce_min_sync(0xFFFFFFFFu, hmin);
+  hmax = __reduce_max_sync(0xFFFFFFFFu, hmax);
+  uint32_t w[R];
+  if (hmin == hmax) {
+    uint32_t lmin = ~0u, lmax = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r < R - 1 || lane + 32 * r < n) {
+        lmin = min(lmin, (uint32_t)u[r]);
+        lmax = max(lmax, (uint32_t)u[r]);
+      }
+    }
+    lmin = __reduce_min_sync(0xFFFFFFFFu, lmin);
+    lmax = __reduce_max_sync(0xFFFFFFFFu, lmax);
+    if (lmin == lmax) {  // all equal: input order is the stable order
+      if (s.buf)
+        for (uint32_t i = lane; i < n; i += 32) {
+          A[s.lo + i] = src[i];
+          static_cast<V*>(VA)[s.lo + i] = vsrc[i];
+        }
+      return true;
+    }
+    const uint32_t sh = __clz(lmax - lmin);
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = ((uint32_t)u[r] - lmin) << sh;
+  } else {
+    const uint64_t base = (uint64_t)hmin << 32;
+    const uint32_t sh = __clz(hmax - hmin);
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) sc[q * 32 + lane] = 0;
+  __syncwarp();
+  uint32_t at[R], rk[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t slot = __umulhi(w[r], NS), owner = w[r] >> 27;
+    at[r] = (slot - owner * R) * 32 + owner;
+    rk[r] = (r < R - 1 || lane + 32 * r < n) ? atomicAdd(&sc[at[r]], 1u) : 0u;
+  }
+  __syncwarp();
+  uint32_t c[R], loc = 0, big = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    c[q] = sc[q * 32 + lane];
+    loc += c[q];
+    big = max(big, c[q]);
+  }
+  uint32_t incl = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl += o;
+  }
+  if (__reduce_max_sync(0xFFFFFFFFu, big) > kMaxSlot) return false;
+  uint32_t st[R];
+  uint32_t run = incl - loc;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    st[q] = run;
+    sc[q * 32 + lane] = run;
+    run += c[q];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < R - 1 || lane + 32 * r < n) {
+      const uint32_t p = sc[at[r]] + rk[r];
+      sk[p] = u[r];
+      si[p] = (uint16_t)(lane + 32 * r);
+    }
+  __syncwarp();
+  // insertion sort by (key, index) inside the lane's slots of >= 2 keys
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (c[q] < 2) continue;
+    const uint32_t a0 = st[q], a1 = st[q] + c[q];
+    for (uint32_t x = a0 + 1; x < a1; ++x) {
+      const uint64_t v = sk[x];
+      const uint16_t vi = si[x];
+      uint32_t y = x;
+      while (y > a0 && (sk[y - 1] > v || (sk[y - 1] == v && si[y - 1] > vi))) {
+        sk[y] = sk[y - 1];
+        si[y] = si[y - 1];
+        --y;
+      }
+      sk[y] = v;
+      si[y] = vi;
+    }
+  }
+  __syncwarp();
+  V val[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    val[r] = (r < R - 1 || lane + 32 * r < n) ? vsrc[si[lane + 32 * r]] : V(0);
+  __syncwarp();  // every value is read before any is overwritten (vsrc may be VA)
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < R - 1 || lane + 32 * r < n) {
+      A[s.lo + lane + 32 * r] = unord(sk[lane + 32 * r], dt);
+      static_cast<V*>(VA)[s.lo + lane + 32 * r] = val[r];
+    }
+  __syncwarp();
+  return true;
+}
+
+template <int VB>
+__global__ void __launch_bounds__(kTPB, 3) k_base_small_kv(const Span* spans, uint64_t n, uint64_t* A,
+                                                        const uint64_t* Bbuf, void* VA, const void* VBuf, int dt) {
+  using V = ValT<VB>;
+  __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
+  __shared__ uint16_t s_idx[kTPB / 32][kWarpSortMax];
+  __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
+  const unsigned wid = threadIdx.x >> 5;
+  uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
+  for (; w < n; w += nw) {
+    const Span s = spans[w];
+    if (s.n < 2) {
+      if (s.n == 1 && s.buf && (threadIdx.x & 31) == 0) {
+        A[s.lo] = Bbuf[s.lo];
+        static_cast<V*>(VA)[s.lo] = static_cast<const V*>(VBuf)[s.lo];
+      }
+      continue;
+    }
+    uint64_t* sk = s_keys[wid];
+    uint16_t* si = s_idx[wid];
+    uint32_t* sc = s_cnt[wid];
+    bool done;
+    switch ((s.n + 31) >> 5) {  // uniform across the warp
+      case 1: done = warp_placed_sort_kv<1, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 2: done = warp_placed_sort_kv<2, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 3: done = warp_placed_sort_kv<3, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 4: done = warp_placed_sort_kv<4, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 5: done = warp_placed_sort_kv<5, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 6: done = warp_placed_sort_kv<6, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      case 7: done = warp_placed_sort_kv<7, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+      default: done = warp_placed_sort_kv<8, VB>(s, A, Bbuf, VA, VBuf, dt, sk, si, sc); break;
+    }
+    if (done) continue;
+    if (s.n <= 32) warp_sort_span_kv<1, VB>(s, A, Bbuf, VA, VBuf, dt);
+    else if (s.n <= 64) warp_sort_span_kv<2, VB>(s, A, Bbuf, VA, VBuf, dt);
+    else if (s.n <= 128) warp_sort_span_kv<4, VB>(s, A, Bbuf, VA, VBuf, dt);
+    else warp_sort_span_kv<8, VB>(s, A, Bbuf, VA, VBuf, dt);
+  }
+}
+
+// Block bitonic network over P (ord key, index) pairs in shared memory.
+__device__ void block_bitonic_smem_kv(uint64_t* sm, uint32_t* si, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t x = sm[i], y = sm[ixj];
+          const uint32_t xi = si[i], yi = si[ixj];
+          const bool up = (i & k) == 0;
+          const bool gt = x > y || (x == y && xi > yi);
+          if (gt == up) {
+            sm[i] = y;
+            sm[ixj] = x;
+            si[i] = yi;
+            si[ixj] = xi;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// CTA base case (257 .. 8192 keys) of a key-value sort.
+template <int VB>
+__global__ void __launch_bounds__(1024) k_base_large_kv(const Span* spans, uint64_t n, uint64_t* A,
+                                                        const uint64_t* Bbuf, void* VA, const void* VBuf, int dt) {
+  using V = ValT<VB>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    const Span s = spans[w];
+    const uint64_t* src = s.buf ? Bbuf : A;
+    const V* vsrc = static_cast<const V*>(s.buf ? VBuf : VA) + s.lo;
+    uint32_t P = 2;
+    while (P < s.n) P <<= 1;
+    uint32_t* si = reinterpret_cast<uint32_t*>(sm + P);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+      sm[i] = i < s.n ? ord_of(src[s.lo + i], dt) : ~0ull;
+      si[i] = i;
+    }
+    __syncthreads();
+    block_bitonic_smem_kv(sm, si, P);
+    // values gathered into registers first: the source may be the destination
+    V val[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t i = threadIdx.x + r * blockDim.x;
+      val[r] = i < s.n ? vsrc[si[i]] : V(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t i = threadIdx.x + r * blockDim.x;
+      if (i < s.n) {
+        A[s.lo + i] = unord(sm[i], dt);
+        static_cast<V*>(VA)[s.lo + i] = val[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int VB>
+__global__ void k_copy_spans_kv(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                                const void* VBuf) {
+  using V = ValT<VB>;
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    const Span s = spans[w];
+    for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+      A[s.lo + i] = Bbuf[s.lo + i];
+      static_cast<V*>(VA)[s.lo + i] = static_cast<const V*>(VBuf)[s.lo + i];
+    }
+  }
+}
+
+// Depth-limit fallback of a key-value sort: runs of 2048 sorted by (ord,
+// index) in shared memory with their values gathered, then stable merge
+// passes (equal keys: the left run first) moving (key, value) pairs between
+// the two buffers; the result lands in A.
+template <int VB>
+__global__ void __launch_bounds__(1024) k_fallback_kv(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
+                                                      void* VA, void* VBuf, int dt) {
+  using V = ValT<VB>;
+  __shared__ uint64_t sm[kSortChunk];
+  __shared__ uint32_t si[kSortChunk];
+  for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
+    const Span s = spans[w];
+    uint64_t* src = s.buf ? Bbuf : A;
+    uint64_t* oth = s.buf ? A : Bbuf;
+    V* vsrc = static_cast<V*>(s.buf ? VBuf : VA);
+    V* voth = static_cast<V*>(s.buf ? VA : VBuf);
+    for (uint64_t r0 = 0; r0 < s.n; r0 += kSortChunk) {
+      const uint32_t len = (uint32_t)(s.n - r0 < kSortChunk ? s.n - r0 : kSortChunk);
+      for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+        sm[i] = i < len ? ord_of(src[s.lo + r0 + i], dt) : ~0ull;
+        si[i] = i;
+      }
+      __syncthreads();
+      block_bitonic_smem_kv(sm, si, kSortChunk);
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        oth[s.lo + r0 + i] = sm[i];
+        voth[s.lo + r0 + i] = vsrc[s.lo + r0 + si[i]];
+      }
+      __syncthreads();
+    }
+    uint64_t* cur = oth;
+    uint64_t* nxt = src;
+    V* vcur = voth;
+    V* vnxt = vsrc;
+    for (uint64_t wd = kSortChunk; wd < s.n; wd *= 2) {
+      for (uint64_t o = (uint64_t)threadIdx.x * 8; o < s.n; o += (uint64_t)blockDim.x * 8) {
+        const uint64_t a0 = (o / (2 * wd)) * (2 * wd);
+        const uint64_t a1 = a0 + wd < s.n ? a0 + wd : s.n;
+        const uint64_t b1 = a0 + 2 * wd < s.n ? a0 + 2 * wd : s.n;
+        const uint64_t na = a1 - a0, nbb = b1 - a1;
+        const uint64_t* X = cur + s.lo + a0;
+        const uint64_t* Y = cur + s.lo + a1;
+        const V* XV = vcur + s.lo + a0;
+        const V* YV = vcur + s.lo + a1;
+        const uint64_t diag = o - a0;
+        uint64_t lo = diag > nbb ? diag - nbb : 0, hi = diag < na ? diag : na;
+        while (lo < hi) {  // stable merge path: X[i] goes before Y[j] when X[i] <= Y[j]
+          const uint64_t mid = (lo + hi) >> 1;
+          if (X[mid] <= Y[diag - 1 - mid]) lo = mid + 1;
+          else hi = mid;
+        }
+        uint64_t i = lo, j = diag - lo;
+        const uint64_t lim = b1 - o < 8 ? b1 - o : 8;
+        for (uint64_t k = 0; k < lim; ++k) {
+          const bool takeX = (j >= nbb) || (i < na && X[i] <= Y[j]);
+          if (takeX) {
+            nxt[s.lo + o + k] = X[i];
+            vnxt[s.lo + o + k] = XV[i++];
+          } else {
+            nxt[s.lo + o + k] = Y[j];
+            vnxt[s.lo + o + k] = YV[j++];
+          }
+        }
+      }
+      __syncthreads();
+      uint64_t* t = cur;
+      cur = nxt;
+      nxt = t;
+      V* tv = vcur;
+      vcur = vnxt;
+      vnxt = tv;
+    }
+    V* VAv = static_cast<V*>(VA);
+    for (uint64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+      const uint64_t k = cur[s.lo + i];
+      const V v = vcur[s.lo + i];
+      A[s.lo + i] = unord(k, dt);  // cur may be A itself: same index, read first
+      VAv[s.lo + i] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -1399,24 +1828,31 @@ int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi
   return 3;
 }
 
-template <int MODE>
+template <int MODE, int VB>
 static void launch_k3(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
-  size_t sm = k3_smem(a) + (MODE == K3_MASK_OWN ? (size_t)kWarps * a.nb_pad_max * 4 : 0);
+  size_t sm = k3_smem(a) + (MODE == K3_MASK_OWN ? (size_t)kWarps * a.nb_pad_max * 4 : 0) + (size_t)VB * kTile;
   static size_t set[64] = {};
-  allow_smem(k_scatter<MODE>, sm, set);
+  allow_smem(k_scatter<MODE, VB>, sm, set);
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MODE>, kTPB, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MODE, VB>, kTPB, sm);
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_scatter<MODE><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  k_scatter<MODE, VB><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+}
+
+template <int VB>
+static void launch_k3_vb(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
+  if (a.nb_pad_max <= kMaskBuckets) launch_k3<K3_MASK_STAGE, VB>(a, rp, st);
+  else if (a.nb_pad_max <= 2 * kMaskBuckets) launch_k3<K3_MASK_OWN, VB>(a, rp, st);
+  else launch_k3<K3_MATCH, VB>(a, rp, st);
 }
 
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (!a.nchunks) return;
-  if (a.nb_pad_max <= kMaskBuckets) launch_k3<K3_MASK_STAGE>(a, rp, st);
-  else if (a.nb_pad_max <= 2 * kMaskBuckets) launch_k3<K3_MASK_OWN>(a, rp, st);
-  else launch_k3<K3_MATCH>(a, rp, st);
+  if (a.vbytes == 8) launch_k3_vb<8>(a, rp, st);
+  else if (a.vbytes == 4) launch_k3_vb<4>(a, rp, st);
+  else launch_k3_vb<0>(a, rp, st);
 }
 
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
@@ -1427,20 +1863,38 @@ void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   k_children<<<a.nitems, 1024, sm, st>>>(a, rp);
 }
 
-void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, int dt, cudaStream_t st) {
+void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
+                       uint32_t vb, int dt, cudaStream_t st) {
   if (!n) return;
   uint64_t warps = n;
   uint64_t blocks = (warps * 32 + kTPB - 1) / kTPB;
   uint64_t cap = (uint64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
-  k_base_small<<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, dt);
+  if (vb == 8) k_base_small_kv<8><<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+  else if (vb == 4) k_base_small_kv<4><<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+  else k_base_small<<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, dt);
 }
 
-void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, int dt,
-                       cudaStream_t st) {
+template <typename F>
+static void launch_large(F* f, const Span* spans, uint64_t n, uint32_t P, size_t sm, cudaStream_t st, size_t* set,
+                         uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf, int dt) {
+  allow_smem(f, sm, set);
+  uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
+  uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
+  f<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+}
+
+void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                       const void* VBuf, uint32_t vb, int dt, cudaStream_t st) {
   if (!n) return;
   uint32_t P = 2;
   while (P < max_len) P <<= 1;
+  if (vb) {  // (key, index) pairs: 12 bytes per slot
+    static size_t set8[64] = {}, set4[64] = {};
+    if (vb == 8) launch_large(k_base_large_kv<8>, spans, n, P, (size_t)P * 12, st, set8, A, Bbuf, VA, VBuf, dt);
+    else launch_large(k_base_large_kv<4>, spans, n, P, (size_t)P * 12, st, set4, A, Bbuf, VA, VBuf, dt);
+    return;
+  }
   size_t sm = (size_t)P * 8;
   static size_t set[64] = {};
   allow_smem(k_base_large, sm, set);
@@ -1449,16 +1903,22 @@ void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t
   k_base_large<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, dt);
 }
 
-void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, cudaStream_t st) {
+void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
+                       uint32_t vb, cudaStream_t st) {
   if (!n) return;
   uint64_t grid = n < (uint64_t)sm_count() * 16 ? n : (uint64_t)sm_count() * 16;
-  k_copy_spans<<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf);
+  if (vb == 8) k_copy_spans_kv<8><<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf);
+  else if (vb == 4) k_copy_spans_kv<4><<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf);
+  else k_copy_spans<<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf);
 }
 
-void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, int dt, cudaStream_t st) {
+void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
+                     int dt, cudaStream_t st) {
   if (!n) return;
   uint64_t grid = n < (uint64_t)sm_count() * 2 ? n : (uint64_t)sm_count() * 2;
-  k_fallback<<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, dt);
+  if (vb == 8) k_fallback_kv<8><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+  else if (vb == 4) k_fallback_kv<4><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+  else k_fallback<<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, dt);
 }
 
 void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,

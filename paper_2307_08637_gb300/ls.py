@@ -30,7 +30,7 @@ EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
     "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_tune_export", "ls_tune_import",
-    "ls_sort_host_batch",
+    "ls_sort_host_batch", "ls_sort_pairs", "ls_workspace_size_pairs",
 )
 
 
@@ -175,6 +175,11 @@ def lib() -> C.CDLL:
     L.ls_sort_segmented.restype = C.c_int
     L.ls_sort_host.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Stats)]
     L.ls_sort_host.restype = C.c_int
+    L.ls_sort_pairs.argtypes = [vp, vp, vp, u32, u64, C.c_int, C.POINTER(Params), vp, C.c_size_t, C.POINTER(Stats),
+                                vp]
+    L.ls_sort_pairs.restype = C.c_int
+    L.ls_workspace_size_pairs.argtypes = [vp, u64, u32, C.c_int, C.POINTER(Params), C.POINTER(C.c_size_t)]
+    L.ls_workspace_size_pairs.restype = C.c_int
     L.ls_sort_host_batch.argtypes = [vp, C.POINTER(vp), C.POINTER(u64), u32, C.c_int, C.POINTER(Params),
                                      C.POINTER(Stats)]
     L.ls_sort_host_batch.restype = C.c_int
@@ -273,6 +278,14 @@ class Context:
         """Drop the cached workspace tensor (its memory returns to torch's allocator)."""
         self._ws = None
 
+    def workspace_bytes(self, nbytes: int):
+        """A cached device workspace of at least nbytes."""
+        import torch
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = None
+            self._ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
     def workspace(self, n: int, nseg: int, dtype: int, p: Params):
         import torch
         nbytes = ls_workspace_size(self, n, nseg, dtype, p)
@@ -301,6 +314,36 @@ def ls_sort(ctx: Context, keys, p: Params | None = None, workspace=None, stream=
         _check(rc, "ls_sort")
     st.status = rc if rc else st.status
     return st
+
+
+def ls_sort_pairs(ctx: Context, keys, vals, p: Params | None = None, stream=None, check: bool = True) -> Stats:
+    """Sort keys in place and permute vals (4- or 8-byte elements, same length)
+    the same way; stable for equal keys."""
+    p = p or ls_params_default()
+    dt = _dtype_code(keys)
+    n = keys.numel()
+    if vals.numel() != n or vals.element_size() not in (4, 8) or not vals.is_contiguous():
+        raise ValueError("vals must be a contiguous tensor of n 4- or 8-byte elements")
+    vb = vals.element_size()
+    nb = C.c_size_t()
+    _check(lib().ls_workspace_size_pairs(ctx.handle, n, vb, dt, C.byref(p), C.byref(nb)), "ls_workspace_size_pairs")
+    ws = ctx.workspace_bytes(nb.value)
+    st = Stats()
+    rc = lib().ls_sort_pairs(ctx.handle, _ptr(keys), _ptr(vals), vb, n, dt, C.byref(p), _ptr(ws), ws.numel(),
+                             C.byref(st), _stream(stream))
+    if check:
+        _check(rc, "ls_sort_pairs")
+    return st
+
+
+def ls_argsort(ctx: Context, keys, p: Params | None = None, stream=None):
+    """Sort keys in place and return the stable argsort of the original keys
+    (int64 indices: sorted[i] = original[idx[i]])."""
+    import torch
+    n = keys.numel()
+    idx = torch.arange(n, dtype=torch.int32 if n < 2**31 else torch.int64, device=keys.device)
+    ls_sort_pairs(ctx, keys, idx, p, stream)
+    return idx.long()
 
 
 def ls_sort_segmented(ctx: Context, keys, offsets, p: Params | None = None, workspace=None, stream=None,
