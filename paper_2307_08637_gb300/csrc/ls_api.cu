@@ -1047,10 +1047,27 @@ ls_status ls_sort_host_batch(ls_ctx* ctx, void* const* h_keys, const uint64_t* n
         return false;
     return true;
   };
+  // page-locked arrays mapped into the device's address space move through a
+  // small copy kernel over the host link, which leaves the copy engines to
+  // the sorts' own small copies; other arrays go through the engines
+  std::vector<void*> mapped(count, nullptr);
+  for (uint32_t i = 0; i < count; ++i) {
+    cudaPointerAttributes at;
+    if (h_keys[i] && cudaPointerGetAttributes(&at, h_keys[i]) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer)
+      mapped[i] = at.devicePointer;
+    else
+      cudaGetLastError();  // clear a lookup failure of an unregistered pointer
+  }
   auto h2d = [&](uint32_t i) -> bool {
     const uint32_t q = i % nb;
     if (i >= nb && cudaStreamWaitEvent(ctx->s_in, ev[q][2], 0) != cudaSuccess) return false;
-    if (!copy(base + q * keyb, h_keys[i], n[i] * 8, cudaMemcpyHostToDevice, ctx->s_in)) return false;
+    if (mapped[i]) {
+      launch_link_copy(mapped[i], base + q * keyb, n[i] * 8, ctx->s_in);
+      if (cudaGetLastError() != cudaSuccess) return false;
+    } else if (!copy(base + q * keyb, h_keys[i], n[i] * 8, cudaMemcpyHostToDevice, ctx->s_in)) {
+      return false;
+    }
     return cudaEventRecord(ev[q][0], ctx->s_in) == cudaSuccess;
   };
   if (r == LS_OK && !h2d(0)) r = LS_ECUDA;
@@ -1068,7 +1085,9 @@ ls_status ls_sort_host_batch(ls_ctx* ctx, void* const* h_keys, const uint64_t* n
     if (r != LS_OK) break;
     if (cudaEventRecord(ev[q][1], ctx->s_sort) != cudaSuccess ||
         cudaStreamWaitEvent(ctx->s_out, ev[q][1], 0) != cudaSuccess ||
-        !copy(h_keys[i], base + q * keyb, n[i] * 8, cudaMemcpyDeviceToHost, ctx->s_out) ||
+        (mapped[i] ? (launch_link_copy(base + q * keyb, mapped[i], n[i] * 8, ctx->s_out),
+                      cudaGetLastError() != cudaSuccess)
+                   : !copy(h_keys[i], base + q * keyb, n[i] * 8, cudaMemcpyDeviceToHost, ctx->s_out)) ||
         cudaEventRecord(ev[q][2], ctx->s_out) != cudaSuccess)
       r = LS_ECUDA;
   }

@@ -193,6 +193,10 @@ struct ChildArgs {
 };
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st);
 
+// Copy bytes (a multiple of 8) between device memory and mapped page-locked
+// host memory with a small kernel (16 blocks) instead of a copy engine.
+void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st);
+
 // Base cases, copies home and the depth-limit fallback.  VA / VBuf / vb:
 // values of a key-value sort (vb = 4 or 8 bytes; 0 for keys only).
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,

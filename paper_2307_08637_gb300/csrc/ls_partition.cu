@@ -1613,6 +1613,36 @@ __global__ void __launch_bounds__(1024) k_fallback(const Span* spans, uint64_t n
   }
 }
 
+// ---------------------------------------------------- host <-> device
+
+// Copy `bytes` (a multiple of 8) between device memory and page-locked host
+// memory mapped into the device's address space, with loads and stores over
+// the host link instead of a copy engine (the engines stay free for a
+// concurrent sort's small copies).  16-byte words when both ends allow.
+__global__ void k_link_copy(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst, size_t bytes) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    const size_t n16 = bytes / 16;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+      const uint4 a = s4[i], b = s4[i + stride], c = s4[i + 2 * stride], d = s4[i + 3 * stride];
+      d4[i] = a;
+      d4[i + stride] = b;
+      d4[i + 2 * stride] = c;
+      d4[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) d4[i] = s4[i];
+    if (bytes % 16 && blockIdx.x == 0 && threadIdx.x == 0)
+      *reinterpret_cast<uint2*>(dst + bytes - 8) = *reinterpret_cast<const uint2*>(src + bytes - 8);
+  } else {
+    const uint2* s2 = reinterpret_cast<const uint2*>(src);
+    uint2* d2 = reinterpret_cast<uint2*>(dst);
+    for (const size_t n8 = bytes / 8; i < n8; i += stride) d2[i] = s2[i];
+  }
+}
+
 // ---------------------------------------------------- ls_classify kernels
 
 __global__ void k_direct_classify(const DModel* mp, const Leaf* leaves, const uint64_t* __restrict__ keys, uint64_t n,
@@ -1919,6 +1949,11 @@ void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
   if (vb == 8) k_fallback_kv<8><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
   else if (vb == 4) k_fallback_kv<4><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
   else k_fallback<<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, dt);
+}
+
+void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st) {
+  if (!bytes) return;
+  k_link_copy<<<16, 512, 0, st>>>(static_cast<const unsigned char*>(src), static_cast<unsigned char*>(dst), bytes);
 }
 
 void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,
