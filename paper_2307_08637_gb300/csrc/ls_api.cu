@@ -30,6 +30,7 @@ using namespace lsg;
 namespace {
 
 constexpr uint32_t kBatchItems = 2048;
+constexpr uint64_t kPinItems = 4096;  // next-level items read back with the level counters
 constexpr uint32_t kDirBits = 13;
 constexpr size_t kAlign = 256;
 
@@ -804,11 +805,29 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
       first = false;
       b0 = b1;
     }
+    // one readback per level: counters, device status and the first
+    // kPinItems next-level items (K2 wrote them), into page-locked memory
     LevelCounters c;
-    CK(cudaMemcpyAsync(&c, d_ctr, sizeof c, cudaMemcpyDeviceToHost, st));
     unsigned int dstat = 0;
-    CK(cudaMemcpyAsync(&dstat, ctx->d_status, sizeof dstat, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    const uint64_t pin_items = std::min<uint64_t>(kPinItems, lay.icap);
+    {
+      const size_t need = sizeof(LevelCounters) + 16 + pin_items * sizeof(Item);
+      if (ctx->h_pin_bytes < need) {
+        if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+        ctx->h_pin = nullptr;
+        ctx->h_pin_bytes = 0;
+        CK(cudaHostAlloc(&ctx->h_pin, need, cudaHostAllocDefault));
+        ctx->h_pin_bytes = need;
+      }
+      char* hp = static_cast<char*>(ctx->h_pin);
+      CK(cudaMemcpyAsync(hp, d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hp + sizeof(LevelCounters), ctx->d_status, sizeof dstat, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hp + sizeof(LevelCounters) + 16, at<Item>(ws, lay.o_next), pin_items * sizeof(Item),
+                         cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      memcpy(&c, hp, sizeof c);
+      memcpy(&dstat, hp + sizeof(LevelCounters), sizeof dstat);
+    }
     if (c.overflow) {
       fprintf(stderr, "ls: workspace list capacity exceeded at level %u\n", level);
       return LS_ENOMEM;
@@ -822,9 +841,13 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     // while the GPU sorts this level's finished spans
     if (c.n_next) {
       items.resize(c.n_next);
-      CK(cudaMemcpyAsync(items.data(), at<Item>(ws, lay.o_next), c.n_next * sizeof(Item), cudaMemcpyDeviceToHost,
-                         st));
-      CK(cudaStreamSynchronize(st));
+      const uint64_t first = std::min<uint64_t>(c.n_next, pin_items);
+      memcpy(items.data(), static_cast<char*>(ctx->h_pin) + sizeof(LevelCounters) + 16, first * sizeof(Item));
+      if (c.n_next > first) {
+        CK(cudaMemcpyAsync(items.data() + first, at<Item>(ws, lay.o_next) + first, (c.n_next - first) * sizeof(Item),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      }
     }
     ls_status r = finish_spans(s, c);
     if (r != LS_OK) return r;
@@ -939,6 +962,7 @@ void ls_destroy(ls_ctx* ctx) {
   if (ctx->d_cache) cudaFree(ctx->d_cache);
   for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out})
     if (s) cudaStreamDestroy(s);
+  if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   delete ctx;
 }
 
