@@ -9,7 +9,9 @@
   per-level statistics (decisions, bucket fills, base-case counts);
 * the 2e9-key skewed u64 workload (RETRAIN recursion): the sorted output
   against the independent sort, and the root model against the oracle's on
-  the same bytes.
+  the same bytes;
+* the 4096-segment float64 batch (6.3e8 keys): every segment against
+  independent stable sorts, per-segment root decisions against the oracle's.
 """
 import numpy as np
 import pytest
@@ -104,3 +106,33 @@ def test_full_2e9_u64_skewed_retrain(ctx):
     ctx.free_workspace()
     want = independent_sort(bits, lsg.LS_U64)
     assert torch.equal(work, want)
+
+
+def test_full_c4_segmented_4096(ctx):
+    """4096 float64 segments (6.3e8 keys): every segment sorted exactly
+    (independent stable sorts: by ord, then by segment), and the per-segment
+    root decisions equal to the oracle's on a sample of segments."""
+    keys, off, names = datagen.segmented(4096, 4)
+    p = lsg.ls_params_default(basecase_threshold=T)
+    d = torch.from_numpy(keys).to("cuda:0")
+    st, dec = lsg.ls_sort_segmented(ctx, d, off, p)
+    got = d.view(torch.int64)
+    ctx.free_workspace()
+    bits = torch.from_numpy(keys.view(np.int64)).to("cuda:0")
+    lens = torch.from_numpy(np.diff(off).astype(np.int64)).to("cuda:0")
+    seg = torch.repeat_interleave(torch.arange(lens.numel(), device="cuda:0"), lens)
+    o = ord_signed(bits, lsg.LS_F64)
+    o, perm = torch.sort(o, stable=True)
+    seg = seg[perm]
+    del perm
+    seg, perm = torch.sort(seg, stable=True)
+    want = ord_signed(o[perm], lsg.LS_F64)
+    del o, perm, seg
+    assert torch.equal(got, want)
+    op = oracle.params(basecase_threshold=T)
+    for s in range(0, 4096, 128):
+        x = keys[int(off[s]):int(off[s + 1])]
+        if x.size <= T:
+            continue
+        tr, _, _, _ = oracle.root_decision(x, op, segment=s)
+        assert dec[s] == tr.root_decision, s
