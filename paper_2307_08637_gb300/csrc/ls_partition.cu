@@ -1,15 +1,16 @@
 // ls_partition.cu -- the partitioning side of learned SampleSort on GB300:
-//   K1  classify + per-item histogram (+ min/max for the homogeneity check of
-//       Sec. 2.2, + NaN check), shared-memory histograms with warp-aggregated
-//       atomics (__match_any_sync);
-//   K2  per item: exclusive scan of bucket counts, bucket write cursors,
-//       children (next level / base case / final), level statistics;
-//   K3  scatter: classify again, rank keys per bucket in shared memory, take
-//       each bucket's slice of the output with one atomic fetch-and-add per
-//       (tile, bucket) (the IPS4o parallelisation idea of Sec. 2.4), stage the
-//       tile bucket-by-bucket in shared memory and write contiguous runs;
-//   base case: warp-register bitonic sort (<= 256 keys) and shared-memory
-//       bitonic sort (<= 8192 keys); fallback merge sort past max_depth.
+//   K1  classify + per-chunk histogram (+ homogeneity flag for the check of
+//       Sec. 2.2, + NaN check), shared-memory histograms, u16 bucket ids;
+//   chunk prefixes: per chunk and bucket, where the chunk's keys of that
+//       bucket start (a stable counting sort's offsets, Sec. 2.4);
+//   K2  per item: bucket write cursors, children (next level / base case /
+//       final), level statistics;
+//   K3  stable scatter: rank keys per bucket with warp votes and warp-private
+//       counters, stage each tile grouped by bucket in shared memory and
+//       write contiguous runs;
+//   base case: warp model-placed counting sort (<= 256 keys), shared-memory
+//       bitonic sort (<= 4096 keys), merge-sort fallback past max_depth;
+//   key-value forms of K3 and the base cases, copies, the host-link copy.
 #include <cstdio>
 
 #include <type_traits>
@@ -246,39 +247,31 @@ __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams
 
 // ------------------------------------------------------------------ K3
 
-constexpr uint32_t kWarps = kTPB / 32;
-constexpr uint32_t kWarpKeys = kTile / kWarps;  // keys of a tile ranked by one warp
-constexpr uint32_t kMaskBuckets = kTile * 8 / (kWarps * 4);  // peer masks fit in the stage buffer
-
 // Rank of this lane's key among the keys of the same id that the warp has
 // seen so far (its earlier steps, then lower lanes of this step), and the
 // advance of the warp's counter for that id.  The lanes holding the same id
-// are found either with a per-warp word per id in shared memory (each lane
-// ORs its bit in, reads the word back and takes its bit out again, so the
-// words are zero between steps; MASK) or with the warp match instruction,
-// whose cost grows with the number of distinct ids in the warp.  FULL: every
-// lane holds a key; otherwise lanes with id 0xFFFF take no part.  Branch
-// free: every lane issues the same shared-memory operations, with operands
-// that change nothing where a lane has nothing to do.
-template <bool MASK, bool FULL>
-__device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t* wm, uint32_t* myc, unsigned lane, uint32_t wsh,
+// are found with one warp vote per id bit (ids below 2^nbits): a lane keeps
+// the voters that agree with it on every bit.  Votes need no shared memory
+// and no ordering between lanes, and their cost grows with log2 of the
+// bucket count only.  FULL: every lane holds a key; otherwise lanes with id
+// 0xFFFF take no part.  Branch free: every lane issues the same counter
+// atomic, adding zero where it is not its group's leader.
+template <bool FULL>
+__device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t nbits, uint32_t* myc, unsigned lane, uint32_t wsh,
                                               unsigned lt) {
   const bool valid = FULL || b != 0xFFFFu;
   const uint32_t bb = valid ? b : 0u;
-  const unsigned bit = 1u << lane;
-  unsigned p;
-  if constexpr (MASK) {
-    atomicOr(&wm[bb], valid ? bit : 0u);
-    __syncwarp();
-    p = wm[bb];
-    __syncwarp();
-    atomicAnd(&wm[bb], valid ? ~bit : ~0u);
-  } else {
-    p = __match_any_sync(0xFFFFFFFFu, b);
+  unsigned p = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+  for (uint32_t i = 0; i < 12; ++i) {
+    if (i < nbits) {  // uniform
+      const bool on = (bb >> i) & 1u;
+      const unsigned v = __ballot_sync(0xFFFFFFFFu, on);
+      p &= on ? v : ~v;
+    }
   }
   if (!valid) p = 0;
   const int leader = __ffs(p) - 1;
-  // every lane adds (zero where it is not the leader): no divergent branch
   const uint32_t old = atomicAdd(&myc[bb], (int)lane == leader ? (uint32_t)__popc(p) << wsh : 0u);
   return ((__shfl_sync(0xFFFFFFFFu, old, leader & 31) >> wsh) & 0xFFFFu) + __popc(p & lt);
 }
@@ -286,52 +279,48 @@ __device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t* wm, uint32_t
 // Stable scatter, one tile of kTile keys at a time.  Chunks are taken in
 // order from a global counter; a chunk's per-bucket start comes from the
 // chunk-prefix kernels (bucket cursor + keys of the bucket in the item's
-// earlier chunks).  Inside a tile each warp owns kWarpKeys consecutive keys
-// and ranks them in order with warp-private counters; a per-bucket prefix
-// over the warps and a scan over the buckets place every key in a staging
-// buffer grouped by bucket, which is written out with runs of consecutive
-// destinations.  Keys keep their relative order within a bucket (the stable
-// counting sort of the partitioning step).  Counters of warps 2i and 2i+1
-// share a word, 16 bits each (a warp ranks at most kWarpKeys keys).
-// How K3 finds the lanes of a warp step that hold the same bucket id.
-enum K3Mode {
-  K3_MATCH = 0,       // warp match instruction (any number of buckets)
-  K3_MASK_STAGE = 1,  // per-warp masks in the staging buffer (nb_pad <= kMaskBuckets)
-  K3_MASK_OWN = 2     // per-warp masks in their own area (nb_pad <= 2 kMaskBuckets)
-};
+// earlier chunks).  Inside a tile each warp owns kTile/(TPB/32) consecutive
+// keys and ranks them in order with warp-private counters; a per-bucket
+// prefix over the warps and a scan over the buckets place every key in a
+// staging buffer grouped by bucket, which is written out with runs of
+// consecutive destinations.  Keys keep their relative order within a bucket
+// (the stable counting sort of the partitioning step).  Counters of warps 2i
+// and 2i+1 share a word, 16 bits each (a warp ranks at most 512 keys).
+// TPB: threads per block; QM: bucket ranges of TPB buckets (nb_pad <= QM*TPB).
 
 // Payload type of a key-value sort: VB bytes per value (0: keys only).
 template <int VB>
 using ValT = typename std::conditional<VB == 8, uint64_t, uint32_t>::type;
 
-template <int MODE, int VB>
-__global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1) k_scatter(PassArgs a, RunParams rp) {
-  constexpr bool MASK = MODE != K3_MATCH;
+// Resident blocks per SM the register budget is sized for (shared memory
+// allows as many for 1024- and 2048-bucket tables).
+constexpr int k3_min_blocks(int tpb, int qm, int vb) {
+  return tpb == 512 ? (vb == 8 ? 1 : 2) : qm <= 8 ? (vb == 8 ? 1 : 2) : 1;
+}
+
+template <int TPB, int QM, int VB>
+__global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(PassArgs a, RunParams rp) {
+  constexpr uint32_t kW = TPB / 32;          // warps
+  constexpr uint32_t kKT = kTile / TPB;      // keys per thread per tile
+  constexpr uint32_t kWK = kTile / kW;       // keys of a tile ranked by one warp
+  static_assert(kWK <= 0xFFFFu && QM * kW <= 128, "warp counters are 16 bits; 128 warp totals");
   using V = ValT<VB>;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t nbp = a.nb_pad_max;
   uint64_t* sRun = reinterpret_cast<uint64_t*>(smem);          // next destination per bucket
-  uint64_t* stage = sRun + nbp;                                // kTile keys; warp peer masks while ranking
+  uint64_t* stage = sRun + nbp;                                // kTile keys, grouped by bucket
   uint32_t* sLs = reinterpret_cast<uint32_t*>(stage + kTile);  // tile-local start per bucket
   uint32_t* sCnt = sLs + nbp;                                  // tile count per bucket
-  uint32_t* wcnt = sCnt + nbp;                                 // [kWarps/2][nbp] packed warp counters
-  uint16_t* sid = reinterpret_cast<uint16_t*>(wcnt + (kWarps / 2) * nbp);  // bucket of each staged key
-  __shared__ uint32_t wsum[kWarps * 16];
+  uint32_t* wcnt = sCnt + nbp;                                 // [kW/2][nbp] packed warp counters
+  uint16_t* sid = reinterpret_cast<uint16_t*>(wcnt + (kW / 2) * nbp);  // bucket of each staged key
+  V* const sv = reinterpret_cast<V*>(sid + kTile);                     // staged values (key-value sorts)
+  __shared__ uint32_t wsum[128];
   __shared__ unsigned long long s_chunk[2];
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t wsh = 16 * (wid & 1);
   uint32_t* myc = wcnt + (wid >> 1) * nbp;
-  uint32_t* const masks =
-      MODE == K3_MASK_OWN ? reinterpret_cast<uint32_t*>(sid + kTile) : reinterpret_cast<uint32_t*>(stage);
-  uint32_t* wm = masks + wid * nbp;
-  // staged values (key-value sorts): after the masks' own area or the ids
-  V* const sv = reinterpret_cast<V*>(MODE == K3_MASK_OWN ? reinterpret_cast<unsigned char*>(masks + kWarps * nbp)
-                                                          : reinterpret_cast<unsigned char*>(sid + kTile));
   const unsigned lt = (1u << lane) - 1u;
-  for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp; j += kTPB) wcnt[j] = 0;
-  for (uint32_t j = threadIdx.x; j < kTile * 2; j += kTPB) reinterpret_cast<uint32_t*>(stage)[j] = 0;
-  if (MODE == K3_MASK_OWN)
-    for (uint32_t j = threadIdx.x; j < kWarps * nbp; j += kTPB) masks[j] = 0;
+  for (uint32_t j = threadIdx.x; j < (kW / 2) * nbp; j += TPB) wcnt[j] = 0;
   bool oob = false;
   for (int par = 0;; par ^= 1) {
     if (threadIdx.x == 0) s_chunk[par] = atomicAdd(a.chunk_ctr, 1ull);
@@ -343,8 +332,9 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
     if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
     const Item& it = a.items[pi];
     const uint32_t nbk = pl.nb_pad;
+    const uint32_t nbits = nbk > 1 ? 32u - __clz(nbk - 1u) : 0u;
     const unsigned long long* ex = a.excl + ch * nbp;
-    for (uint32_t b = threadIdx.x; b < nbk; b += kTPB) {
+    for (uint32_t b = threadIdx.x; b < nbk; b += TPB) {
       sRun[b] = a.cursors[pl.cnt_off + b] + ex[b];
       sCnt[b] = 0;
       sLs[b] = 0;
@@ -357,25 +347,25 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
     const V* vsrc = VB ? static_cast<const V*>(it.buf ? a.valsB : a.valsA) + it.lo + c0 : nullptr;
     V* vdst = VB ? static_cast<V*>(it.buf ? a.valsA : a.valsB) : nullptr;
     const uint64_t lo = it.lo, n = it.n;
-    const uint32_t Q = (nbk + kTPB - 1) / kTPB;  // bucket ranges of kTPB (at most 16)
-    uint64_t v[kKPT];
-    uint32_t bk[kKPT];
-    V vv[VB ? kKPT : 1];
+    const uint32_t Q = (nbk + TPB - 1) / TPB;  // bucket ranges of TPB (at most QM)
+    uint64_t v[kKT];
+    uint32_t bk[kKT];
+    V vv[VB ? kKT : 1];
     auto load_tile = [&](uint64_t t0) {
       const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
-      const uint64_t* s = src + t0 + wid * kWarpKeys + lane;
-      const uint16_t* d = idin + t0 + wid * kWarpKeys + lane;
+      const uint64_t* s = src + t0 + wid * kWK + lane;
+      const uint16_t* d = idin + t0 + wid * kWK + lane;
       if (len == kTile) {
 #pragma unroll
-        for (int k = 0; k < kKPT; ++k) {
+        for (int k = 0; k < (int)kKT; ++k) {
           v[k] = s[k * 32];
           bk[k] = d[k * 32];
-          if constexpr (VB != 0) vv[k] = vsrc[t0 + wid * kWarpKeys + lane + k * 32];
+          if constexpr (VB != 0) vv[k] = vsrc[t0 + wid * kWK + lane + k * 32];
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < kKPT; ++k) {
-          const uint32_t pos = wid * kWarpKeys + k * 32 + lane;
+        for (int k = 0; k < (int)kKT; ++k) {
+          const uint32_t pos = wid * kWK + k * 32 + lane;
           v[k] = pos < len ? s[k * 32] : 0;
           bk[k] = pos < len ? (uint32_t)d[k * 32] : 0xFFFFu;
           if constexpr (VB != 0) vv[k] = pos < len ? vsrc[t0 + pos] : V(0);
@@ -387,23 +377,21 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
       constexpr bool FULL = decltype(full_tag)::value;
       // rank: bk[k] becomes id | (rank among the warp's keys of that id) << 16
 #pragma unroll
-      for (int k = 0; k < kKPT; ++k) bk[k] |= rank_step<MASK, FULL>(bk[k], wm, myc, lane, wsh, lt) << 16;
+      for (int k = 0; k < (int)kKT; ++k) bk[k] |= rank_step<FULL>(bk[k], nbits, myc, lane, wsh, lt) << 16;
       __syncthreads();
-      // per bucket b = q*kTPB + tid: advance the run by the previous tile's
+      // per bucket b = q*TPB + tid: advance the run by the previous tile's
       // count, prefix over the warps (in place), tile count; then one scan
       // over all buckets (ranges q-major, then warps, then lanes)
-      constexpr uint32_t QMAX = MODE == K3_MASK_STAGE ? kMaskBuckets / kTPB
-                                : MODE == K3_MASK_OWN ? 2 * kMaskBuckets / kTPB : 16;  // bucket ranges of kTPB
-      uint32_t cnt[QMAX];
+      uint32_t cnt[QM];
 #pragma unroll
-      for (uint32_t q = 0; q < QMAX; ++q) {
-        const uint32_t b = q * kTPB + threadIdx.x;
+      for (uint32_t q = 0; q < QM; ++q) {
+        const uint32_t b = q * TPB + threadIdx.x;
         cnt[q] = 0;
         if (q < Q && b < nbk) {
           sRun[b] += sLs[b] + sCnt[b];  // undo the previous tile's offset, advance past its keys
           uint32_t t = 0;
 #pragma unroll
-          for (uint32_t w2 = 0; w2 < kWarps / 2; ++w2) {
+          for (uint32_t w2 = 0; w2 < kW / 2; ++w2) {
             const uint32_t x = wcnt[w2 * nbp + b];
             const uint32_t t1 = t + (x & 0xFFFFu);
             wcnt[w2 * nbp + b] = t | (t1 << 16);
@@ -413,13 +401,13 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
           cnt[q] = t;
         }
       }
-      uint32_t inc[QMAX];
+      uint32_t inc[QM];
 #pragma unroll
-      for (uint32_t q = 0; q < QMAX; ++q) inc[q] = cnt[q];
+      for (uint32_t q = 0; q < QM; ++q) inc[q] = cnt[q];
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
-        for (uint32_t q = 0; q < QMAX; ++q) {
+        for (uint32_t q = 0; q < QM; ++q) {
           if (q < Q) {  // uniform
             const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc[q], d);
             if (lane >= (unsigned)d) inc[q] += o;
@@ -427,20 +415,20 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
         }
       }
 #pragma unroll
-      for (uint32_t q = 0; q < QMAX; ++q) {
-        const uint32_t b = q * kTPB + threadIdx.x;
+      for (uint32_t q = 0; q < QM; ++q) {
+        const uint32_t b = q * TPB + threadIdx.x;
         if (q < Q) {
-          if (lane == 31) wsum[q * kWarps + wid] = inc[q];
+          if (lane == 31) wsum[q * kW + wid] = inc[q];
           if (b < nbk) sLs[b] = inc[q] - cnt[q];  // exclusive within the warp's 32 buckets
         }
       }
       __syncthreads();
-      if (wid == 0) {  // scan the Q*kWarps warp totals, 4 per lane
+      if (wid == 0) {  // scan the Q*kW warp totals, 4 per lane
         uint32_t e[4], s4 = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const uint32_t idx = lane * 4 + i;
-          e[i] = idx < Q * kWarps ? wsum[idx] : 0u;
+          e[i] = idx < Q * kW ? wsum[idx] : 0u;
           s4 += e[i];
         }
         uint32_t x = s4;
@@ -453,25 +441,24 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const uint32_t idx = lane * 4 + i;
-          if (idx < Q * kWarps) wsum[idx] = run;
+          if (idx < Q * kW) wsum[idx] = run;
           run += e[i];
         }
       }
       __syncthreads();
       for (uint32_t q = 0; q < Q; ++q) {
-        const uint32_t b = q * kTPB + threadIdx.x;
+        const uint32_t b = q * TPB + threadIdx.x;
         if (b < nbk) {
-          const uint32_t ls = sLs[b] + wsum[q * kWarps + wid];
+          const uint32_t ls = sLs[b] + wsum[q * kW + wid];
           sLs[b] = ls;
           sRun[b] -= ls;  // destination of staged position p is sRun[b] + p
         }
       }
       __syncthreads();
-      // stage grouped by bucket (overwrites the peer masks, all zero now);
-      // in a partial tile the empty lanes write a zero key to the last slot,
-      // which no key of the tile uses
+      // stage grouped by bucket; in a partial tile the empty lanes write a
+      // zero key to the last slot, which no key of the tile uses
 #pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
+      for (int k = 0; k < (int)kKT; ++k) {
         const uint32_t b = bk[k] & 0xFFFFu;
         const bool valid = FULL || b != 0xFFFFu;
         const uint32_t bb = valid ? b : 0u;
@@ -487,7 +474,6 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
       auto put = [&](uint32_t p) {
         const uint64_t o = sRun[sid[p]] + p;
         const uint64_t x = stage[p];
-        if (MODE == K3_MASK_STAGE) stage[p] = 0;  // peer masks of the next tile start from zero
         const bool ok = o - lo < n;  // K1 and K3 disagree: never write outside the item
         if (ok) {
           dst[o] = x;
@@ -497,11 +483,11 @@ __global__ void __launch_bounds__(kTPB, MODE == K3_MASK_STAGE ? (VB ? 2 : 3) : 1
       };
       if constexpr (FULL) {
 #pragma unroll 4
-        for (uint32_t p = threadIdx.x; p < kTile; p += kTPB) put(p);
+        for (uint32_t p = threadIdx.x; p < kTile; p += TPB) put(p);
       } else {
-        for (uint32_t p = threadIdx.x; p < len; p += kTPB) put(p);
+        for (uint32_t p = threadIdx.x; p < len; p += TPB) put(p);
       }
-      for (uint32_t j = threadIdx.x; j < (kWarps / 2) * nbp / 4; j += kTPB)
+      for (uint32_t j = threadIdx.x; j < (kW / 2) * nbp / 4; j += TPB)
         reinterpret_cast<uint4*>(wcnt)[j] = make_uint4(0, 0, 0, 0);
       __syncthreads();
     };
@@ -1813,8 +1799,8 @@ static void allow_smem(F* f, size_t sm, size_t* set) {
 static size_t k1_smem(const PassArgs& a) {
   return a.nb_pad_max * (8 + 4) + a.aux_bytes + 16;
 }
-static size_t k3_smem(const PassArgs& a) {
-  return a.nb_pad_max * (8 + 4 + 4 + 2 * kWarps) + kTile * (8 + 2) + 16;
+static size_t k3_smem(const PassArgs& a, uint32_t tpb, uint32_t vb) {
+  return a.nb_pad_max * (8 + 4 + 4 + 2 * (tpb / 32)) + kTile * (8 + 2 + vb) + 16;
 }
 
 template <int CLS, int DT, bool NANCHK>
@@ -1858,24 +1844,26 @@ int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi
   return 3;
 }
 
-template <int MODE, int VB>
+template <int TPB, int QM, int VB>
 static void launch_k3(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
-  size_t sm = k3_smem(a) + (MODE == K3_MASK_OWN ? (size_t)kWarps * a.nb_pad_max * 4 : 0) + (size_t)VB * kTile;
+  const size_t sm = k3_smem(a, TPB, VB);
   static size_t set[64] = {};
-  allow_smem(k_scatter<MODE, VB>, sm, set);
+  allow_smem(k_scatter<TPB, QM, VB>, sm, set);
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<MODE, VB>, kTPB, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter<TPB, QM, VB>, TPB, sm);
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_scatter<MODE, VB><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  k_scatter<TPB, QM, VB><<<(unsigned)grid, TPB, sm, st>>>(a, rp);
 }
 
+// Up to 1024 buckets: 16-warp blocks (two per SM); larger tables keep the
+// warp counters of 8-warp blocks within shared memory.
 template <int VB>
 static void launch_k3_vb(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
-  if (a.nb_pad_max <= kMaskBuckets) launch_k3<K3_MASK_STAGE, VB>(a, rp, st);
-  else if (a.nb_pad_max <= 2 * kMaskBuckets) launch_k3<K3_MASK_OWN, VB>(a, rp, st);
-  else launch_k3<K3_MATCH, VB>(a, rp, st);
+  if (a.nb_pad_max <= 1024) launch_k3<512, 2, VB>(a, rp, st);
+  else if (a.nb_pad_max <= 2048) launch_k3<256, 8, VB>(a, rp, st);
+  else launch_k3<256, 16, VB>(a, rp, st);
 }
 
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
