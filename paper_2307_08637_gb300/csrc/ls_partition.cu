@@ -157,21 +157,25 @@ __device__ __forceinline__ void hist_add(uint32_t* sH, uint32_t b, bool agg) {
 // One chunk of K1: classify, store ids, histogram; OR every key's bits into
 // `diff` against the item's first key (all equal <=> the item is
 // homogeneous) and, when NANCHK, flag NaNs (|bits| above infinity's).
+constexpr int kK1KPT = 8;                     // K1: keys per thread per step
+constexpr uint32_t kK1Tile = kTPB * kK1KPT;
+constexpr int kK1Blocks = 4;                  // K1: resident blocks per SM (register budget)
+
 template <int CLS, int DT, bool NANCHK>
 __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const uint64_t* sT, const void* sD,
                                          uint32_t* sH, const uint64_t* src, uint16_t* idout, uint64_t clen,
                                          uint64_t first, uint64_t& diff, bool& nan) {
   constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
-  for (uint64_t t0 = 0; t0 < clen; t0 += kTile) {
-    const uint32_t len = clen - t0 < kTile ? (uint32_t)(clen - t0) : kTile;
+  for (uint64_t t0 = 0; t0 < clen; t0 += kK1Tile) {
+    const uint32_t len = clen - t0 < kK1Tile ? (uint32_t)(clen - t0) : kK1Tile;
     const uint64_t* s = src + t0 + threadIdx.x;
     uint16_t* d = idout + t0 + threadIdx.x;
-    if (len == kTile) {
-      uint64_t v[kKPT];
+    if (len == kK1Tile) {
+      uint64_t v[kK1KPT];
 #pragma unroll
-      for (int k = 0; k < kKPT; ++k) v[k] = s[k * kTPB];
+      for (int k = 0; k < kK1KPT; ++k) v[k] = s[k * kTPB];
 #pragma unroll
-      for (int k = 0; k < kKPT; ++k) {
+      for (int k = 0; k < kK1KPT; ++k) {
         const uint64_t bits = v[k];
         if (NANCHK) nan |= (bits & kAbs) > kInf;
         diff |= bits ^ first;
@@ -180,7 +184,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
         hist_add(sH, b, c.agg);
       }
     } else {
-      for (int k = 0; k < kKPT; ++k) {
+      for (int k = 0; k < kK1KPT; ++k) {
         const uint32_t idx = k * kTPB + threadIdx.x;
         uint32_t b = 0xFFFFFFFFu;
         if (idx < len) {
@@ -203,7 +207,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
 // homogeneous.  One kernel per classifier kind, key type and NaN check keeps
 // each instance's registers and instructions to what it needs.
 template <int CLS, int DT, bool NANCHK>
-__global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams rp) {
+__global__ void __launch_bounds__(kTPB, kK1Blocks) k_classify_hist(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
   void* sD = sT + a.nb_pad_max;  // directory or FP32 leaves (aux_bytes, 16-byte aligned)
@@ -250,30 +254,29 @@ __global__ void __launch_bounds__(kTPB, 3) k_classify_hist(PassArgs a, RunParams
 // Rank of this lane's key among the keys of the same id that the warp has
 // seen so far (its earlier steps, then lower lanes of this step), and the
 // advance of the warp's counter for that id.  The lanes holding the same id
-// are found with one warp vote per id bit (ids below 2^nbits): a lane keeps
-// the voters that agree with it on every bit.  Votes need no shared memory
-// and no ordering between lanes, and their cost grows with log2 of the
-// bucket count only.  FULL: every lane holds a key; otherwise lanes with id
-// 0xFFFF take no part.  Branch free: every lane issues the same counter
-// atomic, adding zero where it is not its group's leader.
-template <bool FULL>
-__device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t nbits, uint32_t* myc, unsigned lane, uint32_t wsh,
-                                              unsigned lt) {
+// are found with one warp vote per id bit (ids below 2^NB): a lane keeps the
+// voters that agree with it on every bit.  Votes need no shared memory and
+// their cost grows with log2 of the bucket count only.  The warp's 16-bit
+// counter for the id is read by every lane of the group and advanced by the
+// group's lowest lane (the other warp sharing the word owns its other half).
+// FULL: every lane holds a key; otherwise lanes with id 0xFFFF take no part.
+template <bool FULL, uint32_t NB>
+__device__ __forceinline__ uint32_t rank_step(uint32_t b, uint32_t* myc, unsigned lane, uint32_t wsh, unsigned lt) {
   const bool valid = FULL || b != 0xFFFFu;
   const uint32_t bb = valid ? b : 0u;
+  uint16_t* c16 = reinterpret_cast<uint16_t*>(myc + bb) + (wsh >> 4);
+  const uint32_t old = *c16;
   unsigned p = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
-  for (uint32_t i = 0; i < 12; ++i) {
-    if (i < nbits) {  // uniform
-      const bool on = (bb >> i) & 1u;
-      const unsigned v = __ballot_sync(0xFFFFFFFFu, on);
-      p &= on ? v : ~v;
-    }
+  for (uint32_t i = 0; i < NB; ++i) {
+    const bool on = (bb >> i) & 1u;
+    const unsigned v = __ballot_sync(0xFFFFFFFFu, on);
+    p &= on ? v : ~v;
   }
   if (!valid) p = 0;
-  const int leader = __ffs(p) - 1;
-  const uint32_t old = atomicAdd(&myc[bb], (int)lane == leader ? (uint32_t)__popc(p) << wsh : 0u);
-  return ((__shfl_sync(0xFFFFFFFFu, old, leader & 31) >> wsh) & 0xFFFFu) + __popc(p & lt);
+  if ((int)lane == __ffs(p) - 1) *c16 = (uint16_t)(old + __popc(p));
+  __syncwarp();  // the next step's reads see this step's counters
+  return old + __popc(p & lt);
 }
 
 // Stable scatter, one tile of kTile keys at a time.  Chunks are taken in
@@ -303,6 +306,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
   constexpr uint32_t kW = TPB / 32;          // warps
   constexpr uint32_t kKT = kTile / TPB;      // keys per thread per tile
   constexpr uint32_t kWK = kTile / kW;       // keys of a tile ranked by one warp
+  constexpr uint32_t kNB = QM * TPB <= 1024 ? 10 : QM * TPB <= 2048 ? 11 : 12;  // id bits (ids < nb_pad)
   static_assert(kWK <= 0xFFFFu && QM * kW <= 128, "warp counters are 16 bits; 128 warp totals");
   using V = ValT<VB>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -332,7 +336,6 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
     if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
     const Item& it = a.items[pi];
     const uint32_t nbk = pl.nb_pad;
-    const uint32_t nbits = nbk > 1 ? 32u - __clz(nbk - 1u) : 0u;
     const unsigned long long* ex = a.excl + ch * nbp;
     for (uint32_t b = threadIdx.x; b < nbk; b += TPB) {
       sRun[b] = a.cursors[pl.cnt_off + b] + ex[b];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
       constexpr bool FULL = decltype(full_tag)::value;
       // rank: bk[k] becomes id | (rank among the warp's keys of that id) << 16
 #pragma unroll
-      for (int k = 0; k < (int)kKT; ++k) bk[k] |= rank_step<FULL>(bk[k], nbits, myc, lane, wsh, lt) << 16;
+      for (int k = 0; k < (int)kKT; ++k) bk[k] |= rank_step<FULL, kNB>(bk[k], myc, lane, wsh, lt) << 16;
       __syncthreads();
       // per bucket b = q*TPB + tid: advance the run by the previous tile's
       // count, prefix over the warps (in place), tile count; then one scan
