@@ -686,6 +686,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
   // evaluations leave is searched.
   uint64_t L = lo, H = hi;
   double vL = vlo, vH = vhi;
+  int near = 0;  // -1: the pivot lies just below H; +1: just above L
   {
     const double xlo = q.xlo, xhi = q.xhi;
     uint32_t l0 = q.l0, l1 = q.l1;
@@ -713,9 +714,11 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
         if (vu >= t) {
           H = u;
           vH = vu;
+          near = -1;
         } else {
           L = u;
           vL = vu;
+          near = 1;
         }
       }
     } else if (lf.a > 0.0) {
@@ -741,6 +744,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
               H = u - 1;
               vH = v2;
             }
+            near = -1;
           } else {
             L = u;
             vL = vu;
@@ -753,8 +757,41 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
               L = u + 1;
               vL = v2;
             }
+            near = 1;
           }
         }
+      }
+    }
+  }
+  // The guess lands a few ord from the pivot (the model's FP64 roundings
+  // make v flat over a few ord): gallop away from it to a tight bracket
+  // before the general search.
+  if (near < 0) {
+    for (uint64_t step = 1; step <= (1ull << 40) && H - L > 1; step <<= 1) {
+      const uint64_t c = H - L > step ? H - step : L;
+      if (c == L) break;
+      const double vc = ev(c);
+      if (vc >= t) {
+        H = c;
+        vH = vc;
+      } else {
+        L = c;
+        vL = vc;
+        break;
+      }
+    }
+  } else if (near > 0) {
+    for (uint64_t step = 1; step <= (1ull << 40) && H - L > 1; step <<= 1) {
+      const uint64_t c = H - L > step ? L + step : H;
+      if (c == H) break;
+      const double vc = ev(c);
+      if (vc < t) {
+        L = c;
+        vL = vc;
+      } else {
+        H = c;
+        vH = vc;
+        break;
       }
     }
   }
