@@ -1013,7 +1013,8 @@ __device__ __forceinline__ void warp_sort_span_kv(const Span& s, uint64_t* A, co
 // insertion-sort fix, Sec. 2.2): inside a bucket the keys are close to
 // uniform in ord space, so a linear map between the span's extremes places
 // them into 32R slots (R = ceil(n / 32) keys per lane); a counting sort by
-// slot and an insertion sort inside each slot give the exact order.  Spans
+// slot and a rank count inside each slot (the insertion-sort fix done as one
+// comparison pass per key, without a dependent chain) give the exact order.  Spans
 // whose largest slot holds more than kMaxSlot keys (clustered data) return
 // false and take the bitonic network instead.
 constexpr uint32_t kSlots = 256;  // slots of the largest size class (32 per key register)
@@ -1026,8 +1027,8 @@ constexpr uint32_t kMaxSlot = 24;
 // clz(lmax - lmin)); slot = floor(w 32R / 2^32).  Monotone in u, so sorting
 // by slot and then inside slots sorts the span.  Slot s belongs to lane
 // s / R (= w >> 27) and is stored at (s mod R) * 32 + s / R, so the per-lane
-// reads of the scan hit distinct banks.  Counts and starts of a lane's
-// slots stay in registers.
+// reads of the scan hit distinct banks; after the scan the word holds the
+// slot's start and count.
 template <int R>
 __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
                                                  uint64_t* sk, uint32_t* sc) {
@@ -1101,34 +1102,40 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
     if (lane >= (unsigned)d) incl += o;
   }
   if (__reduce_max_sync(0xFFFFFFFFu, big) > kMaxSlot) return false;  // uniform across the warp
-  uint32_t st[R];
   uint32_t run = incl - loc;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    st[q] = run;
-    sc[q * 32 + lane] = run;  // slot start
+    sc[q * 32 + lane] = run | (c[q] << 16);  // slot start and count
     run += c[q];
+  }
+  __syncwarp();
+  uint32_t e[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    e[r] = sc[at[r]];
+    if (r < R - 1 || lane + 32 * r < n) sk[(e[r] & 0xFFFFu) + rk[r]] = u[r];
+  }
+  __syncwarp();
+  // order inside the slots: a key's place is its slot's start plus the keys
+  // of the slot before it (smaller, or equal and staged earlier); the reads
+  // are independent, so a slot of c keys costs c loads, not a chain
+  uint32_t pos[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t a0 = e[r] & 0xFFFFu, me = a0 + rk[r];
+    const uint32_t cn = (r < R - 1 || lane + 32 * r < n) ? e[r] >> 16 : 0u;
+    uint32_t p = a0;
+#pragma unroll 4
+    for (uint32_t i = a0; i < a0 + cn; ++i) {
+      const uint64_t x = sk[i];
+      p += (x < u[r]) | ((x == u[r]) & (i < me));
+    }
+    pos[r] = p;
   }
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (r < R - 1 || lane + 32 * r < n) sk[sc[at[r]] + rk[r]] = u[r];
-  __syncwarp();
-  // insertion sort inside the lane's slots that hold two or more keys
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    if (c[q] < 2) continue;
-    const uint32_t a0 = st[q], a1 = st[q] + c[q];
-    for (uint32_t x = a0 + 1; x < a1; ++x) {
-      const uint64_t v = sk[x];
-      uint32_t y = x;
-      while (y > a0 && sk[y - 1] > v) {
-        sk[y] = sk[y - 1];
-        --y;
-      }
-      sk[y] = v;
-    }
-  }
+    if (r < R - 1 || lane + 32 * r < n) sk[pos[r]] = u[r];
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -1137,7 +1144,7 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
   return true;
 }
 
-__global__ void __launch_bounds__(kTPB, 3) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
+__global__ void __launch_bounds__(kTPB, 4) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
                                                      int dt) {
   __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
   __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
@@ -1252,41 +1259,46 @@ __device__ __forceinline__ bool warp_placed_sort_kv(const Span& s, uint64_t* A, 
     if (lane >= (unsigned)d) incl += o;
   }
   if (__reduce_max_sync(0xFFFFFFFFu, big) > kMaxSlot) return false;
-  uint32_t st[R];
   uint32_t run = incl - loc;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    st[q] = run;
-    sc[q * 32 + lane] = run;
+    sc[q * 32 + lane] = run | (c[q] << 16);  // slot start and count
     run += c[q];
+  }
+  __syncwarp();
+  uint32_t e[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    e[r] = sc[at[r]];
+    if (r < R - 1 || lane + 32 * r < n) {
+      const uint32_t p = (e[r] & 0xFFFFu) + rk[r];
+      sk[p] = u[r];
+      si[p] = (uint16_t)(lane + 32 * r);
+    }
+  }
+  __syncwarp();
+  // order inside the slots by (key, input index): a pair's place is its
+  // slot's start plus the pairs of the slot that precede it
+  uint32_t pos[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t a0 = e[r] & 0xFFFFu, me = lane + 32 * r;
+    const uint32_t cn = (r < R - 1 || lane + 32 * r < n) ? e[r] >> 16 : 0u;
+    uint32_t p = a0;
+#pragma unroll 4
+    for (uint32_t i = a0; i < a0 + cn; ++i) {
+      const uint64_t x = sk[i];
+      p += (x < u[r]) | ((x == u[r]) & ((uint32_t)si[i] < me));
+    }
+    pos[r] = p;
   }
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (r < R - 1 || lane + 32 * r < n) {
-      const uint32_t p = sc[at[r]] + rk[r];
-      sk[p] = u[r];
-      si[p] = (uint16_t)(lane + 32 * r);
+      sk[pos[r]] = u[r];
+      si[pos[r]] = (uint16_t)(lane + 32 * r);
     }
-  __syncwarp();
-  // insertion sort by (key, index) inside the lane's slots of >= 2 keys
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    if (c[q] < 2) continue;
-    const uint32_t a0 = st[q], a1 = st[q] + c[q];
-    for (uint32_t x = a0 + 1; x < a1; ++x) {
-      const uint64_t v = sk[x];
-      const uint16_t vi = si[x];
-      uint32_t y = x;
-      while (y > a0 && (sk[y - 1] > v || (sk[y - 1] == v && si[y - 1] > vi))) {
-        sk[y] = sk[y - 1];
-        si[y] = si[y - 1];
-        --y;
-      }
-      sk[y] = v;
-      si[y] = vi;
-    }
-  }
   __syncwarp();
   V val[R];
 #pragma unroll
