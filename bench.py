@@ -306,6 +306,7 @@ def run_ours(args):
                  "learned_speedup": s_ms / step_ms,
                  "scatter_gbs": SCATTER_BYTES_PER_KEY * ps["scatter"]["keys"] / (ps["scatter"]["ms"] / 1e3) / 1e9,
                  "classify_gbs": CLASSIFY_BYTES_PER_KEY * ps["classify"]["keys"] / (ps["classify"]["ms"] / 1e3) / 1e9,
+                 "passes_ms_per_step": {k: v["ms"] / len(ms_s) for k, v in ps.items()},
                  "level1_max_bucket": {d: int(sts_s[i].level[0].max_child) for i, (d, _) in enumerate(inputs)},
                  "level1_bucket_sumsq": {d: int(sts_s[i].level[0].sumsq_child) for i, (d, _) in enumerate(inputs)}}
 

@@ -157,15 +157,20 @@ __device__ __forceinline__ void hist_add(uint32_t* sH, uint32_t b, bool agg) {
 // One chunk of K1: classify, store ids, histogram; OR every key's bits into
 // `diff` against the item's first key (all equal <=> the item is
 // homogeneous) and, when NANCHK, flag NaNs (|bits| above infinity's).
-constexpr int kK1KPT = 8;                     // K1: keys per thread per step
-constexpr uint32_t kK1Tile = kTPB * kK1KPT;
-constexpr int kK1Blocks = 4;                  // K1: resident blocks per SM (register budget)
+// K1 keys per thread per step and resident blocks per SM (register budget):
+// the guess classifier is short and gains from more warps; the search
+// classifiers are chains of dependent table reads and gain from more
+// independent keys per thread.
+__host__ __device__ constexpr int k1_kpt(int cls) { return cls == CLS_GUESS ? 8 : 16; }
+__host__ __device__ constexpr int k1_blocks(int cls) { return cls == CLS_GUESS ? 4 : 3; }
 
 template <int CLS, int DT, bool NANCHK>
 __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const uint64_t* sT, const void* sD,
                                          uint32_t* sH, const uint64_t* src, uint16_t* idout, uint64_t clen,
                                          uint64_t first, uint64_t& diff, bool& nan) {
   constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  constexpr int kK1KPT = k1_kpt(CLS);
+  constexpr uint32_t kK1Tile = kTPB * kK1KPT;
   for (uint64_t t0 = 0; t0 < clen; t0 += kK1Tile) {
     const uint32_t len = clen - t0 < kK1Tile ? (uint32_t)(clen - t0) : kK1Tile;
     const uint64_t* s = src + t0 + threadIdx.x;
@@ -207,7 +212,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
 // homogeneous.  One kernel per classifier kind, key type and NaN check keeps
 // each instance's registers and instructions to what it needs.
 template <int CLS, int DT, bool NANCHK>
-__global__ void __launch_bounds__(kTPB, kK1Blocks) k_classify_hist(PassArgs a, RunParams rp) {
+__global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs a, RunParams rp) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
   void* sD = sT + a.nb_pad_max;  // directory or FP32 leaves (aux_bytes, 16-byte aligned)
@@ -564,71 +569,71 @@ __global__ void k_chunk_carry(const ChunkSeg* __restrict__ segs, const Plan* __r
 
 // ------------------------------------------------------------------ K2
 
-// Block-wide exclusive scan of one uint32 per thread (blockDim 1024).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* wtmp, uint32_t* total) {
-  unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = x;
+constexpr int kK2Threads = 256;
+constexpr int kK2Warps = kK2Threads / 32;
+
+// Block-wide exchange for K2: exclusive scans of N uint32 per thread (totals
+// to every thread) and sums of M uint64 per thread (to every thread), with
+// one pass through shared memory.  s32 holds kK2Warps*N words, s64
+// kK2Warps*M; the caller separates reuses of them with a barrier.
+template <int N, int M>
+__device__ __forceinline__ void k2_exchange(uint32_t (&x)[N], uint32_t (&tot)[N], unsigned long long (&y)[M],
+                                            uint32_t* s32, unsigned long long* s64) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) inc[k] = x[k];
+#pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-    if (lane >= (unsigned)d) incl += o;
-  }
-  __syncthreads();
-  if (lane == 31) wtmp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    unsigned nw = blockDim.x >> 5;
-    uint32_t w = lane < nw ? wtmp[lane] : 0;
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t o = __shfl_up_sync(0xFFFFFFFFu, w, d);
-      if (lane >= (unsigned)d) w += o;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc[k], d);
+      if (lane >= (unsigned)d) inc[k] += o;
     }
-    if (lane < nw) wtmp[lane] = w;
   }
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    for (int d = 16; d > 0; d >>= 1) y[k] += __shfl_xor_sync(0xFFFFFFFFu, y[k], d);
+  if (lane == 31)
+#pragma unroll
+    for (int k = 0; k < N; ++k) s32[wid * N + k] = inc[k];
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < M; ++k) s64[wid * M + k] = y[k];
   __syncthreads();
-  uint32_t r = incl - x + (wid > 0 ? wtmp[wid - 1] : 0);
-  if (total) *total = wtmp[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* tmp) {
-  for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, d);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = x;
-  __syncthreads();
-  unsigned long long r = 0;
-  if (threadIdx.x == 0)
-    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) r += tmp[w];
-  __syncthreads();
-  return r;  // valid in thread 0
-}
-
-__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x, unsigned long long* tmp) {
-  for (int d = 16; d > 0; d >>= 1) {
-    unsigned long long o = __shfl_down_sync(0xFFFFFFFFu, x, d);
-    x = o > x ? o : x;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    uint32_t before = 0, all = 0;
+    for (unsigned w = 0; w < (unsigned)kK2Warps; ++w) {
+      const uint32_t v = s32[w * N + k];
+      before += w < wid ? v : 0u;
+      all += v;
+    }
+    x[k] = inc[k] - x[k] + before;
+    tot[k] = all;
   }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) tmp[threadIdx.x >> 5] = x;
-  __syncthreads();
-  unsigned long long r = 0;
-  if (threadIdx.x == 0)
-    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) r = tmp[w] > r ? tmp[w] : r;
-  __syncthreads();
-  return r;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    unsigned long long t = 0;
+    for (unsigned w = 0; w < (unsigned)kK2Warps; ++w) t += s64[w * M + k];
+    y[k] = t;
+  }
 }
 
 enum { L_NEXT = 0, L_SMALL, L_LARGE, L_COPY, L_FALLBACK, L_N };
 
-__global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
+// K2, one block per item: bucket starts and write cursors from the counts,
+// the item's level statistics, and the children lists (next level, base
+// cases, copies, fallback).  Thread t owns a contiguous range of buckets, so
+// the lists keep bucket order within an item.
+__global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams rp) {
   uint32_t pi = blockIdx.x;
   const Item& it = a.items[pi];
   Plan& pl = a.plans[pi];
-  __shared__ uint32_t wtmp[32];
-  __shared__ unsigned long long ltmp[32];
+  __shared__ uint32_t s32[kK2Warps * L_N];
+  __shared__ unsigned long long s64[kK2Warps * 6];
+  __shared__ unsigned long long smax[kK2Warps];
   __shared__ unsigned long long s_base[L_N];
-  __shared__ int s_noprog;
-  __shared__ uint32_t s_tot;
   uint32_t level = it.level;
   uint32_t cl = level + 1 < LS_MAX_LEVELS ? level + 1 : LS_MAX_LEVELS - 1;
   DevLevelStats* ls = a.stats + (level < LS_MAX_LEVELS ? level : LS_MAX_LEVELS - 1);
@@ -662,28 +667,31 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
   const uint64_t* T = a.pivots + pl.tab_off;
   bool has_T = pl.cls != CLS_DIRECT;
   uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
-  uint32_t b0 = threadIdx.x * per;
+  uint32_t b0 = threadIdx.x * per < nb ? threadIdx.x * per : nb;
   uint32_t b1 = b0 + per < nb ? b0 + per : nb;
-  // exclusive scan of counts -> bucket starts (uint32 is enough per item up
-  // to 2^32 keys; items are smaller than that on one GPU)
-  uint64_t locsum = 0;
-  for (uint32_t b = b0; b < b1; ++b) locsum += cnt[b];
-  if (threadIdx.x == 0) s_noprog = 0;
-  uint32_t excl32 = block_excl_scan((uint32_t)locsum, wtmp, &s_tot);
-  uint64_t run = excl32;
-  unsigned long long mxc = 0, sq = 0, eqk = 0, bk = 0, bki = 0, fbk = 0, fbi = 0;
-  uint32_t nl[L_N] = {0, 0, 0, 0, 0};
+  // exclusive scan of counts -> bucket starts (uint32 is enough per item:
+  // items are shorter than 2^32 keys), largest bucket, sum of squares, and
+  // the no-progress test (one bucket holds the whole item)
+  unsigned long long mxc = 0, sq[2] = {0, 0};
+  uint32_t sc1[1] = {0}, tot1[1];
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
+    sc1[0] += (uint32_t)sz;
     mxc = sz > mxc ? sz : mxc;
-    sq += sz * sz;
-    if (sz == it.n && !(eq && (b & 1))) s_noprog = 1;
+    sq[0] += sz * sz;
+    if (sz == it.n && !(eq && (b & 1))) sq[1] = 1;
   }
-  __syncthreads();
-  bool noprog = s_noprog != 0;
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, mxc, d);
+    mxc = o > mxc ? o : mxc;
+  }
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mxc;
+  k2_exchange<1, 2>(sc1, tot1, sq, s32, s64);
+  uint64_t run = sc1[0];
+  unsigned long long tmax = 0;
+  for (int w = 0; w < kK2Warps; ++w) tmax = smax[w] > tmax ? smax[w] : tmax;
+  const bool noprog = sq[1] != 0;
   // level statistics of this item
-  unsigned long long tmax = block_max_u64(mxc, ltmp);
-  unsigned long long tsq = block_sum_u64(sq, ltmp);
   if (threadIdx.x == 0) {
     atomicAdd(&ls->items, 1ull);
     atomicAdd(&ls->keys, (unsigned long long)it.n);
@@ -691,7 +699,7 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
     else if (eq) atomicAdd(&ls->splitter_eq, 1ull);
     else atomicAdd(&ls->splitter, 1ull);
     atomicMax(&ls->max_child, tmax);
-    atomicAdd(&ls->sumsq_child, tsq);
+    atomicAdd(&ls->sumsq_child, sq[0]);
   }
   if (noprog) {
     // no-progress guard: redo the same range at the next level with the
@@ -747,6 +755,8 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
   // count list entries: base case / fallback / next level per non-final
   // bucket; one copy run per maximal run of final buckets (only when the
   // destination is the workspace buffer)
+  unsigned long long eqk = 0, bk = 0, bki = 0, fbk = 0, fbi = 0;
+  uint32_t nl[L_N] = {0, 0, 0, 0, 0};
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
     if (eq && (b & 1)) eqk += sz;
@@ -772,38 +782,32 @@ __global__ void __launch_bounds__(1024) k_children(ChildArgs a, RunParams rp) {
       nl[L_NEXT]++;
     }
   }
-  uint32_t pos[L_N];
-  for (int q = 0; q < L_N; ++q) {
-    uint32_t tot;
-    pos[q] = block_excl_scan(nl[q], wtmp, &tot);
-    if (threadIdx.x == 0) {
+  uint32_t tot[L_N];
+  unsigned long long sums[5] = {eqk, bk, bki, fbk, fbi};
+  __syncthreads();  // the first exchange's words are read by every thread before they are reused
+  k2_exchange<L_N, 5>(nl, tot, sums, s32, s64);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < L_N; ++q) {
       unsigned long long* ctr = (q == L_NEXT)    ? &a.ctr->n_next
                                 : (q == L_SMALL) ? &a.ctr->n_base_small
                                 : (q == L_LARGE) ? &a.ctr->n_base_large
                                 : (q == L_COPY)  ? &a.ctr->n_copy
                                                  : &a.ctr->n_fallback;
-      s_base[q] = tot ? atomicAdd(ctr, (unsigned long long)tot) : 0ull;
+      s_base[q] = tot[q] ? atomicAdd(ctr, (unsigned long long)tot[q]) : 0ull;
     }
-  }
-  unsigned long long s_eqk = block_sum_u64(eqk, ltmp);
-  unsigned long long s_bk = block_sum_u64(bk, ltmp);
-  unsigned long long s_bki = block_sum_u64(bki, ltmp);
-  unsigned long long s_fbk = block_sum_u64(fbk, ltmp);
-  unsigned long long s_fbi = block_sum_u64(fbi, ltmp);
-  if (threadIdx.x == 0) {
-    if (s_eqk) atomicAdd(&ls->eq_keys, s_eqk);
-    if (s_bki) {
-      atomicAdd(&cs->base_items, s_bki);
-      atomicAdd(&cs->base_keys, s_bk);
+    if (sums[0]) atomicAdd(&ls->eq_keys, sums[0]);
+    if (sums[2]) {
+      atomicAdd(&cs->base_items, sums[2]);
+      atomicAdd(&cs->base_keys, sums[1]);
     }
-    if (s_fbi) {
-      atomicAdd(&cs->fallback_items, s_fbi);
-      atomicAdd(&cs->fallback_keys, s_fbk);
+    if (sums[4]) {
+      atomicAdd(&cs->fallback_items, sums[4]);
+      atomicAdd(&cs->fallback_keys, sums[3]);
     }
   }
   __syncthreads();
   unsigned long long wp[L_N];
-  for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + pos[q];
+  for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + nl[q];
   const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.large_cap, a.copy_cap, a.fallback_cap};
   bool ovf = false;
   uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
@@ -1893,7 +1897,7 @@ void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   size_t sm = (size_t)(LS_MAX_FANOUT + 1) * 8 + LS_MAX_FANOUT + 16;
   static size_t set[64] = {};
   allow_smem(k_children, sm, set);
-  k_children<<<a.nitems, 1024, sm, st>>>(a, rp);
+  k_children<<<a.nitems, kK2Threads, sm, st>>>(a, rp);
 }
 
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
