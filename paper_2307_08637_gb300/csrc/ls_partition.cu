@@ -1539,12 +1539,162 @@ __device__ void block_bitonic_smem(uint64_t* sm, uint32_t P) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_base_large(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
-                                                     int dt) {
+// Model-placed base case for one span of 257..4096 keys by one 256-thread
+// block: the warp form's linear map between the span's extremes, counting
+// sort by slot and rank count inside slots, with block-wide reductions.
+// Slot s (of 256R) belongs to thread s / R (= w >> 24) and is stored at
+// (s mod R) * 256 + s / R.  Returns false (uniformly) when a slot holds
+// more than kMaxSlotL keys; the caller then sorts the span with the
+// bitonic network.
+constexpr uint32_t kLargeTPB = 256;
+constexpr int kLargeR = 16;  // keys per thread: spans of up to 4096 keys
+constexpr uint32_t kMaxSlotL = 32;
+
+__device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
+                                                  uint64_t* sk, uint32_t* sc, uint32_t* red) {
+  const uint32_t n = s.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr uint32_t kW = kLargeTPB / 32;
+  const uint32_t R = (n + kLargeTPB - 1) / kLargeTPB;
+  const uint64_t* src = (s.buf ? Bbuf : A) + s.lo;
+  uint64_t u[kLargeR];
+  uint32_t hmin = ~0u, hmax = 0;
+#pragma unroll
+  for (int r = 0; r < kLargeR; ++r) {
+    const uint32_t i = tid + kLargeTPB * r;
+    u[r] = i < n ? ord_of(src[i], dt) : 0ull;
+    if (i < n) {
+      hmin = min(hmin, (uint32_t)(u[r] >> 32));
+      hmax = max(hmax, (uint32_t)(u[r] >> 32));
+    }
+  }
+  auto block_minmax = [&](uint32_t& mn, uint32_t& mx) {
+    mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if (lane == 0) {
+      red[wid] = mn;
+      red[kW + wid] = mx;
+    }
+    __syncthreads();
+    mn = red[0];
+    mx = red[kW];
+    for (uint32_t q = 1; q < kW; ++q) {
+      mn = min(mn, red[q]);
+      mx = max(mx, red[kW + q]);
+    }
+    __syncthreads();
+  };
+  block_minmax(hmin, hmax);
+  uint32_t w[kLargeR];
+  if (hmin == hmax) {  // uniform: one high word, exact low-word extremes
+    uint32_t lmin = ~0u, lmax = 0;
+#pragma unroll
+    for (int r = 0; r < kLargeR; ++r)
+      if (tid + kLargeTPB * r < n) {
+        lmin = min(lmin, (uint32_t)u[r]);
+        lmax = max(lmax, (uint32_t)u[r]);
+      }
+    block_minmax(lmin, lmax);
+    if (lmin == lmax) {  // all equal: already sorted; bring home if needed
+      if (s.buf)
+        for (uint32_t i = tid; i < n; i += kLargeTPB) A[s.lo + i] = src[i];
+      return true;
+    }
+    const uint32_t sh = __clz(lmax - lmin);
+#pragma unroll
+    for (int r = 0; r < kLargeR; ++r) w[r] = ((uint32_t)u[r] - lmin) << sh;
+  } else {
+    const uint64_t base = (uint64_t)hmin << 32;
+    const uint32_t sh = __clz(hmax - hmin);
+#pragma unroll
+    for (int r = 0; r < kLargeR; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
+  }
+  const uint32_t NS = kLargeTPB * R;
+  for (uint32_t i = tid; i < NS; i += kLargeTPB) sc[i] = 0;
+  __syncthreads();
+  uint32_t at[kLargeR], rk[kLargeR];
+#pragma unroll
+  for (int r = 0; r < kLargeR; ++r) {
+    const uint32_t slot = __umulhi(w[r], NS), owner = w[r] >> 24;
+    at[r] = (slot - owner * R) * kLargeTPB + owner;
+    rk[r] = tid + kLargeTPB * r < n ? atomicAdd(&sc[at[r]], 1u) : 0u;
+  }
+  __syncthreads();
+  // exclusive scan of the slot counts in slot order (thread t: slots tR..tR+R-1)
+  uint32_t loc = 0, big = 0;
+#pragma unroll
+  for (int q = 0; q < kLargeR; ++q)
+    if ((uint32_t)q < R) {
+      const uint32_t c = sc[q * kLargeTPB + tid];
+      loc += c;
+      big = max(big, c);
+    }
+  uint32_t incl = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= (unsigned)d) incl += o;
+  }
+  big = __reduce_max_sync(0xFFFFFFFFu, big);
+  if (lane == 31) red[wid] = incl;
+  if (lane == 0) red[kW + wid] = big;
+  __syncthreads();
+  uint32_t before = 0, bmax = 0;
+  for (uint32_t q = 0; q < kW; ++q) {
+    before += q < wid ? red[q] : 0u;
+    bmax = max(bmax, red[kW + q]);
+  }
+  __syncthreads();
+  if (bmax > kMaxSlotL) return false;  // uniform across the block
+  uint32_t run = before + incl - loc;
+#pragma unroll
+  for (int q = 0; q < kLargeR; ++q)
+    if ((uint32_t)q < R) {
+      const uint32_t c = sc[q * kLargeTPB + tid];
+      sc[q * kLargeTPB + tid] = run | (c << 16);  // slot start and count
+      run += c;
+    }
+  __syncthreads();
+  uint32_t e[kLargeR];
+#pragma unroll
+  for (int r = 0; r < kLargeR; ++r) {
+    e[r] = tid + kLargeTPB * r < n ? sc[at[r]] : 0u;
+    if (tid + kLargeTPB * r < n) sk[(e[r] & 0xFFFFu) + rk[r]] = u[r];
+  }
+  __syncthreads();
+  // a key's place: its slot's start plus the keys of the slot before it
+#pragma unroll
+  for (int r = 0; r < kLargeR; ++r) {
+    const uint32_t a0 = e[r] & 0xFFFFu, cn = e[r] >> 16, me = a0 + rk[r];
+    uint32_t p = a0;
+#pragma unroll 4
+    for (uint32_t i = a0; i < a0 + cn; ++i) {
+      const uint64_t x = sk[i];
+      p += (x < u[r]) | ((x == u[r]) & (i < me));
+    }
+    e[r] = p;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kLargeR; ++r)
+    if (tid + kLargeTPB * r < n) sk[e[r]] = u[r];
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += kLargeTPB) A[s.lo + i] = unord(sk[i], dt);
+  __syncthreads();
+  return true;
+}
+
+// Spans of kWarpSortMax+1 .. T keys: the placed block sort, else (clustered
+// spans, or spans above 4096 keys) a bitonic network over P = 2^ceil(log2 n)
+// keys in shared memory.  sk holds cap keys, then 4096 slot words.
+__global__ void __launch_bounds__(kLargeTPB, 2) k_base_large(const Span* spans, uint64_t n, uint64_t* A,
+                                                             const uint64_t* Bbuf, int dt, uint32_t cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* sc = reinterpret_cast<uint32_t*>(sm + cap);
+  __shared__ uint32_t red[2 * (kLargeTPB / 32)];
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
+    if (s.n <= kLargeTPB * kLargeR && block_placed_sort(s, A, Bbuf, dt, sm, sc, red)) continue;
     const uint64_t* src = s.buf ? Bbuf : A;
     uint32_t P = 2;
     while (P < s.n) P <<= 1;
@@ -1932,12 +2082,15 @@ void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t
     else launch_large(k_base_large_kv<4>, spans, n, P, (size_t)P * 12, st, set4, A, Bbuf, VA, VBuf, dt);
     return;
   }
-  size_t sm = (size_t)P * 8;
+  const uint32_t cap = P > kLargeTPB * kLargeR ? P : kLargeTPB * kLargeR;
+  size_t sm = (size_t)cap * 8 + (size_t)kLargeTPB * kLargeR * 4;
   static size_t set[64] = {};
   allow_smem(k_base_large, sm, set);
-  uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
-  uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
-  k_base_large<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, dt);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_base_large, kLargeTPB, sm);
+  if (per < 1) per = 1;
+  uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
+  k_base_large<<<(unsigned)grid, kLargeTPB, sm, st>>>(spans, n, A, Bbuf, dt, cap);
 }
 
 void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,

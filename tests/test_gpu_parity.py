@@ -190,6 +190,34 @@ def test_sort_edge_sizes(ctx, n):
     assert_same_sort(out, tr, got, st)
 
 
+def _large_span_inputs():
+    """Single spans of 257..8192 keys (the root goes straight to the block
+    base case): spread keys, keys sharing their high word, clustered keys
+    (one slot overflows and the block falls back to the bitonic network),
+    two values, and all-equal-but-one."""
+    rng = np.random.default_rng(11)
+    cases = []
+    for n in (257, 300, 1000, 2049, 4000, 4096):
+        cases.append(("normal", n, rng.standard_normal(n)))
+        cases.append(("low_word", n, rng.integers(0, 5000, n, dtype=np.uint64)))
+        c = np.full(n, 7.25)
+        c[rng.permutation(n)[: n // 10]] = rng.standard_normal(n // 10)
+        cases.append(("clustered", n, c))
+        cases.append(("two_values", n, np.where(rng.random(n) < 0.5, -3.0, 3.0)))
+        e = np.full(n, 1.5)
+        e[rng.integers(0, n)] = -2.0
+        cases.append(("one_differs", n, e))
+    for n in (4097, 6000, 8192):
+        cases.append(("normal", n, rng.standard_normal(n)))
+    return cases
+
+
+@pytest.mark.parametrize("name,n,x", _large_span_inputs(), ids=lambda v: str(v) if not hasattr(v, "shape") else "")
+def test_base_case_large_spans(ctx, name, n, x):
+    out, tr, hist, got, st = run_both(ctx, x, basecase_threshold=8192)
+    assert_same_sort(out, tr, got, st)
+
+
 def test_sort_special_values_and_all_equal(ctx):
     rng = np.random.default_rng(0)
     pool = np.array([-np.inf, -1e300, -1.0, -5e-324, -0.0, 0.0, 5e-324, 0.5, 1.0, 1e300, np.inf])
