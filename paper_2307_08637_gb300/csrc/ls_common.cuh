@@ -153,6 +153,10 @@ __host__ __device__ __forceinline__ uint64_t seed_item(uint64_t seed, uint64_t s
 
 // ------------------------------------------------------------- FP64 model
 
+// First statement of every kernel: wait for the stream's previous kernel
+// when this one was launched as a programmatic dependent (no-op otherwise).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ double dmax(double p, double q) { return (p < q) ? q : p; }
 __device__ __forceinline__ double dmin(double p, double q) { return (q < p) ? q : p; }
 

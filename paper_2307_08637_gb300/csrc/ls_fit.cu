@@ -124,6 +124,7 @@ __device__ double block_tree_sum(double* p, double* q, uint64_t m) {
 // ------------------------------------------------------------ sampling
 
 __global__ void k_sample_gather(FreshArgs f, RunParams rp, uint64_t* __restrict__ samp) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= f.total_samples) return;
   uint32_t fi = find_seg(f.samp_prefix, f.nfresh, g);
@@ -145,6 +146,7 @@ __global__ void k_sample_gather(FreshArgs f, RunParams rp, uint64_t* __restrict_
 }
 
 __global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   bool valid = g < f.total_samples;
   uint32_t fi = valid ? find_seg(f.samp_prefix, f.nfresh, g) : 0xFFFFFFFFu;
@@ -166,6 +168,7 @@ __global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
 
 __global__ void __launch_bounds__(kTPB) k_sort_chunks(uint64_t* __restrict__ a, const uint64_t* __restrict__ off,
                                                       const uint64_t* __restrict__ cpre, uint32_t nseg) {
+  pdl_wait();
   __shared__ uint64_t sm[kSortChunk];
   uint64_t c = blockIdx.x;
   uint32_t s = find_seg(cpre, nseg, c);
@@ -199,6 +202,7 @@ __global__ void __launch_bounds__(kTPB) k_sort_chunks(uint64_t* __restrict__ a, 
 __global__ void __launch_bounds__(kTPB) k_merge_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                      const uint64_t* __restrict__ off,
                                                      const uint64_t* __restrict__ cpre, uint32_t nseg, uint64_t w) {
+  pdl_wait();
   uint64_t c = blockIdx.x;
   uint32_t s = find_seg(cpre, nseg, c);
   uint64_t sb = off[s];
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(kTPB) k_merge_pass(const uint64_t* __restrict_
 
 // One warp per root chunk of every candidate.
 __global__ void k_fit_root_partials(FitArgs a, RunParams rp) {
+  pdl_wait();
   const uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (g >= a.total_rchunks) return;  // uniform across the warp
   const uint32_t c = find_seg(a.rchunk_prefix, a.ncand, g);
@@ -249,6 +254,7 @@ __global__ void k_fit_root_partials(FitArgs a, RunParams rp) {
 
 // Per candidate: tree-combine the root chunk partials, fit the root.
 __global__ void k_fit_root_finish(FitArgs a, RunParams rp) {
+  pdl_wait();
   uint32_t c = blockIdx.x;
   const Plan& pl = a.plans[a.cand[c]];
   uint64_t b0 = a.rchunk_prefix[c];
@@ -281,6 +287,7 @@ __global__ void k_fit_root_finish(FitArgs a, RunParams rp) {
 
 // Route every sample point to its leaf (stored), then mark run starts.
 __global__ void k_fit_route_leaf(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_of) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= a.total_cand_samples) return;
   uint32_t c = find_seg(a.cand_soff, a.ncand, g);
@@ -291,6 +298,7 @@ __global__ void k_fit_route_leaf(FitArgs a, RunParams rp, uint32_t* __restrict__
 }
 
 __global__ void k_fit_route_starts(FitArgs a, const uint32_t* __restrict__ leaf_of) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= a.total_cand_samples) return;
   uint32_t c = find_seg(a.cand_soff, a.ncand, g);
@@ -312,6 +320,7 @@ __global__ void k_fit_route_starts(FitArgs a, const uint32_t* __restrict__ leaf_
 }
 
 __global__ void k_fit_leaf_chunk_count(FitArgs a) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t tot = (uint64_t)a.ncand * a.L;
   if (g > tot) return;
@@ -327,6 +336,7 @@ __global__ void k_fit_leaf_chunk_count(FitArgs a) {
 
 // One warp per leaf chunk of every candidate.
 __global__ void k_fit_leaf_partials(FitArgs a, RunParams rp) {
+  pdl_wait();
   const uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint32_t tot = a.ncand * a.L;
   if (g >= a.lchunk_prefix[tot] || g >= a.lchunk_bound) return;  // uniform across the warp
@@ -350,6 +360,7 @@ __global__ void k_fit_leaf_partials(FitArgs a, RunParams rp) {
 }
 
 __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_cnt) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= (uint64_t)a.ncand * a.L) return;
   uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
@@ -390,6 +401,7 @@ __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict_
 // associative and a parallel prefix max gives the sequential result bit for
 // bit.  One block per candidate; also sets the model's finite flag.
 __global__ void __launch_bounds__(1024) k_fit_monotone(FitArgs a, const uint32_t* __restrict__ leaf_cnt) {
+  pdl_wait();
   uint32_t c = blockIdx.x;
   const Plan& pl = a.plans[a.cand[c]];
   DModel& md = a.models[pl.model];
@@ -629,6 +641,7 @@ __device__ __forceinline__ void pivot_prep(const DModel& m, const Leaf* lv, cons
 __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
                                  uint32_t nb_pad, const DModel* models, const Leaf* leaves,
                                  uint64_t* __restrict__ pivots, RunParams rp) {
+  pdl_wait();
   __shared__ PivotPrep s_prep;
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const bool shared_prep = nb_pad % blockDim.x == 0;
@@ -804,6 +817,7 @@ __global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t*
 // the block adds its histogram to the candidate's counts at the end.
 __global__ void k_imbalance_count(FitArgs a, const uint64_t* __restrict__ pivots,
                                   unsigned long long* __restrict__ cnt, uint32_t nbp_max) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
   uint32_t* sH = reinterpret_cast<uint32_t*>(sT + nbp_max);
@@ -829,6 +843,7 @@ __global__ void k_imbalance_count(FitArgs a, const uint64_t* __restrict__ pivots
 }
 
 __global__ void k_imbalance_max(FitArgs a, unsigned long long* __restrict__ cnt) {
+  pdl_wait();
   uint32_t c = blockIdx.x;
   Plan& pl = a.plans[a.cand[c]];
   unsigned long long mx = 0;
@@ -854,6 +869,7 @@ __global__ void k_imbalance_max(FitArgs a, unsigned long long* __restrict__ cnt)
 // Alg. 5 BuildPartitionModel: RMI iff the input is large and the sample has
 // few duplicates (and, in AUTO, the sample is not badly imbalanced).
 __global__ void k_decide(FreshArgs f, const DModel* models, RunParams rp) {
+  pdl_wait();
   uint32_t fi = blockIdx.x * blockDim.x + threadIdx.x;
   if (fi >= f.nfresh) return;
   uint32_t pi = f.fresh[fi];
@@ -898,6 +914,7 @@ __global__ void k_decide(FreshArgs f, const DModel* models, RunParams rp) {
 // forced).  Written as exact pivots: bucket = #{j : T[j] <= ord}.
 __global__ void __launch_bounds__(1024) k_splitter_build(FreshArgs f, const uint64_t* __restrict__ samp,
                                                          uint64_t* __restrict__ pivots, RunParams rp) {
+  pdl_wait();
   uint32_t pi = f.fresh[blockIdx.x];
   Plan& pl = f.plans[pi];
   const Item& it = f.items[pi];
@@ -1011,6 +1028,7 @@ __global__ void __launch_bounds__(1024) k_splitter_build(FreshArgs f, const uint
 
 __global__ void k_dir_build(Plan* plans, uint32_t nplans, uint32_t cells, const uint64_t* __restrict__ pivots,
                             uint16_t* __restrict__ dirs) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t per = (uint64_t)cells + 1;
   if (g >= (uint64_t)nplans * per) return;
@@ -1073,6 +1091,7 @@ struct GradScratch {
 
 __global__ void k_grad_fwd(const DModel* mp, const Leaf* leaves, const uint64_t* __restrict__ bits, uint64_t S,
                            int dt, double* pred, double* resid, GradScratch g) {
+  pdl_wait();
   uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (j >= S) return;
   DModel m = *mp;
@@ -1099,6 +1118,7 @@ __global__ void k_grad_fwd(const DModel* mp, const Leaf* leaves, const uint64_t*
 }
 
 __global__ void k_grad_leaf_starts(const uint64_t* __restrict__ sorted, uint64_t S, uint32_t L, uint32_t* lstart) {
+  pdl_wait();
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q >= S) return;
   uint32_t lf = (uint32_t)(sorted[q] >> 32);
@@ -1115,6 +1135,7 @@ __global__ void k_grad_leaf_starts(const uint64_t* __restrict__ sorted, uint64_t
 }
 
 __global__ void k_grad_chunk_count(const uint32_t* lstart, uint32_t L, uint64_t* lch) {
+  pdl_wait();
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > L) return;
   lch[i] = (i == L) ? 0 : ((uint64_t)(lstart[i + 1] - lstart[i]) + kChunk - 1) / kChunk;
@@ -1122,6 +1143,7 @@ __global__ void k_grad_chunk_count(const uint32_t* lstart, uint32_t L, uint64_t*
 
 __global__ void k_grad_leaf_partials(const uint64_t* __restrict__ sorted, const uint32_t* lstart, const uint64_t* lchp,
                                      uint32_t L, uint64_t bound, GradScratch g) {
+  pdl_wait();
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q >= lchp[L] || q >= bound) return;
   uint32_t i = find_seg(lchp, L, q);
@@ -1142,6 +1164,7 @@ __global__ void k_grad_leaf_partials(const uint64_t* __restrict__ sorted, const 
 
 __global__ void k_grad_leaf_finish(const uint64_t* lchp, uint32_t L, uint64_t bound, uint64_t S, GradScratch g,
                                    double* grad_a, double* grad_b) {
+  pdl_wait();
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   uint64_t p0 = lchp[i], m = lchp[i + 1] - p0;
@@ -1153,6 +1176,7 @@ __global__ void k_grad_leaf_finish(const uint64_t* lchp, uint32_t L, uint64_t bo
 }
 
 __global__ void k_grad_root_partials(uint64_t S, uint64_t nch, GradScratch g) {
+  pdl_wait();
   uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (c >= nch) return;
   uint64_t a0 = c * kChunk, a1 = a0 + kChunk < S ? a0 + kChunk : S;
@@ -1167,6 +1191,7 @@ __global__ void k_grad_root_partials(uint64_t S, uint64_t nch, GradScratch g) {
 }
 
 __global__ void k_grad_root_finish(uint64_t S, uint64_t nch, GradScratch g, double* grad_root) {
+  pdl_wait();
   double srx = block_tree_sum(g.rpart, g.rpart + 2 * nch, nch);
   double sr = block_tree_sum(g.rpart + nch, g.rpart + 3 * nch, nch);
   if (threadIdx.x == 0 && grad_root) {
@@ -1198,6 +1223,7 @@ __device__ __forceinline__ void fmodel_one(const DModel* models, const Leaf* lea
 
 __global__ void k_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots,
                          uint32_t L, FModel* fm, FLeaf* fl) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= (uint64_t)nslots * (L + 1)) return;
   uint32_t c = (uint32_t)(g / (L + 1)), i = (uint32_t)(g % (L + 1));
@@ -1205,6 +1231,7 @@ __global__ void k_fmodel(const DModel* models, const Leaf* leaves, const int32_t
 }
 
 __global__ void k_fmodel_fit(FitArgs a) {
+  pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= (uint64_t)a.ncand * (a.L + 1)) return;
   uint32_t c = (uint32_t)(g / (a.L + 1)), i = (uint32_t)(g % (a.L + 1));
@@ -1219,12 +1246,12 @@ uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, co
                              uint32_t nseg, uint64_t total_chunks, uint64_t max_len, cudaStream_t st,
                              uint64_t* launches) {
   if (total_chunks == 0) return a;
-  k_sort_chunks<<<(unsigned)total_chunks, kTPB, 0, st>>>(a, d_off, d_chunk_prefix, nseg);
+  pdl_launch(k_sort_chunks, (unsigned)total_chunks, kTPB, 0, st, a, d_off, d_chunk_prefix, nseg);
   ++*launches;
   uint64_t* cur = a;
   uint64_t* oth = b;
   for (uint64_t w = kSortChunk; w < max_len; w *= 2) {
-    k_merge_pass<<<(unsigned)total_chunks, kTPB, 0, st>>>(cur, oth, d_off, d_chunk_prefix, nseg, w);
+    pdl_launch(k_merge_pass, (unsigned)total_chunks, kTPB, 0, st, cur, oth, d_off, d_chunk_prefix, nseg, w);
     ++*launches;
     uint64_t* t = cur;
     cur = oth;
@@ -1235,35 +1262,35 @@ uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, co
 
 void launch_sample_gather(const FreshArgs& f, const RunParams& rp, uint64_t* samp, cudaStream_t st) {
   if (!f.total_samples) return;
-  k_sample_gather<<<grid_for(f.total_samples), kTPB, 0, st>>>(f, rp, samp);
+  pdl_launch(k_sample_gather, grid_for(f.total_samples), kTPB, 0, st, f, rp, samp);
 }
 
 void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st) {
   if (!f.total_samples) return;
-  k_dups<<<grid_for(f.total_samples), kTPB, 0, st>>>(f, samp);
+  pdl_launch(k_dups, grid_for(f.total_samples), kTPB, 0, st, f, samp);
 }
 
 void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches) {
   if (!a.ncand) return;
-  k_fit_root_partials<<<grid_for(a.total_rchunks * 32, 128), 128, 0, st>>>(a, rp);
-  k_fit_root_finish<<<a.ncand, 1024, 0, st>>>(a, rp);
+  pdl_launch(k_fit_root_partials, grid_for(a.total_rchunks * 32, 128), 128, 0, st, a, rp);
+  pdl_launch(k_fit_root_finish, a.ncand, 1024, 0, st, a, rp);
   cudaMemsetAsync(a.leaf_start, 0, (size_t)a.ncand * (a.L + 1) * sizeof(uint32_t), st);
-  k_fit_route_leaf<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, rp, a.leaf_of);
-  k_fit_route_starts<<<grid_for(a.total_cand_samples), kTPB, 0, st>>>(a, a.leaf_of);
+  pdl_launch(k_fit_route_leaf, grid_for(a.total_cand_samples), kTPB, 0, st, a, rp, a.leaf_of);
+  pdl_launch(k_fit_route_starts, grid_for(a.total_cand_samples), kTPB, 0, st, a, a.leaf_of);
   uint64_t tot = (uint64_t)a.ncand * a.L;
-  k_fit_leaf_chunk_count<<<grid_for(tot + 1), kTPB, 0, st>>>(a);
+  pdl_launch(k_fit_leaf_chunk_count, grid_for(tot + 1), kTPB, 0, st, a);
   launch_scan_exclusive_u64(a.lchunk_cnt, a.lchunk_prefix, tot, a.scan_tmp, a.scan_tmp_elems, st);
-  k_fit_leaf_partials<<<grid_for(a.lchunk_bound * 32, 128), 128, 0, st>>>(a, rp);
-  k_fit_leaf_finish<<<grid_for(tot, 128), 128, 0, st>>>(a, rp, a.leaf_cnt);
-  k_fit_monotone<<<a.ncand, 1024, 0, st>>>(a, a.leaf_cnt);
-  k_fmodel_fit<<<grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st>>>(a);
+  pdl_launch(k_fit_leaf_partials, grid_for(a.lchunk_bound * 32, 128), 128, 0, st, a, rp);
+  pdl_launch(k_fit_leaf_finish, grid_for(tot, 128), 128, 0, st, a, rp, a.leaf_cnt);
+  pdl_launch(k_fit_monotone, a.ncand, 1024, 0, st, a, a.leaf_cnt);
+  pdl_launch(k_fmodel_fit, grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st, a);
   *launches += 13;
 }
 
 void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
                    FModel* fm, FLeaf* fl, cudaStream_t st) {
   if (!nslots) return;
-  k_fmodel<<<grid_for((uint64_t)nslots * (L + 1)), kTPB, 0, st>>>(models, leaves, slots, nslots, L, fm, fl);
+  pdl_launch(k_fmodel, grid_for((uint64_t)nslots * (L + 1)), kTPB, 0, st, models, leaves, slots, nslots, L, fm, fl);
 }
 
 void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,
@@ -1271,7 +1298,7 @@ void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
                            cudaStream_t st) {
   if (!nlist) return;
   uint64_t n = (uint64_t)nlist * nb_pad;
-  k_learned_pivots<<<grid_for(n, 128), 128, 0, st>>>(plans, items, list, nlist, nb_pad, models, leaves, pivots, rp);
+  pdl_launch(k_learned_pivots, grid_for(n, 128), 128, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots, rp);
 }
 
 void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,
@@ -1292,27 +1319,27 @@ void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cn
   const uint64_t per = (a.total_cand_samples + a.ncand - 1) / a.ncand;  // mean samples per candidate
   uint64_t gx = (per + kTPB * 8 - 1) / (kTPB * 8);
   gx = gx < 1 ? 1 : (gx > 256 ? 256 : gx);
-  k_imbalance_count<<<dim3((unsigned)gx, a.ncand), kTPB, sm, st>>>(a, pivots, cnt_pool, nbp_max);
-  k_imbalance_max<<<a.ncand, kTPB, 0, st>>>(a, cnt_pool);
+  pdl_launch(k_imbalance_count, dim3((unsigned)gx, a.ncand), kTPB, sm, st, a, pivots, cnt_pool, nbp_max);
+  pdl_launch(k_imbalance_max, a.ncand, kTPB, 0, st, a, cnt_pool);
   *launches += 2;
 }
 
 void launch_decide(const FreshArgs& f, const DModel* models, const RunParams& rp, cudaStream_t st) {
   if (!f.nfresh) return;
-  k_decide<<<grid_for(f.nfresh, 128), 128, 0, st>>>(f, models, rp);
+  pdl_launch(k_decide, grid_for(f.nfresh, 128), 128, 0, st, f, models, rp);
 }
 
 void launch_splitter_build(const FreshArgs& f, const uint64_t* samp, uint64_t* pivots, const RunParams& rp,
                            cudaStream_t st) {
   if (!f.nfresh) return;
-  k_splitter_build<<<f.nfresh, 1024, 0, st>>>(f, samp, pivots, rp);
+  pdl_launch(k_splitter_build, f.nfresh, 1024, 0, st, f, samp, pivots, rp);
 }
 
 void launch_dir_build(Plan* plans, uint32_t nplans, uint32_t cells, const uint64_t* pivots, uint16_t* dirs,
                       cudaStream_t st) {
   if (!nplans) return;
   uint64_t n = (uint64_t)nplans * (cells + 1);
-  k_dir_build<<<grid_for(n), kTPB, 0, st>>>(plans, nplans, cells, pivots, dirs);
+  pdl_launch(k_dir_build, grid_for(n), kTPB, 0, st, plans, nplans, cells, pivots, dirs);
 }
 
 size_t fit_grad_scratch_bytes(uint64_t S, uint32_t L) {
@@ -1364,20 +1391,20 @@ void launch_fit_grad(const DModel* model, const Leaf* leaves, const uint64_t* sa
   g.part = reinterpret_cast<double*>(take(2 * bound * 8));
   g.rpart = reinterpret_cast<double*>(take(4 * (nch + 1) * 8));
   const Leaf* lv = leaves + hm.leaf_off;
-  k_grad_fwd<<<grid_for(S), kTPB, 0, st>>>(model, lv, sample_bits, S, dt, pred, resid, g);
+  pdl_launch(k_grad_fwd, grid_for(S), kTPB, 0, st, model, lv, sample_bits, S, dt, pred, resid, g);
   uint64_t hoff[2] = {0, S};
   uint64_t hcp[2] = {0, (S + kSortChunk - 1) / kSortChunk};
   cudaMemcpyAsync(g.segoff, hoff, sizeof hoff, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(g.cpre, hcp, sizeof hcp, cudaMemcpyHostToDevice, st);
   uint64_t dummy = 0;
   uint64_t* sorted = segmented_sort_u64(g.key, g.key2, g.segoff, g.cpre, 1, hcp[1], S, st, &dummy);
-  k_grad_leaf_starts<<<grid_for(S), kTPB, 0, st>>>(sorted, S, L, g.lstart);
-  k_grad_chunk_count<<<grid_for(L + 1), kTPB, 0, st>>>(g.lstart, L, g.lch);
+  pdl_launch(k_grad_leaf_starts, grid_for(S), kTPB, 0, st, sorted, S, L, g.lstart);
+  pdl_launch(k_grad_chunk_count, grid_for(L + 1), kTPB, 0, st, g.lstart, L, g.lch);
   launch_scan_exclusive_u64(g.lch, g.lchp, L, g.stmp, g.stmp_elems, st);
-  k_grad_leaf_partials<<<grid_for(bound), kTPB, 0, st>>>(sorted, g.lstart, g.lchp, L, bound, g);
-  k_grad_leaf_finish<<<grid_for(L), kTPB, 0, st>>>(g.lchp, L, bound, S, g, grad_a, grad_b);
-  k_grad_root_partials<<<grid_for(nch), kTPB, 0, st>>>(S, nch, g);
-  k_grad_root_finish<<<1, 1024, 0, st>>>(S, nch, g, grad_root);
+  pdl_launch(k_grad_leaf_partials, grid_for(bound), kTPB, 0, st, sorted, g.lstart, g.lchp, L, bound, g);
+  pdl_launch(k_grad_leaf_finish, grid_for(L), kTPB, 0, st, g.lchp, L, bound, S, g, grad_a, grad_b);
+  pdl_launch(k_grad_root_partials, grid_for(nch), kTPB, 0, st, S, nch, g);
+  pdl_launch(k_grad_root_finish, 1, 1024, 0, st, S, nch, g, grad_root);
   cudaStreamSynchronize(st);  // hoff / hcp live on this stack frame
 }
 

@@ -10,6 +10,31 @@
 
 namespace lsg {
 
+// Programmatic dependent launch: a kernel launched this way may be set up
+// while the previous kernel of its stream is still running; every kernel's
+// first statement (pdl_wait) blocks until that kernel has finished and its
+// writes are visible, so the stream order of the data is unchanged and only
+// the launch latency between dependent kernels is hidden.
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+}  // namespace lsg
+
+namespace lsg {
+
 // Run parameters copied into kernels by value.
 struct RunParams {
   uint32_t B;             // learned fanout

@@ -213,6 +213,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
 // each instance's registers and instructions to what it needs.
 template <int CLS, int DT, bool NANCHK>
 __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs a, RunParams rp) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
   void* sD = sT + a.nb_pad_max;  // directory or FP32 leaves (aux_bytes, 16-byte aligned)
@@ -308,6 +309,7 @@ constexpr int k3_min_blocks(int tpb, int qm, int vb) {
 
 template <int TPB, int QM, int VB>
 __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(PassArgs a, RunParams rp) {
+  pdl_wait();
   constexpr uint32_t kW = TPB / 32;          // warps
   constexpr uint32_t kKT = kTile / TPB;      // keys per thread per tile
   constexpr uint32_t kWK = kTile / kW;       // keys of a tile ranked by one warp
@@ -516,6 +518,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
 // the thread that owns the column, before it is written).
 __global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans, uint32_t* agg,
                                unsigned long long* __restrict__ excl, uint32_t nbp) {
+  pdl_wait();
   const ChunkSeg sg = segs[blockIdx.x];
   const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
   if (b >= plans[sg.plan].nb_pad) return;
@@ -537,6 +540,7 @@ __global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __
 // runs).  One thread per column; the loads of eight runs are issued together.
 __global__ void k_run_scan(const uint2* __restrict__ multi, const ChunkSeg* __restrict__ segs,
                            const Plan* __restrict__ plans, uint32_t* agg, uint32_t nbp) {
+  pdl_wait();
   const uint2 mi = multi[blockIdx.x];  // (first run, number of runs)
   const ChunkSeg f = segs[mi.x];
   const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
@@ -559,6 +563,7 @@ __global__ void k_run_scan(const uint2* __restrict__ multi, const ChunkSeg* __re
 // Carry pass: add each run's carry (from k_run_scan) to its chunks.
 __global__ void k_chunk_carry(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans,
                               const uint32_t* __restrict__ agg, unsigned long long* __restrict__ excl, uint32_t nbp) {
+  pdl_wait();
   const ChunkSeg sg = segs[blockIdx.x];
   if (blockIdx.x == sg.first) return;
   const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
@@ -627,6 +632,7 @@ enum { L_NEXT = 0, L_SMALL, L_LARGE, L_COPY, L_FALLBACK, L_N };
 // cases, copies, fallback).  Thread t owns a contiguous range of buckets, so
 // the lists keep bucket order within an item.
 __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams rp) {
+  pdl_wait();
   uint32_t pi = blockIdx.x;
   const Item& it = a.items[pi];
   Plan& pl = a.plans[pi];
@@ -1150,6 +1156,7 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
 
 __global__ void __launch_bounds__(kTPB, 4) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
                                                      int dt) {
+  pdl_wait();
   __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
   __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
   const unsigned wid = threadIdx.x >> 5;
@@ -1322,6 +1329,7 @@ __device__ __forceinline__ bool warp_placed_sort_kv(const Span& s, uint64_t* A, 
 template <int VB>
 __global__ void __launch_bounds__(kTPB, 3) k_base_small_kv(const Span* spans, uint64_t n, uint64_t* A,
                                                         const uint64_t* Bbuf, void* VA, const void* VBuf, int dt) {
+  pdl_wait();
   using V = ValT<VB>;
   __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
   __shared__ uint16_t s_idx[kTPB / 32][kWarpSortMax];
@@ -1388,6 +1396,7 @@ __device__ void block_bitonic_smem_kv(uint64_t* sm, uint32_t* si, uint32_t P) {
 template <int VB>
 __global__ void __launch_bounds__(1024) k_base_large_kv(const Span* spans, uint64_t n, uint64_t* A,
                                                         const uint64_t* Bbuf, void* VA, const void* VBuf, int dt) {
+  pdl_wait();
   using V = ValT<VB>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
@@ -1427,6 +1436,7 @@ __global__ void __launch_bounds__(1024) k_base_large_kv(const Span* spans, uint6
 template <int VB>
 __global__ void k_copy_spans_kv(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA,
                                 const void* VBuf) {
+  pdl_wait();
   using V = ValT<VB>;
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     const Span s = spans[w];
@@ -1444,6 +1454,7 @@ __global__ void k_copy_spans_kv(const Span* spans, uint64_t n, uint64_t* A, cons
 template <int VB>
 __global__ void __launch_bounds__(1024) k_fallback_kv(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
                                                       void* VA, void* VBuf, int dt) {
+  pdl_wait();
   using V = ValT<VB>;
   __shared__ uint64_t sm[kSortChunk];
   __shared__ uint32_t si[kSortChunk];
@@ -1688,6 +1699,7 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
 // keys in shared memory.  sk holds cap keys, then 4096 slot words.
 __global__ void __launch_bounds__(kLargeTPB, 2) k_base_large(const Span* spans, uint64_t n, uint64_t* A,
                                                              const uint64_t* Bbuf, int dt, uint32_t cap) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
   uint32_t* sc = reinterpret_cast<uint32_t*>(sm + cap);
@@ -1707,6 +1719,7 @@ __global__ void __launch_bounds__(kLargeTPB, 2) k_base_large(const Span* spans, 
 }
 
 __global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf) {
+  pdl_wait();
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
     for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) A[s.lo + i] = Bbuf[s.lo + i];
@@ -1718,6 +1731,7 @@ __global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const u
 // passes), leaving the result in A.
 __global__ void __launch_bounds__(1024) k_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
                                                    int dt) {
+  pdl_wait();
   __shared__ uint64_t sm[kSortChunk];
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
@@ -1775,6 +1789,7 @@ __global__ void __launch_bounds__(1024) k_fallback(const Span* spans, uint64_t n
 // the host link instead of a copy engine (the engines stay free for a
 // concurrent sort's small copies).  16-byte words when both ends allow.
 __global__ void k_link_copy(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst, size_t bytes) {
+  pdl_wait();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
@@ -1803,6 +1818,7 @@ __global__ void k_link_copy(const unsigned char* __restrict__ src, unsigned char
 __global__ void k_direct_classify(const DModel* mp, const Leaf* leaves, const uint64_t* __restrict__ keys, uint64_t n,
                                   int dt, double P, double Bg, uint32_t B, uint32_t* ids,
                                   unsigned long long* hist) {
+  pdl_wait();
   DModel m = *mp;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t b = refine_id(m, leaves + m.leaf_off, key_value(keys[i], dt), P, Bg, B);
@@ -1815,6 +1831,7 @@ __global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const
                                  const uint64_t* __restrict__ keys, uint64_t n, int dt, uint32_t* ids,
                                  unsigned long long* hist, uint32_t nb_pad, uint32_t cells, const FModel* fmp,
                                  const FLeaf* flp, uint32_t aux_bytes) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sT = reinterpret_cast<uint64_t*>(smem);
   void* sAux = sT + nb_pad;
@@ -1863,6 +1880,7 @@ __global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const
 
 __global__ void k_scan_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, size_t n,
                              uint64_t* __restrict__ bsum) {
+  pdl_wait();
   __shared__ uint64_t w[32];
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   uint64_t x = i < n ? in[i] : 0;
@@ -1889,17 +1907,20 @@ __global__ void k_scan_block(const uint64_t* __restrict__ in, uint64_t* __restri
 }
 
 __global__ void k_scan_add(uint64_t* __restrict__ out, size_t n, const uint64_t* __restrict__ boff) {
+  pdl_wait();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] += boff[blockIdx.x];
 }
 
 __global__ void k_scan_total(uint64_t* out, size_t n, const uint64_t* in) {
+  pdl_wait();
   // out[n] = out[n-1] + in[n-1]
   if (n == 0) out[0] = 0;
   else out[n] = out[n - 1] + in[n - 1];
 }
 
 __global__ void k_fill_u64(uint64_t* p, uint64_t v, size_t n) {
+  pdl_wait();
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
 }
@@ -1924,22 +1945,22 @@ void launch_scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, uint
                                cudaStream_t st) {
   (void)tmp_elems;
   if (n == 0) {
-    k_scan_total<<<1, 1, 0, st>>>(out, 0, in);
+    pdl_launch(k_scan_total, 1, 1, 0, st, out, 0, in);
     return;
   }
   size_t nb = (n + kScanTPB - 1) / kScanTPB;
   uint64_t* bsum = tmp;
   uint64_t* boff = tmp + nb + 1;
-  k_scan_block<<<(unsigned)nb, kScanTPB, 0, st>>>(in, out, n, bsum);
+  pdl_launch(k_scan_block, (unsigned)nb, kScanTPB, 0, st, in, out, n, bsum);
   if (nb > 1) {
     launch_scan_exclusive_u64(bsum, boff, nb, tmp + 2 * nb + 2, 0, st);
-    k_scan_add<<<(unsigned)nb, kScanTPB, 0, st>>>(out, n, boff);
+    pdl_launch(k_scan_add, (unsigned)nb, kScanTPB, 0, st, out, n, boff);
   }
-  k_scan_total<<<1, 1, 0, st>>>(out, n, in);
+  pdl_launch(k_scan_total, 1, 1, 0, st, out, n, in);
 }
 
 void launch_fill_u64(uint64_t* p, uint64_t v, size_t n, cudaStream_t st) {
-  if (n) k_fill_u64<<<grid_for(n), kTPB, 0, st>>>(p, v, n);
+  if (n) pdl_launch(k_fill_u64, grid_for(n), kTPB, 0, st, p, v, n);
 }
 
 static int sm_count() {
@@ -1982,7 +2003,7 @@ static void launch_k1(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_classify_hist<CLS, DT, NANCHK><<<(unsigned)grid, kTPB, sm, st>>>(a, rp);
+  pdl_launch(k_classify_hist<CLS, DT, NANCHK>, (unsigned)grid, kTPB, sm, st, a, rp);
 }
 
 template <int CLS>
@@ -2006,10 +2027,10 @@ int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi
                         const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st) {
   if (!nsegs) return 0;
   const unsigned cols = (nbp + kTPB - 1) / kTPB;
-  k_chunk_prefix<<<dim3(nsegs, cols), kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  pdl_launch(k_chunk_prefix, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp);
   if (!nmulti) return 1;
-  k_run_scan<<<dim3(nmulti, cols), kTPB, 0, st>>>(multi, segs, plans, agg, nbp);
-  k_chunk_carry<<<dim3(nsegs, cols), kTPB, 0, st>>>(segs, plans, agg, excl, nbp);
+  pdl_launch(k_run_scan, dim3(nmulti, cols), kTPB, 0, st, multi, segs, plans, agg, nbp);
+  pdl_launch(k_chunk_carry, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp);
   return 3;
 }
 
@@ -2023,7 +2044,7 @@ static void launch_k3(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (per < 1) per = 1;
   uint64_t grid = (uint64_t)sm_count() * per;
   if (grid > a.nchunks) grid = a.nchunks;
-  k_scatter<TPB, QM, VB><<<(unsigned)grid, TPB, sm, st>>>(a, rp);
+  pdl_launch(k_scatter<TPB, QM, VB>, (unsigned)grid, TPB, sm, st, a, rp);
 }
 
 // Up to 1024 buckets: 16-warp blocks (two per SM); larger tables keep the
@@ -2047,7 +2068,7 @@ void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   size_t sm = (size_t)(LS_MAX_FANOUT + 1) * 8 + LS_MAX_FANOUT + 16;
   static size_t set[64] = {};
   allow_smem(k_children, sm, set);
-  k_children<<<a.nitems, kK2Threads, sm, st>>>(a, rp);
+  pdl_launch(k_children, a.nitems, kK2Threads, sm, st, a, rp);
 }
 
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
@@ -2057,9 +2078,9 @@ void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_
   uint64_t blocks = (warps * 32 + kTPB - 1) / kTPB;
   uint64_t cap = (uint64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
-  if (vb == 8) k_base_small_kv<8><<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
-  else if (vb == 4) k_base_small_kv<4><<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
-  else k_base_small<<<(unsigned)blocks, kTPB, 0, st>>>(spans, n, A, Bbuf, dt);
+  if (vb == 8) pdl_launch(k_base_small_kv<8>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
+  else if (vb == 4) pdl_launch(k_base_small_kv<4>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
+  else pdl_launch(k_base_small, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt);
 }
 
 template <typename F>
@@ -2068,7 +2089,7 @@ static void launch_large(F* f, const Span* spans, uint64_t n, uint32_t P, size_t
   allow_smem(f, sm, set);
   uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
   uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
-  f<<<(unsigned)grid, tpb, sm, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
+  pdl_launch(f, (unsigned)grid, tpb, sm, st, spans, n, A, Bbuf, VA, VBuf, dt);
 }
 
 void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
@@ -2090,25 +2111,25 @@ void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_base_large, kLargeTPB, sm);
   if (per < 1) per = 1;
   uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
-  k_base_large<<<(unsigned)grid, kLargeTPB, sm, st>>>(spans, n, A, Bbuf, dt, cap);
+  pdl_launch(k_base_large, (unsigned)grid, kLargeTPB, sm, st, spans, n, A, Bbuf, dt, cap);
 }
 
 void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
                        uint32_t vb, cudaStream_t st) {
   if (!n) return;
   uint64_t grid = n < (uint64_t)sm_count() * 16 ? n : (uint64_t)sm_count() * 16;
-  if (vb == 8) k_copy_spans_kv<8><<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf);
-  else if (vb == 4) k_copy_spans_kv<4><<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf, VA, VBuf);
-  else k_copy_spans<<<(unsigned)grid, kTPB, 0, st>>>(spans, n, A, Bbuf);
+  if (vb == 8) pdl_launch(k_copy_spans_kv<8>, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf);
+  else if (vb == 4) pdl_launch(k_copy_spans_kv<4>, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf);
+  else pdl_launch(k_copy_spans, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf);
 }
 
 void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
                      int dt, cudaStream_t st) {
   if (!n) return;
   uint64_t grid = n < (uint64_t)sm_count() * 2 ? n : (uint64_t)sm_count() * 2;
-  if (vb == 8) k_fallback_kv<8><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
-  else if (vb == 4) k_fallback_kv<4><<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, VA, VBuf, dt);
-  else k_fallback<<<(unsigned)grid, 1024, 0, st>>>(spans, n, A, Bbuf, dt);
+  if (vb == 8) pdl_launch(k_fallback_kv<8>, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
+  else if (vb == 4) pdl_launch(k_fallback_kv<4>, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
+  else pdl_launch(k_fallback, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, dt);
 }
 
 void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st) {
@@ -2122,7 +2143,7 @@ void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t*
   uint64_t grid = grid_for(n);
   uint64_t cap = (uint64_t)sm_count() * 8;
   if (grid > cap) grid = cap;
-  k_direct_classify<<<(unsigned)grid, kTPB, 0, st>>>(m, leaves, keys, n, dt, P, Bg, B, ids, hist);
+  pdl_launch(k_direct_classify, (unsigned)grid, kTPB, 0, st, m, leaves, keys, n, dt, P, Bg, B, ids, hist);
 }
 
 void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint16_t* dirs, const uint64_t* keys,
@@ -2136,7 +2157,7 @@ void launch_table_classify(const Plan* plan, const uint64_t* pivots, const uint1
   uint64_t grid = grid_for(n);
   uint64_t cap = (uint64_t)sm_count() * 4;
   if (grid > cap) grid = cap;
-  k_table_classify<<<(unsigned)grid, kTPB, sm, st>>>(plan, pivots, dirs, keys, n, dt, ids, hist, nb_pad, cells, fm,
+  pdl_launch(k_table_classify, (unsigned)grid, kTPB, sm, st, plan, pivots, dirs, keys, n, dt, ids, hist, nb_pad, cells, fm,
                                                       fl, aux);
 }
 
