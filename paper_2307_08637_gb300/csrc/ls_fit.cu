@@ -635,180 +635,225 @@ __device__ __forceinline__ void pivot_prep(const DModel& m, const Leaf* lv, cons
   q.invP = 1.0 / P;
 }
 
+// Bracket state of one pivot search: v(L) < t <= v(H), the pivot in (L, H].
+// near = 2: probe the guess held in step; < 0: gallop down from H by step;
+// 1: gallop up from L; 0: search.
+struct PivotWork {
+  uint64_t L, H, step;
+  double vL, vH, t;
+  uint32_t j;
+  int8_t near;
+  uint8_t it;
+};
+
+// The start of pivot j of an item: trivial slots, then the analytic guess
+// inside the leaf whose F-range reaches the target (the leaf model is
+// linear, so x* = x0 + (t/P - b)/a lands within a few ord of the pivot).
+// Returns true when T[j] is written, else sets up the search in w: the
+// item's bracket with the guess as its first probe (near = 2).
+__device__ __forceinline__ bool pivot_start(uint32_t j, uint32_t B, const PivotPrep& q, const DModel& m,
+                                            const Leaf* lv, double Bg, uint64_t lo, uint64_t hi, int dt, uint64_t* T,
+                                            PivotWork& w) {
+  if (j >= B) {
+    T[j] = ~0ull;
+    return true;
+  }
+  if (j == 0) {
+    T[0] = lo;
+    return true;
+  }
+  if (j <= q.kmin) {
+    T[j] = lo;
+    return true;
+  }
+  if (j > q.kmax) {
+    T[j] = hi;
+    return true;
+  }
+  const double t = __dadd_rn((double)j, Bg);
+  const uint64_t L = lo, H = hi;
+  int near = 0;
+  // target F; it steers the leaf choice and the analytic guess only, the
+  // pivot itself is confirmed by exact evaluations
+  const double tF = __dmul_rn(t, q.invP);
+  uint32_t l0 = q.l0, l1 = q.l1;
+  while (l0 < l1) {  // first leaf whose clamp maximum reaches tF
+    uint32_t mid = (l0 + l1) >> 1;
+    if (lv[mid].hi < tF) l0 = mid + 1;
+    else l1 = mid;
+  }
+  const Leaf lf = lv[l0];
+  uint64_t guess = 0;
+  if (!(tF > lf.lo) && l0 > q.l0) {
+    // the target is at or below this leaf's floor: F jumps over it where
+    // the root starts routing to leaf l0, so that boundary is the pivot
+    const uint64_t u = root_boundary(m, l0, dt, lo, hi);
+    if (u > L && u <= H) guess = u;
+  } else if (lf.a > 0.0) {
+    const double xs = lf.x0 + (tF - lf.b) / lf.a;
+    if (xs >= q.xlo && xs <= q.xhi) {
+      uint64_t u;
+      if (dt) u = xs >= 18446744073709549568.0 ? ~0ull : (uint64_t)xs;
+      else u = ord_of((uint64_t)__double_as_longlong(xs), 0);
+      if (u > L && u < H) guess = u;
+    }
+  }
+  if (guess) {  // the first probe evaluates the guess, then the search gallops from it
+    near = 2;
+  }
+  w.L = L;
+  w.H = H;
+  w.step = guess ? guess : 1;
+  w.vL = q.vlo;
+  w.vH = q.vhi;
+  w.t = t;
+  w.j = j;
+  w.near = (int8_t)near;
+  w.it = 0;
+  return false;
+}
+
+// One probe of a pivot search.  The guess lands a few ord from the pivot
+// (the model's FP64 roundings make v flat over a few ord), so the search
+// first gallops away from it (steps 1, 2, 4, ...) to a tight bracket, then
+// bisects; wide brackets (no usable guess) take interpolation steps with a
+// bisection every fourth step.  Any bracketing search finds the same pivot.
+__device__ __forceinline__ void pivot_probe(const ItemEval& ev, PivotWork& w) {
+  if (w.near == 2) {  // the analytic guess, then a gallop away from it
+    const uint64_t c = w.step;
+    const double v = ev(c);
+    w.step = 1;
+    if (v >= w.t) {
+      w.H = c;
+      w.vH = v;
+      w.near = -1;
+    } else {
+      w.L = c;
+      w.vL = v;
+      w.near = 1;
+    }
+    return;
+  }
+  uint64_t c = 0;
+  if (w.near < 0) {
+    c = w.H - w.L > w.step ? w.H - w.step : w.L;
+    if (c == w.L) w.near = 0;
+  } else if (w.near > 0) {
+    c = w.H - w.L > w.step ? w.L + w.step : w.H;
+    if (c == w.H) w.near = 0;
+  }
+  if (w.near == 0) {
+    const uint64_t span = w.H - w.L;
+    if (span > 64 && (w.it & 3) != 3 && w.vH > w.vL) {
+      const float frac =
+          fminf(fmaxf((float)__dsub_rn(w.t, w.vL) / (float)__dsub_rn(w.vH, w.vL), 0.0f), 0.99999994f);
+      const uint64_t f32 = (uint64_t)(frac * 4294967296.0f);
+      uint64_t o = (span >> 32) * f32 + (((span & 0xFFFFFFFFull) * f32) >> 32);
+      if (o < 1) o = 1;
+      if (o > span - 1) o = span - 1;
+      c = w.L + o;
+    } else {
+      c = w.L + (span >> 1);
+    }
+    ++w.it;
+  }
+  const double v = ev(c);
+  if (v >= w.t) {
+    w.H = c;
+    w.vH = v;
+    if (w.near < 0) w.step <<= 1;
+    else w.near = 0;
+  } else {
+    w.L = c;
+    w.vL = v;
+    if (w.near > 0) w.step <<= 1;
+    else w.near = 0;
+  }
+}
+
+constexpr uint32_t kPivotTPB = 256;
+constexpr int kPivotRounds = 96;
+
 // One thread per pivot slot j of each listed item.  When a block lies inside
 // one item (nb_pad a multiple of the block size) the item's end values are
-// evaluated once per block, else by every thread.
-__global__ void k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist,
-                                 uint32_t nb_pad, const DModel* models, const Leaf* leaves,
-                                 uint64_t* __restrict__ pivots, RunParams rp) {
+// evaluated once per block, and the pivots whose guess did not confirm are
+// pooled: each round every pooled search takes one probe and the unfinished
+// ones are packed again, so the FP64 pipe (the bound here) runs full warps
+// instead of warps in which a few lanes gallop.  Other blocks search per
+// thread.
+__global__ void __launch_bounds__(kPivotTPB) k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
+                                                              uint32_t nlist, uint32_t nb_pad, const DModel* models,
+                                                              const Leaf* leaves, uint64_t* __restrict__ pivots,
+                                                              RunParams rp) {
   pdl_wait();
   __shared__ PivotPrep s_prep;
+  __shared__ PivotWork s_w[2][kPivotTPB];
+  __shared__ uint32_t s_n[2];
   const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const bool shared_prep = nb_pad % blockDim.x == 0;
-  if (shared_prep) {  // uniform: the whole block is in range and in one item
+  const bool pooled = nb_pad % blockDim.x == 0;
+  if (pooled) {  // uniform: the whole block is in range and in one item
     if (g >= (uint64_t)nlist * nb_pad) return;
     if (threadIdx.x == 0) {
       const uint32_t pi0 = list[(uint32_t)(g / nb_pad)];
       const Plan& p0 = plans[pi0];
       const DModel m0 = models[p0.model];
       pivot_prep(m0, leaves + m0.leaf_off, items[pi0], p0.P, p0.Bg, rp.B, rp.dt, s_prep);
+      s_n[0] = 0;
+      s_n[1] = 0;
     }
     __syncthreads();
   } else if (g >= (uint64_t)nlist * nb_pad) {
     return;
   }
-  uint32_t li = (uint32_t)(g / nb_pad), j = (uint32_t)(g % nb_pad);
-  uint32_t pi = list[li];
+  const uint32_t li = (uint32_t)(g / nb_pad), j = (uint32_t)(g % nb_pad);
+  const uint32_t pi = list[li];
   Plan& pl = plans[pi];
   const Item& it = items[pi];
   uint64_t* T = pivots + pl.tab_off;
-  uint32_t B = rp.B;
-  if (j >= B) {
-    T[j] = ~0ull;
-    return;
-  }
-  DModel m = models[pl.model];
+  const uint32_t B = rp.B;
+  const DModel m = models[pl.model];
   const Leaf* lv = leaves + m.leaf_off;
-  double P = pl.P, Bg = pl.Bg;
-  uint64_t lo = it.ord_lo, hi = it.ord_hi;
+  const double P = pl.P, Bg = pl.Bg;
   PivotPrep q;
-  if (shared_prep) q = s_prep;
+  if (pooled) q = s_prep;
   else pivot_prep(m, lv, it, P, Bg, B, rp.dt, q);
-  const double vlo = q.vlo, vhi = q.vhi;
-  const uint32_t kmin = q.kmin, kmax = q.kmax;
-  const ItemEval ev{m, lv, lv[q.l0], q.l0 == q.l1, P, rp.dt};
   if (j == 0) {
-    T[0] = lo;
-    pl.kmax = kmax;
+    pl.kmax = q.kmax;
     pl.nb = B;
     pl.nb_pad = nb_pad;
+  }
+  const ItemEval ev{m, lv, lv[q.l0], q.l0 == q.l1, P, rp.dt};
+  PivotWork w;
+  const bool done = pivot_start(j, B, q, m, lv, Bg, it.ord_lo, it.ord_hi, rp.dt, T, w);
+  if (!pooled) {
+    if (!done) {
+      for (int r = 0; r < kPivotRounds && w.H - w.L > 1 && w.near != 0; ++r) pivot_probe(ev, w);
+      T[j] = search_pivot(ev, w.L, w.H, w.t, w.vL, w.vH);
+    }
     return;
   }
-  if (j <= kmin) {
-    T[j] = lo;
-    return;
-  }
-  if (j > kmax) {
-    T[j] = hi;
-    return;
-  }
-  double t = __dadd_rn((double)j, Bg);
-  // Analytic guess inside the leaf whose F-range reaches the target: the
-  // leaf model is linear, so x* = x0 + (t/P - b)/a lands within a few ord
-  // of the pivot; two evaluations confirm it, otherwise the bracket the
-  // evaluations leave is searched.
-  uint64_t L = lo, H = hi;
-  double vL = vlo, vH = vhi;
-  int near = 0;  // -1: the pivot lies just below H; +1: just above L
-  {
-    const double xlo = q.xlo, xhi = q.xhi;
-    uint32_t l0 = q.l0, l1 = q.l1;
-    // target F; it steers the leaf choice and the analytic guess only, the
-    // pivot itself is confirmed by exact evaluations
-    double tF = __dmul_rn(t, q.invP);
-    while (l0 < l1) {  // first leaf whose clamp maximum reaches tF
-      uint32_t mid = (l0 + l1) >> 1;
-      if (lv[mid].hi < tF) l0 = mid + 1;
-      else l1 = mid;
+  if (!done) s_w[0][atomicAdd(&s_n[0], 1u)] = w;
+  __syncthreads();
+  int cur = 0;
+  for (int r = 0; r < kPivotRounds; ++r) {
+    const uint32_t n = s_n[cur];
+    if (n == 0) break;  // uniform
+    if (threadIdx.x < n) {
+      PivotWork x = s_w[cur][threadIdx.x];
+      pivot_probe(ev, x);
+      if (x.H - x.L > 1) s_w[cur ^ 1][atomicAdd(&s_n[cur ^ 1], 1u)] = x;
+      else T[x.j] = x.H;
     }
-    Leaf lf = lv[l0];
-    const uint32_t lstart = q.l0;
-    if (!(tF > lf.lo) && l0 > lstart) {
-      // the target is at or below this leaf's floor: F jumps over it where
-      // the root starts routing to leaf l0, so that boundary is the pivot
-      uint64_t u = root_boundary(m, l0, rp.dt, lo, hi);
-      if (u > L && u <= H) {
-        double vu = ev(u);
-        double v2 = ev(u - 1);
-        if (vu >= t && v2 < t) {
-          T[j] = u;
-          return;
-        }
-        if (vu >= t) {
-          H = u;
-          vH = vu;
-          near = -1;
-        } else {
-          L = u;
-          vL = vu;
-          near = 1;
-        }
-      }
-    } else if (lf.a > 0.0) {
-      double xs = lf.x0 + (tF - lf.b) / lf.a;
-      if (xs >= xlo && xs <= xhi) {
-        uint64_t u;
-        if (rp.dt) {
-          u = xs >= 18446744073709549568.0 ? ~0ull : (uint64_t)xs;
-        } else {
-          u = ord_of((uint64_t)__double_as_longlong(xs), 0);
-        }
-        if (u > L && u < H) {
-          double vu = ev(u);
-          if (vu >= t) {
-            H = u;
-            vH = vu;
-            double v2 = ev(u - 1);
-            if (v2 < t) {
-              T[j] = u;
-              return;
-            }
-            if (u - 1 > L) {
-              H = u - 1;
-              vH = v2;
-            }
-            near = -1;
-          } else {
-            L = u;
-            vL = vu;
-            double v2 = ev(u + 1);
-            if (v2 >= t) {
-              T[j] = u + 1;
-              return;
-            }
-            if (u + 1 < H) {
-              L = u + 1;
-              vL = v2;
-            }
-            near = 1;
-          }
-        }
-      }
-    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_n[cur] = 0;  // the next round's destination
+    cur ^= 1;
+    __syncthreads();
   }
-  // The guess lands a few ord from the pivot (the model's FP64 roundings
-  // make v flat over a few ord): gallop away from it to a tight bracket
-  // before the general search.
-  if (near < 0) {
-    for (uint64_t step = 1; step <= (1ull << 40) && H - L > 1; step <<= 1) {
-      const uint64_t c = H - L > step ? H - step : L;
-      if (c == L) break;
-      const double vc = ev(c);
-      if (vc >= t) {
-        H = c;
-        vH = vc;
-      } else {
-        L = c;
-        vL = vc;
-        break;
-      }
-    }
-  } else if (near > 0) {
-    for (uint64_t step = 1; step <= (1ull << 40) && H - L > 1; step <<= 1) {
-      const uint64_t c = H - L > step ? L + step : H;
-      if (c == H) break;
-      const double vc = ev(c);
-      if (vc < t) {
-        L = c;
-        vL = vc;
-      } else {
-        H = c;
-        vH = vc;
-        break;
-      }
-    }
+  // searches still open after the round limit finish on their own
+  if (threadIdx.x < s_n[cur]) {
+    const PivotWork& x = s_w[cur][threadIdx.x];
+    T[x.j] = search_pivot(ev, x.L, x.H, x.t, x.vL, x.vH);
   }
-  T[j] = search_pivot(ev, L, H, t, vL, vH);
 }
 
 // Classify the candidates' own samples with their learned pivots (sample
@@ -1298,7 +1343,9 @@ void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
                            cudaStream_t st) {
   if (!nlist) return;
   uint64_t n = (uint64_t)nlist * nb_pad;
-  pdl_launch(k_learned_pivots, grid_for(n, 128), 128, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots, rp);
+  const uint32_t tpb = nb_pad >= kPivotTPB ? kPivotTPB : 128;  // pooled blocks when tpb divides nb_pad
+  pdl_launch(k_learned_pivots, grid_for(n, tpb), tpb, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots,
+             rp);
 }
 
 void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,
