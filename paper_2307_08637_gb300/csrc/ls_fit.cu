@@ -166,7 +166,9 @@ __global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
 
 // ------------------------------------------------ segmented sample sort
 
-__global__ void __launch_bounds__(kTPB) k_sort_chunks(uint64_t* __restrict__ a, const uint64_t* __restrict__ off,
+constexpr int kSortTPB = 1024;  // threads of a chunk sort: two of the chunk's 2048 keys each
+
+__global__ void __launch_bounds__(kSortTPB) k_sort_chunks(uint64_t* __restrict__ a, const uint64_t* __restrict__ off,
                                                       const uint64_t* __restrict__ cpre, uint32_t nseg) {
   pdl_wait();
   __shared__ uint64_t sm[kSortChunk];
@@ -1291,7 +1293,7 @@ uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, co
                              uint32_t nseg, uint64_t total_chunks, uint64_t max_len, cudaStream_t st,
                              uint64_t* launches) {
   if (total_chunks == 0) return a;
-  pdl_launch(k_sort_chunks, (unsigned)total_chunks, kTPB, 0, st, a, d_off, d_chunk_prefix, nseg);
+  pdl_launch(k_sort_chunks, (unsigned)total_chunks, kSortTPB, 0, st, a, d_off, d_chunk_prefix, nseg);
   ++*launches;
   uint64_t* cur = a;
   uint64_t* oth = b;
