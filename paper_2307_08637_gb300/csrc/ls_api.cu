@@ -135,7 +135,7 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids,
+      o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids,
       o_vbuf;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
@@ -199,6 +199,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.o_stmp = take(l.stmp_elems * 8);
   l.o_stats = take(LS_MAX_LEVELS * sizeof(DevLevelStats));
   l.o_ctr = take(sizeof(LevelCounters));
+  l.o_rootplan = take(sizeof(Plan));
   l.o_agg = take(l.chunk_cap * l.nbc * 4);
   l.o_excl = take(l.chunk_cap * l.nbc * 8);
   l.seg_cap = l.chunk_cap / kSegChunks + kBatchItems + 8;
@@ -292,7 +293,8 @@ struct Sorter {
   uint64_t launches = 0;
   int32_t* seg_decision = nullptr;  // host, per segment
   uint32_t nseg = 0;
-  std::vector<Item> root_recorded;
+  bool root_copied = false;  // the root's plan waits in the workspace for the final readback
+  uint64_t root_n = 0;
 
   int alloc_model() {
     if (model_free.empty()) return -1;
@@ -630,20 +632,10 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   CK(cudaGetLastError());
 
   if (record_root && stats) {
-    Plan rp0;
-    CK(cudaMemcpyAsync(&rp0, d_plans, sizeof(Plan), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (its[0].n > 0 && !rp0.mixed) {
-      // homogeneity is checked before any model is built (Sec. 2.2): the
-      // sample the device drew speculatively is not part of the decision
-      stats->root_decision = LS_DEC_HOMOGENEOUS;
-    } else {
-      stats->root_decision = rp0.decision;
-      stats->root_nbuckets = rp0.nb;
-      stats->root_sample_size = rp0.S;
-      stats->root_dups = rp0.dups;
-      stats->root_imbalance_max = rp0.imb;
-    }
+    // keep the root's plan for the sort's final readback (no wait here)
+    CK(cudaMemcpyAsync(at<Plan>(s.ws, L.o_rootplan), d_plans, sizeof(Plan), cudaMemcpyDeviceToDevice, st));
+    s.root_copied = true;
+    s.root_n = its[0].n;
   }
   if (s.seg_decision && level0) {
     // per-segment root decisions (level-0 batches)
@@ -865,7 +857,22 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   // statistics
   std::vector<DevLevelStats> hs(LS_MAX_LEVELS);
   CK(cudaMemcpyAsync(hs.data(), d_stats, LS_MAX_LEVELS * sizeof(DevLevelStats), cudaMemcpyDeviceToHost, st));
+  Plan rp0;
+  if (s.root_copied) CK(cudaMemcpyAsync(&rp0, at<Plan>(ws, lay.o_rootplan), sizeof(Plan), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (s.root_copied) {
+    if (s.root_n > 0 && !rp0.mixed) {
+      // homogeneity is checked before any model is built (Sec. 2.2): the
+      // sample the device drew speculatively is not part of the decision
+      stats->root_decision = LS_DEC_HOMOGENEOUS;
+    } else {
+      stats->root_decision = rp0.decision;
+      stats->root_nbuckets = rp0.nb;
+      stats->root_sample_size = rp0.S;
+      stats->root_dups = rp0.dups;
+      stats->root_imbalance_max = rp0.imb;
+    }
+  }
   memcpy(stats->level, hs.data(), sizeof(stats->level));
   stats->level[0].base_items += root_base.base_items;
   stats->level[0].base_keys += root_base.base_keys;
