@@ -135,7 +135,7 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_fmodels, o_fleaves, o_ids,
+      o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_ids,
       o_vbuf;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
@@ -206,6 +206,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.o_segs = take(l.seg_cap * sizeof(ChunkSeg));
   l.o_multi = take((size_t)kBatchItems * sizeof(uint2));
   l.o_chunkctr = take(8);
+  l.o_chunkplan = take(l.chunk_cap * 4);
   l.misc_bytes = 16 * (kBatchItems + 8) * 8;
   l.o_misc = take(l.misc_bytes);
   l.total = off;
@@ -546,6 +547,18 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.nitems = nitems;
   pa.nchunks = tiles;
   if (tiles > L.chunk_cap) return LS_ENOMEM;
+  {
+    // the item of every chunk, for K1 and K3 (one load instead of a search
+    // over the plans per chunk)
+    std::vector<uint32_t> cp(tiles);
+    for (uint32_t i = 0; i < nitems; ++i) {
+      const uint64_t c1 = i + 1 < nitems ? plans[i + 1].chunk_begin : tiles;
+      for (uint64_t c = plans[i].chunk_begin; c < c1; ++c) cp[c] = i;
+    }
+    uint32_t* d_cp = at<uint32_t>(s.ws, L.o_chunkplan);
+    if (tiles) CK(cudaMemcpyAsync(d_cp, cp.data(), tiles * 4, cudaMemcpyHostToDevice, st));
+    pa.chunk_plan = d_cp;
+  }
   pa.agg = at<uint32_t>(s.ws, L.o_agg);
   pa.excl = at<unsigned long long>(s.ws, L.o_excl);
   pa.chunk_ctr = at<unsigned long long>(s.ws, L.o_chunkctr);

@@ -164,6 +164,7 @@ struct PassArgs {
   uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
   unsigned long long* excl;     // per chunk: keys of each bucket in the item's earlier chunks
   unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
+  const uint32_t* chunk_plan;   // per chunk: index of its item in the batch
   uint64_t chunk_keys;          // keys per chunk: a multiple of the tile, at most kChunkKeys
   void* valsA;                  // key-value sorts: payload of buffer A (caller's values) ...
   void* valsB;                  // ... and of the ping-pong buffer B

@@ -29,17 +29,6 @@ constexpr uint32_t kCopyPiece = 65536;
 
 inline unsigned grid_for(uint64_t n, int tpb = kTPB) { return (unsigned)((n + tpb - 1) / tpb); }
 
-// Plan index owning global chunk c (plans sorted by chunk_begin).
-__device__ __forceinline__ uint32_t find_plan(const Plan* __restrict__ plans, uint32_t n, uint64_t c) {
-  uint32_t lo = 0, hi = n;
-  while (hi - lo > 1) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (plans[mid].chunk_begin <= c) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // Warp-aggregated shared-memory increment; returns the key's rank among the
 // keys of its bucket counted so far in this block.  b == ~0u is "no key".
 __device__ __forceinline__ uint32_t agg_inc(uint32_t* h, uint32_t b) {
@@ -223,7 +212,7 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
   Cls c;
   bool nan = false;
   for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
-    const uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    const uint32_t pi = a.chunk_plan[ch];
     if (a.plans[pi].cls != CLS) continue;  // uniform across the block
     if (pi != cur) {
       __syncthreads();
@@ -338,7 +327,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
     __syncthreads();
     const uint64_t ch = s_chunk[par];
     if (ch >= a.nchunks) break;
-    const uint32_t pi = find_plan(a.plans, a.nitems, ch);
+    const uint32_t pi = a.chunk_plan[ch];
     const Plan& pl = a.plans[pi];
     if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
     const Item& it = a.items[pi];
