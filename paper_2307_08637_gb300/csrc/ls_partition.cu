@@ -53,7 +53,10 @@ struct Cls {
 };
 
 // Load item pi's classifier into shared memory (all threads).
-__device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, void* sAux) {
+// aux_model: the model whose FP32 leaves are in sAux (-1: none); items that
+// refine one global model share them, so they are copied once per block.
+__device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cls& c, uint64_t* sT, void* sAux,
+                         int32_t& aux_model) {
   const Plan& pl = a.plans[pi];
   c.cls = pl.cls;
   c.nb_pad = pl.nb_pad;
@@ -80,9 +83,12 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
     for (uint32_t j = threadIdx.x; j <= pl.dir_cells; j += blockDim.x) sD[j] = D[j];
   } else if (c.cls == CLS_GUESS) {
     c.fm = a.fmodels[pl.model];
-    const FLeaf* F = a.fleaves + c.fm.leaf_off;
-    FLeaf* sF = static_cast<FLeaf*>(sAux);
-    for (uint32_t j = threadIdx.x; j < c.fm.L; j += blockDim.x) sF[j] = F[j];
+    if (aux_model != pl.model) {
+      const FLeaf* F = a.fleaves + c.fm.leaf_off;
+      FLeaf* sF = static_cast<FLeaf*>(sAux);
+      for (uint32_t j = threadIdx.x; j < c.fm.L; j += blockDim.x) sF[j] = F[j];
+      aux_model = pl.model;
+    }
   }
 }
 
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
   uint32_t* sH = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(sD) + a.aux_bytes);
   for (uint32_t j = threadIdx.x; j < a.nb_pad_max; j += blockDim.x) sH[j] = 0;
   uint32_t cur = 0xFFFFFFFFu;
+  int32_t aux_model = -1;
   Cls c;
   bool nan = false;
   for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
     if (a.plans[pi].cls != CLS) continue;  // uniform across the block
     if (pi != cur) {
       __syncthreads();
-      load_cls(a, rp, pi, c, sT, sD);
+      load_cls(a, rp, pi, c, sT, sD, aux_model);
       cur = pi;
       __syncthreads();
     }
