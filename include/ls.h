@@ -25,8 +25,8 @@
  *   - Calls are asynchronous on the given stream unless stated otherwise.
  *     Errors that can be seen on the host (bad arguments, too-small
  *     workspace) are returned before anything is launched and leave the
- *     buffers untouched.  Errors found on the device (NaN key, a bounded
- *     wait that ran out) are recorded in a device status word; read it with
+ *     buffers untouched.  Errors found on the device (NaN key, a failed
+ *     consistency check) are recorded in a device status word; read it with
  *     ls_last_device_status().  After such an error the contents of d_keys
  *     are unspecified (still a permutation of some of the input's bytes).
  *   - No exceptions cross this boundary.  A context is not thread-safe: use
@@ -51,7 +51,7 @@ typedef enum {
   LS_EINVAL = 1,    /* bad argument (null pointer, bad dtype, fanout range) */
   LS_ENOMEM = 2,    /* workspace too small, or host/device allocation failed */
   LS_ENAN = 3,      /* a key is NaN (f64 only) */
-  LS_ETIMEOUT = 4,  /* a bounded device wait ran out */
+  LS_ETIMEOUT = 4,  /* a bounded device wait ran out (no kernel of this version waits) */
   LS_ECUDA = 5,     /* a CUDA runtime call failed */
   LS_ENOTIMPL = 6,  /* option not implemented */
   LS_EDEVICE = 7    /* device-side consistency check failed */
