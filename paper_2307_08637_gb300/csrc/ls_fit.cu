@@ -361,10 +361,29 @@ __global__ void k_fit_leaf_partials(FitArgs a, RunParams rp) {
     for (int q = 0; q < 4; ++q) a.lpart[q * a.lchunk_bound + g] = out[q];
 }
 
+// thread_tree_sum's tree over m <= 32 partials held one per lane (lane k:
+// p[k]): every level adds the pairs (2i, 2i+1) and carries an odd last
+// value, so the total is bit-identical.  Every lane returns it.
+__device__ __forceinline__ double warp_tree_sum32(double v, uint32_t m, unsigned lane) {
+  while (m > 1) {  // uniform
+    const uint32_t h = m >> 1;
+    const double x = __shfl_sync(0xFFFFFFFFu, v, (2 * lane) & 31);
+    const double y = __shfl_sync(0xFFFFFFFFu, v, (2 * lane + 1) & 31);
+    const double z = __shfl_sync(0xFFFFFFFFu, v, (m - 1) & 31);
+    if (lane < h) v = __dadd_rn(x, y);
+    else if ((m & 1) && lane == h) v = z;
+    m = h + (m & 1);
+  }
+  return __shfl_sync(0xFFFFFFFFu, v, 0);
+}
+
+// One warp per (candidate, leaf): the leaf's four sums (a warp tree over its
+// chunk partials), its least-squares line and raw clamps.
 __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_cnt) {
   pdl_wait();
-  uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (g >= (uint64_t)a.ncand * a.L) return;
+  const uint64_t g = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  if (g >= (uint64_t)a.ncand * a.L) return;  // uniform across the warp
   uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
   const Plan& pl = a.plans[a.cand[c]];
   const uint64_t* s = a.samp + pl.sample_off;
@@ -373,28 +392,39 @@ __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict_
   uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
   uint64_t st = ls[i] < en ? ls[i] : en;
   uint64_t cnt = en - st;
-  DModel m = a.models[pl.model];
+  const uint32_t leaf_off = a.models[pl.model].leaf_off;
   Leaf l;
   if (cnt == 0) {
-    l.x0 = m.xmin;
+    l.x0 = a.models[pl.model].xmin;
     l.a = 0.0;
     l.b = 0.0;
     l.lo = 0.0;
     l.hi = 0.0;
   } else {
-    uint64_t p0 = a.lchunk_prefix[g];
-    uint64_t nch = a.lchunk_prefix[g + 1] - p0;
+    const uint64_t p0 = a.lchunk_prefix[g];
+    const uint64_t nch = a.lchunk_prefix[g + 1] - p0;
     double sm[4];
-    for (int q = 0; q < 4; ++q) sm[q] = thread_tree_sum(a.lpart + q * a.lchunk_bound + p0, nch);
-    double x_first = ord_value(s[st], rp.dt);
-    double x_last = ord_value(s[en - 1], rp.dt);
-    l.x0 = x_first;
-    linfit(__ull2double_rn(cnt), sm[0], sm[1], sm[2], sm[3], &l.a, &l.b);
-    l.lo = leaf_eval(l, x_first);  // raw min of the leaf (slope >= 0)
-    l.hi = leaf_eval(l, x_last);   // raw max
+    if (nch <= 32) {
+      for (int q = 0; q < 4; ++q) {
+        const double v = lane < nch ? a.lpart[q * a.lchunk_bound + p0 + lane] : 0.0;
+        sm[q] = warp_tree_sum32(v, (uint32_t)nch, lane);
+      }
+    } else if (lane == 0) {
+      for (int q = 0; q < 4; ++q) sm[q] = thread_tree_sum(a.lpart + q * a.lchunk_bound + p0, nch);
+    }
+    if (lane == 0) {
+      double x_first = ord_value(s[st], rp.dt);
+      double x_last = ord_value(s[en - 1], rp.dt);
+      l.x0 = x_first;
+      linfit(__ull2double_rn(cnt), sm[0], sm[1], sm[2], sm[3], &l.a, &l.b);
+      l.lo = leaf_eval(l, x_first);  // raw min of the leaf (slope >= 0)
+      l.hi = leaf_eval(l, x_last);   // raw max
+    }
   }
-  a.leaves[m.leaf_off + i] = l;
-  leaf_cnt[m.leaf_off + i] = (uint32_t)cnt;
+  if (lane == 0) {
+    a.leaves[leaf_off + i] = l;
+    leaf_cnt[leaf_off + i] = (uint32_t)cnt;
+  }
 }
 
 // Monotone RMI (Sec. 4): hi_i = max(0, max over non-empty j <= i of raw
@@ -1328,7 +1358,7 @@ void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t
   pdl_launch(k_fit_leaf_chunk_count, grid_for(tot + 1), kTPB, 0, st, a);
   launch_scan_exclusive_u64(a.lchunk_cnt, a.lchunk_prefix, tot, a.scan_tmp, a.scan_tmp_elems, st);
   pdl_launch(k_fit_leaf_partials, grid_for(a.lchunk_bound * 32, 128), 128, 0, st, a, rp);
-  pdl_launch(k_fit_leaf_finish, grid_for(tot, 128), 128, 0, st, a, rp, a.leaf_cnt);
+  pdl_launch(k_fit_leaf_finish, grid_for(tot * 32, 128), 128, 0, st, a, rp, a.leaf_cnt);
   pdl_launch(k_fit_monotone, a.ncand, 1024, 0, st, a, a.leaf_cnt);
   pdl_launch(k_fmodel_fit, grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st, a);
   *launches += 13;
