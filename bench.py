@@ -65,6 +65,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(seed, rank):
+    """Seed of one rank's arrays: every rank sorts its own inputs (weak scaling)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's value, agreed by all ranks (all-reduce MAX); x on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_keys_per_s(world, keys_per_step, step_ms):
+    """Whole-job throughput: every rank's keys over the slowest rank's step time."""
+    return world * keys_per_step / (step_ms / 1e3)
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -217,7 +239,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = lsg.Context(dev)
     dists = tuple(d for d in args.dists.split(",") if d)
-    inputs = gen_inputs(n, args.seed + 1000 * rank, dists)
+    inputs = gen_inputs(n, rank_seed(args.seed, rank), dists)
     pristine = [torch.from_numpy(x).to(f"cuda:{dev}") for _, x in inputs]
     work = [torch.empty_like(t) for t in pristine]
     p_learned = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, basecase_threshold=BASECASE_T)
@@ -247,13 +269,9 @@ def run_ours(args):
     sord = last.view(torch.int64)
     sord = sord ^ ((sord >> 63) & 0x7FFFFFFFFFFFFFFF)
     assert bool((sord[1:] >= sord[:-1]).all()), "bench output not sorted"
-    step_ms = sum(ms_learned) / len(ms_learned)
-    if world > 1:
-        t = torch.tensor([step_ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(sum(ms_learned) / len(ms_learned), world, f"cuda:{dev}")
     keys_per_step = n * len(inputs)
-    value = world * keys_per_step / (step_ms / 1e3)
+    value = job_keys_per_s(world, keys_per_step, step_ms)
 
     # per-pass device time (all timed learned sorts)
     passes = {}
@@ -295,14 +313,14 @@ def run_ours(args):
             ms, sts = time_sorts(lsg, ctx, work, pristine, p_split, torch, stream)
             ms_s.append(sum(ms))
             sts_s += sts
-        s_ms = sum(ms_s) / len(ms_s)
+        s_ms = max_over_ranks(sum(ms_s) / len(ms_s), world, f"cuda:{dev}")
         ps = {}
         for st in sts_s:
             for k, v in st.passes().items():
                 a = ps.setdefault(k, {"ms": 0.0, "keys": 0})
                 a["ms"] += v["ms"]
                 a["keys"] += v["keys"]
-        split = {"value": world * keys_per_step / (s_ms / 1e3), "unit": "keys/s", "ms_per_step": s_ms,
+        split = {"value": job_keys_per_s(world, keys_per_step, s_ms), "unit": "keys/s", "ms_per_step": s_ms,
                  "learned_speedup": s_ms / step_ms,
                  "scatter_gbs": SCATTER_BYTES_PER_KEY * ps["scatter"]["keys"] / (ps["scatter"]["ms"] / 1e3) / 1e9,
                  "classify_gbs": CLASSIFY_BYTES_PER_KEY * ps["classify"]["keys"] / (ps["classify"]["ms"] / 1e3) / 1e9,
@@ -331,9 +349,10 @@ def run_ours(args):
             assert bool(np.all(h[1:] >= h[:-1])), "end-to-end output not sorted"
             assert hb.sum(dtype=np.uint64) == sb.sum(dtype=np.uint64)
             assert np.bitwise_xor.reduce(hb) == np.bitwise_xor.reduce(sb)
-        e2e = {"value": world * keys_per_step / (sum(tt) / len(tt)), "unit": "keys/s",
+        e2e_ms = max_over_ranks(1e3 * sum(tt) / len(tt), world, f"cuda:{dev}")
+        e2e = {"value": job_keys_per_s(world, keys_per_step, e2e_ms), "unit": "keys/s",
                "h2d_bytes_per_step": 8 * keys_per_step, "d2h_bytes_per_step": 8 * keys_per_step,
-               "ms_per_step": 1e3 * sum(tt) / len(tt),
+               "ms_per_step": e2e_ms,
                "api": "ls_sort_host_batch (six page-locked host arrays, copies pipelined with the sorts)"}
 
     cpu = None
