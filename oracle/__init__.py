@@ -158,6 +158,8 @@ def lib():
             L.lsref_ord.argtypes = [C.c_uint64, C.c_int]
             L.lsref_unord.restype = C.c_uint64
             L.lsref_unord.argtypes = [C.c_uint64, C.c_int]
+            L.lsref_key_value.restype = C.c_double
+            L.lsref_key_value.argtypes = [C.c_uint64, C.c_int]
             L.lsref_splitmix64.restype = C.c_uint64
             L.lsref_splitmix64.argtypes = [C.c_uint64]
             L.lsref_seed_item.restype = C.c_uint64
@@ -231,6 +233,12 @@ def params(**kw) -> Params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def key_value(bits: int, dtype: int) -> float:
+    """The value the model reads for one key (Sec. 2.1's x): the double
+    itself, or a u64 converted to the nearest double (ties to even)."""
+    return float(lib().lsref_key_value(bits, dtype))
 
 
 def ord_keys(keys: np.ndarray) -> np.ndarray:

@@ -438,3 +438,31 @@ def test_trained_rmi_gains_over_untrained_map():
         lin = np.clip(np.floor((np.clip(x, lo, hi) - lo) / (hi - lo) * B), 0, B - 1).astype(np.int64)
         h_lin = np.bincount(lin, minlength=B)
         assert h_rmi.var() * 3 < h_lin.var(), dist
+
+
+def test_u64_key_value_is_the_nearest_double():
+    """The model reads a u64 key as the nearest double, ties to even:
+    Python's int-to-float conversion is correctly rounded, an independent
+    definition."""
+    rng = np.random.default_rng(3)
+    vals = [0, 1, 2**53 - 1, 2**53, 2**53 + 1, 2**53 + 2, 2**53 + 3, 2**54 + 2, 2**54 + 6,
+            2**63 - 1, 2**63, 2**63 + 1024, 2**63 + 1025, 2**64 - 1, 2**64 - 2048, 2**64 - 1025]
+    vals += [int(v) for v in rng.integers(0, 2**63, 200, dtype=np.uint64)]
+    vals += [int(v) | (1 << 63) for v in rng.integers(0, 2**63, 200, dtype=np.uint64)]
+    for v in vals:
+        assert oracle.key_value(v, oracle.U64) == float(v), v
+
+
+def test_depth_limit_sorts_the_rest_and_counts_it():
+    """Past max_depth a bucket is sorted directly (reading 18): the output
+    is still the sorted input, and the trace counts those keys as fallback
+    keys, one level below the limit."""
+    x = datagen.generate("mix_gauss", 200_000, 5)
+    for depth in (1, 2):
+        p = oracle.params(max_depth=depth, basecase_threshold=16, fanout=64, min_learned_n=10_000)
+        out, rc, tr, _, _ = oracle.sort(x, p)
+        assert rc == 0
+        assert_sorted_equal(out, x)
+        lv = tr.levels()
+        assert sum(l["fallback_keys"] for l in lv) > 0
+        assert all(l["items"] == 0 for l in lv[depth + 1:])
