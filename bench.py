@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -118,7 +119,9 @@ class Clocks:
     def __init__(self, dev: int):
         self.dev = dev
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{dev}.csv")
+        # the raw samples: LS_CLOCKS_DIR if set (to keep them), else a temporary directory
+        out_dir = os.environ.get("LS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_gpu{dev}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
