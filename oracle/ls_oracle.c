@@ -680,16 +680,6 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
     RELEASE_INHERITED();
     return 0;
   }
-  /* A bucket that refines the global model past the FP64 resolution of
-   * B^(k+1) is sorted directly: under REFINE_GLOBAL no bucket below the
-   * root draws a new sample (LearnedSort 2.0 trains once, Sec. 2.2). */
-  if (it.kind == KIND_REFINE && pow_exact(p->fanout, it.mk + 1) > REFINE_LIMIT) {
-    heapsort_u64(a, n);
-    ls->fallback_items += 1;
-    ls->fallback_keys += n;
-    RELEASE_INHERITED();
-    return 0;
-  }
   /* Homogeneity check (Sec. 2.2): an all-equal range is already sorted. */
   uint64_t mn = a[0], mx = a[0];
   for (uint64_t i = 1; i < n; ++i) {
@@ -710,12 +700,15 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
   uint32_t mk = 0;
   uint64_t mg = 0;
   int fresh = 1;
-  if (it.kind == KIND_REFINE) { /* B^(mk+1) <= 2^50, checked above */
-    fresh = 0;
-    model = inherited;
-    mk = it.mk;
-    mg = it.mg;
-    decision = LSREF_DEC_LEARNED;
+  if (it.kind == KIND_REFINE) {
+    double P = pow_exact(B, it.mk + 1);
+    if (P <= REFINE_LIMIT) {
+      fresh = 0;
+      model = inherited;
+      mk = it.mk;
+      mg = it.mg;
+      decision = LSREF_DEC_LEARNED;
+    }
   }
   if (fresh) {
     /* BuildPartitionModel (Alg. 5): sample, sort, duplicate test, model. */
@@ -851,12 +844,8 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
     ch.segment = it.segment;
     ch.level = it.level + 1;
     ch.gidx = it.gidx * nb + bb;
-    if (sz == n && !refine_children) {
-      /* no-progress guard: the child is redone with equality buckets.  A
-       * child of a REFINE_GLOBAL model keeps refining the same model
-       * instead (one level finer each time, ended by the FP64 refinement
-       * limit or the depth limit), so no bucket below the root resamples. */
-      ch.kind = KIND_FORCE_SPLITTER;
+    if (sz == n) {
+      ch.kind = KIND_FORCE_SPLITTER; /* no-progress guard */
     } else if (refine_children) {
       ch.kind = KIND_REFINE;
       ch.model = model;

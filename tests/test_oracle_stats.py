@@ -12,9 +12,7 @@ directly from the method's steps recomputes them on small inputs:
   (REFINE_GLOBAL) or a new sample (RETRAIN);
 * Sec. 2.4: splitter tree, equality buckets (final, never recursed), the
   no-progress guard (a child holding all of its parent's keys is redone with
-  equality buckets; under REFINE_GLOBAL it keeps refining the same model,
-  and a bucket past the FP64 refinement limit is sorted directly, so no
-  bucket below the root resamples, as in LearnedSort 2.0).
+  equality buckets).
 
 The recursion uses the oracle only for the RMI fit and its bucket function,
 which have their own pins (closed form, numpy.polyfit); sampling, splitter
@@ -116,14 +114,6 @@ class Model:
             self.terminal += n
             keys[lo:hi] = x[np.argsort(np_ord(x), kind="stable")]
             return
-        if kind == "refine" and p.fanout ** (mk + 1) > REFINE_LIMIT:
-            # past the FP64 refinement limit a REFINE_GLOBAL bucket is sorted
-            # directly: no bucket below the root draws a new sample
-            L["fallback_items"] += 1
-            L["fallback_keys"] += n
-            self.terminal += n
-            keys[lo:hi] = x[np.argsort(np_ord(x), kind="stable")]
-            return
         u = np_ord(x)
         if u.min() == u.max():
             L["homogeneous"] += 1
@@ -131,7 +121,7 @@ class Model:
             return
         B = p.fanout
         fresh = True
-        if kind == "refine":
+        if kind == "refine" and B ** (mk + 1) <= REFINE_LIMIT:
             fresh = False
             decision = "learned"
         if fresh:
@@ -208,10 +198,9 @@ class Model:
                 self.terminal += sz
                 continue
             clo = lo + int(start[b])
-            refine = decision == "learned" and p.recurse_model == oracle.RECURSE_REFINE_GLOBAL
-            if sz == n and not refine:
+            if sz == n:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "force_splitter", None, 0, 0)
-            elif refine:
+            elif decision == "learned" and p.recurse_model == oracle.RECURSE_REFINE_GLOBAL:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "refine", model, mk + 1, mg * B + b)
             else:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "fresh", None, 0, 0)
@@ -299,27 +288,3 @@ def test_level_statistics_of_a_planted_example():
     assert lv[1]["items"] == 1 and lv[1]["keys"] == 3
     assert lv[1]["base_items"] == 2 and lv[1]["base_keys"] == 4
     assert Model(p).run(x)[1] == lv
-
-
-def test_refine_chain_never_resamples():
-    """Under REFINE_GLOBAL a bucket the model cannot split keeps refining the
-    same model, one level finer each time, and past the FP64 limit B^(k+1) >
-    2^50 it is sorted directly: two distinct keys far beyond the sample range
-    share F (the input is clamped to the sample's range), so their bucket
-    makes no progress at levels 0..4 and is finished by the direct sort at
-    level 5 (1000^6 > 2^50)."""
-    rng = np.random.default_rng(1)
-    x = np.concatenate([rng.normal(size=3000), np.full(50, 1e300), np.full(50, np.nextafter(1e300, np.inf))])
-    rng.shuffle(x)
-    p = oracle.params(fanout=1000, basecase_threshold=4, partitioner=oracle.PART_LEARNED, sample_rate=0.1,
-                      min_sample=16)
-    out, rc, tr, _, _ = oracle.sort(x, p)
-    assert rc == 0
-    lv = tr.levels()
-    assert len(lv) == 6 and all(l["noprogress"] >= 1 for l in lv[1:5])
-    assert lv[5]["fallback_items"] >= 1 and lv[5]["fallback_keys"] >= 100 and lv[5]["items"] == 0
-    assert all(l["splitter"] == 0 and l["splitter_eq"] == 0 for l in lv)  # no sample below the root
-    m = Model(p)
-    ref, ref_levels = m.run(x)
-    assert ref_levels == lv and m.terminal == x.size
-    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
