@@ -193,8 +193,9 @@ ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dty
                             size_t* bytes);
 
 /* Sort d_keys[0..n) ascending by ord (the sorting problem of Sec. 1-2).
- * In place from the caller's view; the library ping-pongs through
- * d_workspace (>= ls_workspace_size bytes, 256-byte aligned).  Stream
+ * d_keys must be 8-byte aligned (LS_EINVAL otherwise).  In place from the
+ * caller's view; the library ping-pongs through d_workspace
+ * (>= ls_workspace_size bytes, 256-byte aligned).  Stream
  * ordered; the call synchronises `stream` between recursion levels, so it
  * returns after the sort is complete.  out_stats (nullable) receives the
  * decisions and per-level statistics. */
@@ -238,6 +239,16 @@ ls_status ls_sort_host(ls_ctx* ctx, void* h_keys, uint64_t n, ls_dtype dtype, co
 ls_status ls_sort_host_batch(ls_ctx* ctx, void* const* h_keys, const uint64_t* n, uint32_t count, ls_dtype dtype,
                              const ls_params* p, ls_stats* out_stats);
 
+/* Sample(A) of Alg. 2-5 (Sec. 2.2: the model is trained on a random
+ * sample): writes min(S, n) keys of d_keys[0..n) to d_out, drawn with
+ * replacement, key j from position floor(u_j * n / 2^64) where u_j is the
+ * SplitMix64 output at state seed + (j+1) * 0x9E3779B97F4A7C15; S >= n
+ * copies the keys in order.  Key bits are copied unchanged (dtype only
+ * checks the type).  Both pointers 8-byte aligned, device memory owned by
+ * the caller.  Stream ordered and asynchronous; allocates nothing. */
+ls_status ls_sample(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, uint64_t S, uint64_t seed,
+                    void* d_out, ls_stream_t stream);
+
 /* Train the root model exactly as ls_sort would (sample with the root's
  * seed, sort the sample, fit; Sec. 2.2 / Alg. 5) and copy it to *out_model.
  * Also returns the root decision inputs in *out_stats (nullable).
@@ -272,7 +283,9 @@ ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_s
  * owns the device memory, or a path that must not risk cudaMalloc's
  * device-wide synchronisation.  Same arguments and results as ls_classify,
  * without a context: it classifies on the current device and stream.
- * Scratch is one fixed 256 KB device array inside the library (present on
+ * Every mode is accepted (k >= 50 is rejected with LS_EINVAL, as by
+ * ls_classify).  Scratch is one fixed 288 KB device array inside the library
+ * (enough for every mode at every fanout up to LS_MAX_FANOUT; present on
  * every GPU that loads it, until the process exits); it holds the model and
  * pivot tables of the last call, is fully rewritten by each call, and is
  * shared by all calls: calls that overlap on the GPU race, so serialise them.
@@ -328,6 +341,13 @@ ls_status ls_model_import(ls_model* m, const void* buf, size_t bytes);
 
 /* Human-readable name of a status code (static string). */
 const char* ls_status_string(ls_status s);
+
+/* Description of the last LS_ECUDA / LS_ENOMEM failure raised on the calling
+ * host thread ("" if none): the CUDA error and where it was seen, or which
+ * workspace list ran out.  The library never prints; this is its only
+ * diagnostic channel.  The string is owned by the library and valid until
+ * the thread's next failing call. */
+const char* ls_last_error_detail(void);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,6 @@
 // race on the array: serialise them.  The array occupies kStaticScratchBytes
 // on every GPU that loads the library, until the process exits.
 #include <cstddef>
-#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -25,7 +24,9 @@ using namespace lsg;
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = 256 * 1024;
+// Enough for every mode at every fanout up to LS_MAX_FANOUT (the largest
+// layout, GUESS at 4096 leaves, needs about 274 KB).
+constexpr size_t kStaticScratchBytes = 288 * 1024;
 constexpr uint32_t kStaticDirBits = 13;
 constexpr int kMaxDevices = 64;
 
@@ -53,7 +54,7 @@ cudaError_t scratch_address(int dev, void** out) {
 
 // Scratch layout for fanout B (all offsets 256-aligned).
 struct StaticLayout {
-  size_t model, leaves, item, plan, pivots, dir, list, total;
+  size_t model, leaves, item, plan, pivots, dir, list, fmodel, fleaves, slot, total;
 };
 
 StaticLayout static_layout(uint32_t B, uint32_t nb_pad, uint32_t cells) {
@@ -73,6 +74,12 @@ StaticLayout static_layout(uint32_t B, uint32_t nb_pad, uint32_t cells) {
   off = up256(off + (size_t)(cells + 1) * 2);
   l.list = off;
   off = up256(off + 4);
+  l.fmodel = off;
+  off = up256(off + sizeof(FModel));
+  l.fleaves = off;
+  off = up256(off + (size_t)B * sizeof(FLeaf));
+  l.slot = off;
+  off = up256(off + 4);
   l.total = off;
   return l;
 }
@@ -83,11 +90,15 @@ extern "C" ls_status ls_classify_static(const ls_model* model, const void* d_key
                                         uint32_t k, uint64_t g, int32_t mode, uint32_t* d_ids, uint64_t* d_hist,
                                         ls_stream_t stream) {
   if (!model || (!d_keys && n) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
-  if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < 0 || mode > 3) return LS_EINVAL;
+  if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < LS_CLASSIFY_AUTO || mode > LS_CLASSIFY_GUESS)
+    return LS_EINVAL;
+  // B >= 2, so B^(k+1) > 2^50 for every k >= 50: reject those before the
+  // power loop (k + 1 would also wrap at k = UINT32_MAX).
+  if (k >= 50) return LS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t B = model->L;
   double P = 1.0;
-  for (uint32_t i = 0; i < k + 1; ++i) P = P * (double)B;
+  for (uint32_t i = 0; i <= k && P <= kRefineLimit; ++i) P = P * (double)B;
   if (P > kRefineLimit) return LS_EINVAL;
   const double Bg = (double)((uint64_t)B * g);
   uint32_t nbp = 1;
@@ -95,8 +106,8 @@ extern "C" ls_status ls_classify_static(const ls_model* model, const void* d_key
   const uint32_t cells = 1u << kStaticDirBits;
   const StaticLayout lay = static_layout(B, nbp, cells);
   if (lay.total > kStaticScratchBytes) {
-    fprintf(stderr, "ls_classify_static: fanout %u needs %zu bytes of scratch, the static array holds %zu\n", B,
-            lay.total, kStaticScratchBytes);
+    set_error_detail("ls_classify_static: fanout %u needs %zu bytes of scratch, the static array holds %zu", B,
+                     lay.total, kStaticScratchBytes);
     return LS_ENOMEM;
   }
   int dev = 0;
@@ -111,6 +122,9 @@ extern "C" ls_status ls_classify_static(const ls_model* model, const void* d_key
   uint64_t* d_piv = reinterpret_cast<uint64_t*>(b + lay.pivots);
   uint16_t* d_dir = reinterpret_cast<uint16_t*>(b + lay.dir);
   uint32_t* d_list = reinterpret_cast<uint32_t*>(b + lay.list);
+  FModel* d_fm = reinterpret_cast<FModel*>(b + lay.fmodel);
+  FLeaf* d_fl = reinterpret_cast<FLeaf*>(b + lay.fleaves);
+  int32_t* d_slot = reinterpret_cast<int32_t*>(b + lay.slot);
 
   // Host images of everything the kernels read; every field is written on
   // every call, so nothing from an earlier call is ever used.
@@ -160,19 +174,21 @@ extern "C" ls_status ls_classify_static(const ls_model* model, const void* d_key
     pl.nb = B;
     pl.nb_pad = nbp;
     pl.decision = LS_DEC_LEARNED;
-    pl.cls = (mode == LS_CLASSIFY_TREE) ? CLS_TREE : CLS_DIR;
+    pl.cls = (mode == LS_CLASSIFY_TREE) ? CLS_TREE : (mode == LS_CLASSIFY_GUESS) ? CLS_GUESS : CLS_DIR;
     uint32_t zero = 0;
     if (cudaMemcpyAsync(d_it, &it, sizeof it, cudaMemcpyHostToDevice, st) != cudaSuccess) return LS_ECUDA;
     if (cudaMemcpyAsync(d_pl, &pl, sizeof pl, cudaMemcpyHostToDevice, st) != cudaSuccess) return LS_ECUDA;
     if (cudaMemcpyAsync(d_list, &zero, 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return LS_ECUDA;
+    if (cudaMemcpyAsync(d_slot, &zero, 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return LS_ECUDA;
     RunParams rp;
     memset(&rp, 0, sizeof rp);
     rp.B = B;
     rp.dt = dtype;
     launch_learned_pivots(d_pl, d_it, d_list, 1, nbp, d_m, d_l, d_piv, rp, st);
     launch_dir_build(d_pl, 1, cells, d_piv, d_dir, st);
+    if (mode == LS_CLASSIFY_GUESS) launch_fmodel(d_m, d_l, d_slot, 1, B, d_fm, d_fl, st);
     launch_table_classify(d_pl, d_piv, d_dir, static_cast<const uint64_t*>(d_keys), n, dtype, d_ids,
-                          reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st);
+                          reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st, d_fm, d_fl);
   }
   if (cudaGetLastError() != cudaSuccess) return LS_ECUDA;
   // the host images above live on this stack frame: finish the copies
