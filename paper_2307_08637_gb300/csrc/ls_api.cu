@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -26,6 +27,17 @@
 #include "ls_kernels.h"
 
 using namespace lsg;
+
+namespace {
+thread_local char g_error_detail[256] = "";
+}  // namespace
+
+void lsg::set_error_detail(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_error_detail, sizeof g_error_detail, fmt, ap);
+  va_end(ap);
+}
 
 namespace {
 
@@ -41,13 +53,13 @@ inline uint32_t pow2ceil(uint32_t x) {
   return p;
 }
 
-#define CK(call)                                                                      \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) {                                                          \
-      fprintf(stderr, "ls: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
-      return LS_ECUDA;                                                                \
-    }                                                                                 \
+#define CK(call)                                                        \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      lsg::set_error_detail("CUDA error %s at %s:%d", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return LS_ECUDA;                                                  \
+    }                                                                   \
   } while (0)
 
 ls_status validate_params(const ls_params* p) {
@@ -98,9 +110,13 @@ uint64_t sample_size(uint64_t n, const ls_params* p) {
   return S;
 }
 
+// B^e in FP64, exact while it stays below 2^53.  The loop stops once the
+// product passes the refinement limit (B >= 2, so it only grows): callers
+// compare the result with that limit, and a huge e costs no more than ~50
+// multiplications.
 double pow_exact(uint32_t B, uint32_t e) {
   double P = 1.0;
-  for (uint32_t i = 0; i < e; ++i) P = P * (double)B;
+  for (uint32_t i = 0; i < e && P <= kRefineLimit; ++i) P = P * (double)B;
   return P;
 }
 
@@ -131,12 +147,12 @@ struct Layout {
   uint64_t n = 0;
   uint32_t L = 0, nbc = 0, cells = 0;
   uint64_t icap = 0, scap = 0, mcap = 0, base_cap = 0, large_cap = 0, copy_cap = 0, fb_cap = 0;
-  uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0, seg_cap = 0;
+  uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0, seg_cap = 0, brun_cap = 0;
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
       o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_ids,
-      o_vbuf;
+      o_vbuf, o_bruns;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
@@ -205,7 +221,11 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.seg_cap = l.chunk_cap / kSegChunks + kBatchItems + 8;
   l.o_segs = take(l.seg_cap * sizeof(ChunkSeg));
   l.o_multi = take((size_t)kBatchItems * sizeof(uint2));
-  l.o_chunkctr = take(8);
+  l.o_chunkctr = take(16);
+  // buffered-scatter runs: at most one per item plus the equal shares
+  // (two per resident block; 4096 covers any part this library targets)
+  l.brun_cap = kBatchItems + 4096;
+  l.o_bruns = take(l.brun_cap * sizeof(BufRun));
   l.o_chunkplan = take(l.chunk_cap * 4);
   l.misc_bytes = 16 * (kBatchItems + 8) * 8;
   l.o_misc = take(l.misc_bytes);
@@ -518,8 +538,9 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   // fresh items are decided on the device, so read their plans back
   uint32_t nbp_max = 2, cls_mask = 0;
   bool any_dir = false, any_guess = false;
+  std::vector<Plan> hp;
   if (!fresh.empty()) {
-    std::vector<Plan> hp(nitems);
+    hp.resize(nitems);
     CK(cudaMemcpyAsync(hp.data(), d_plans, nitems * sizeof(Plan), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (const Plan& q : hp) {
@@ -585,7 +606,38 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.vbytes = s.vb;
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
   pa.chunk_keys = ck;
-  CK(cudaMemsetAsync(pa.chunk_ctr, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(pa.chunk_ctr, 0, 2 * sizeof(unsigned long long), st));
+  // Runs of the buffered scatter for every item it may take (whether it
+  // does is decided by K2 on the device): each candidate's keys split into
+  // runs of about an equal share of two runs per resident block (whole items
+  // when smaller), so that blocks get the same work and each bucket's region
+  // of a run is long.  The stable K3 is launched as well and skips them.
+  const std::vector<Plan>& dplans = fresh.empty() ? plans : hp;  // decisions as the device made them
+  std::vector<BufRun> bruns;
+  {
+    uint64_t bkeys = 0;
+    for (uint32_t i = 0; i < nitems; ++i)
+      if (buffered_scatter_candidate(dplans[i], s.vb)) bkeys += its[i].n;
+    const uint64_t slots = 2ull * buffered_scatter_slots();
+    const uint64_t target = std::max<uint64_t>(kTileKeys, (bkeys + slots - 1) / slots);
+    for (uint32_t i = 0; i < nitems; ++i) {
+      const uint64_t n = its[i].n;
+      if (!buffered_scatter_candidate(dplans[i], s.vb)) continue;
+      const uint64_t nr = (n + target - 1) / target;
+      for (uint64_t r = 0; r < nr; ++r) {
+        BufRun br;
+        memset(&br, 0, sizeof br);
+        br.off = n * r / nr;
+        br.len = n * (r + 1) / nr - br.off;
+        br.plan = i;
+        if (br.len) bruns.push_back(br);
+      }
+    }
+    if (bruns.size() > L.brun_cap) return LS_ENOMEM;
+    if (!bruns.empty())
+      CK(cudaMemcpyAsync(at<BufRun>(s.ws, L.o_bruns), bruns.data(), bruns.size() * sizeof(BufRun),
+                         cudaMemcpyHostToDevice, st));
+  }
   s.timer.begin(LS_PASS_CLASSIFY, batch_keys);
   s.launches += launch_classify_hist(pa, s.rp, st);
   s.timer.end();
@@ -640,8 +692,9 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   s.timer.end();
   s.timer.begin(LS_PASS_SCATTER, batch_keys);
   launch_scatter(pa, s.rp, st);
+  launch_scatter_buffered(pa, s.rp, at<BufRun>(s.ws, L.o_bruns), (uint32_t)bruns.size(), st);
   s.timer.end();
-  s.launches += tiles ? 2 : 1;
+  s.launches += (tiles ? 2 : 1) + (bruns.empty() ? 0 : 1);
   CK(cudaGetLastError());
 
   if (record_root && stats) {
@@ -703,6 +756,8 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     if (h_off[s + 1] - h_off[s] >= (1ull << 32)) return LS_EINVAL;
   if (vb != 0 && vb != 4 && vb != 8) return LS_EINVAL;
   if (vb && !d_vals && h_off[nseg] > 0) return LS_EINVAL;
+  // keys (and values) must be naturally aligned 64-bit (32-bit) words
+  if (reinterpret_cast<uintptr_t>(d_keys) % 8 || (vb && reinterpret_cast<uintptr_t>(d_vals) % vb)) return LS_EINVAL;
   Layout lay = compute_layout(n, nseg, p, vb);
   if (n > 0 && (!ws || ws_bytes < lay.total)) return LS_ENOMEM;
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LS_EINVAL;
@@ -834,7 +889,7 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
       memcpy(&dstat, hp + sizeof(LevelCounters), sizeof dstat);
     }
     if (c.overflow) {
-      fprintf(stderr, "ls: workspace list capacity exceeded at level %u\n", level);
+      lsg::set_error_detail("workspace list capacity exceeded at level %u", level);
       return LS_ENOMEM;
     }
     if (dstat != 0) {
@@ -1307,6 +1362,7 @@ ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, ui
   if (!ctx || !model || (!d_keys && n) || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
   if (model->L < 2 || model->L > LS_MAX_FANOUT || mode < 0 || mode > 4) return LS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (k >= 50) return LS_EINVAL;  // B >= 2: B^(k+1) > 2^50 (and k + 1 cannot wrap)
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LS_ECUDA;
   uint32_t B = model->L;
   double P = pow_exact(B, k + 1);
@@ -1381,6 +1437,19 @@ ls_status ls_classify(ls_ctx* ctx, const ls_model* model, const void* d_keys, ui
                         reinterpret_cast<unsigned long long*>(d_hist), nbp, cells, st, d_fm, d_fl);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
+  return LS_OK;
+}
+
+ls_status ls_sample(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, uint64_t S, uint64_t seed,
+                    void* d_out, ls_stream_t stream) {
+  if (!ctx || (dtype != LS_F64 && dtype != LS_U64)) return LS_EINVAL;
+  if (S && (!d_keys || !d_out || n == 0)) return LS_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_keys) % 8 || reinterpret_cast<uintptr_t>(d_out) % 8) return LS_EINVAL;
+  if (S > n) S = n;
+  CK(cudaSetDevice(ctx->device));
+  launch_sample_keys(static_cast<const uint64_t*>(d_keys), n, S, seed, static_cast<uint64_t*>(d_out),
+                     static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
   return LS_OK;
 }
 
@@ -1469,6 +1538,8 @@ ls_status ls_model_import(ls_model* m, const void* buf, size_t bytes) {
   if (m->L < 1 || m->L > LS_MAX_FANOUT) return LS_EINVAL;
   return LS_OK;
 }
+
+const char* ls_last_error_detail(void) { return g_error_detail; }
 
 const char* ls_status_string(ls_status s) {
   switch (s) {

@@ -29,7 +29,7 @@ constexpr uint64_t kChunkKeys = (uint64_t)kTileKeys * kChunkTiles;
 
 enum : uint8_t { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2 };
 enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2, CLS_GUESS = 3 };
-enum : uint8_t { FLAG_SKIP_SCATTER = 1, FLAG_HOMOGENEOUS = 2, FLAG_NOPROGRESS = 4 };
+enum : uint8_t { FLAG_SKIP_SCATTER = 1, FLAG_HOMOGENEOUS = 2, FLAG_NOPROGRESS = 4, FLAG_ORDER_FREE = 8 };
 
 // One RMI leaf f2^(i)(x) = a (x - x0) + b, clamped to [lo, hi] (Sec. 4).
 struct Leaf {

@@ -145,6 +145,19 @@ __global__ void k_sample_gather(FreshArgs f, RunParams rp, uint64_t* __restrict_
   samp[pl.sample_off + j] = ord_of(src[it.lo + pos], rp.dt);
 }
 
+// Sample(A) of Alg. 2-5 for one array with a caller-given stream seed h:
+// key j of the sample is A[floor(u_j n / 2^64)], u_j = SplitMix64 output at
+// h + (j+1) * golden gamma (with replacement); S >= n takes A in order.
+__global__ void k_sample_keys(const uint64_t* __restrict__ keys, uint64_t n, uint64_t S, uint64_t h,
+                              uint64_t* __restrict__ out) {
+  pdl_wait();
+  uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (j >= S) return;
+  uint64_t pos = j;
+  if (S < n) pos = __umul64hi(splitmix64(h + (j + 1) * kGolden), n);
+  out[j] = keys[pos];
+}
+
 __global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
   pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -1340,6 +1353,11 @@ uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, co
 void launch_sample_gather(const FreshArgs& f, const RunParams& rp, uint64_t* samp, cudaStream_t st) {
   if (!f.total_samples) return;
   pdl_launch(k_sample_gather, grid_for(f.total_samples), kTPB, 0, st, f, rp, samp);
+}
+
+void launch_sample_keys(const uint64_t* keys, uint64_t n, uint64_t S, uint64_t h, uint64_t* out, cudaStream_t st) {
+  if (!S) return;
+  pdl_launch(k_sample_keys, grid_for(S), kTPB, 0, st, keys, n, S, h, out);
 }
 
 void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st) {

@@ -10,6 +10,10 @@
 
 namespace lsg {
 
+// Records a description of the last failure on this host thread (returned
+// by ls_last_error_detail); the library never prints.
+void set_error_detail(const char* fmt, ...);
+
 // Programmatic dependent launch: a kernel launched this way may be set up
 // while the previous kernel of its stream is still running; every kernel's
 // first statement (pdl_wait) blocks until that kernel has finished and its
@@ -82,6 +86,8 @@ struct FreshArgs {
 };
 void launch_sample_gather(const FreshArgs& f, const RunParams& rp, uint64_t* samp, cudaStream_t st);
 void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st);
+// One array's sample (key bits) with stream seed h; see ls_sample.
+void launch_sample_keys(const uint64_t* keys, uint64_t n, uint64_t S, uint64_t h, uint64_t* out, cudaStream_t st);
 
 struct FitArgs {
   Plan* plans;
@@ -163,7 +169,7 @@ struct PassArgs {
   unsigned long long* cursors;  // per plan: nb bucket bases in the destination
   uint32_t* agg;                // per chunk: nb_pad_max bucket counts (K1)
   unsigned long long* excl;     // per chunk: keys of each bucket in the item's earlier chunks
-  unsigned long long* chunk_ctr;  // K3 dynamic chunk counter (zeroed)
+  unsigned long long* chunk_ctr;  // [0]: K3 dynamic chunk counter, [1]: K3b run counter (zeroed)
   const uint32_t* chunk_plan;   // per chunk: index of its item in the batch
   uint64_t chunk_keys;          // keys per chunk: a multiple of the tile, at most kChunkKeys
   void* valsA;                  // key-value sorts: payload of buffer A (caller's values) ...
@@ -196,6 +202,36 @@ struct ChunkSeg {
 int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
                         const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
+
+// Buffered scatter (K3b).  When no child of an item is partitioned again
+// (every child is final, a base case or a depth-limit span: K2 sets
+// FLAG_ORDER_FREE), no bucket of the item is ever sampled, so the order of
+// keys inside its buckets does not matter to any later step: its keys go
+// through per-bucket line buffers with atomic position claims (the buffered
+// partitioning of Sec. 2.2 / Sec. 2.4) instead of the stable scatter.
+// Key-only sorts with at most kBufMaxBuckets buckets.  The host plans runs
+// for every candidate (flags are set on the device after planning); each
+// scatter kernel skips the items that belong to the other.
+constexpr uint32_t kBufMaxBuckets = 1024;
+__host__ __device__ inline bool buffered_scatter_candidate(const Plan& pl, uint32_t vbytes) {
+  return vbytes == 0 && pl.nb_pad <= kBufMaxBuckets;
+}
+__host__ __device__ inline bool buffered_scatter_ok(const Plan& pl, uint32_t vbytes) {
+  return buffered_scatter_candidate(pl, vbytes) && (pl.flags & FLAG_ORDER_FREE);
+}
+// A range of one item's keys taken by one K3b block: keys [off, off + len)
+// of the item (item-relative).
+struct BufRun {
+  uint64_t off, len;
+  uint32_t plan, pad;
+  uint64_t pad1;
+};
+static_assert(sizeof(BufRun) == 32, "BufRun layout");
+// Number of K3b blocks that can be resident (the run list is sized for two
+// runs per block).
+uint32_t buffered_scatter_slots();
+void launch_scatter_buffered(const PassArgs& a, const RunParams& rp, const BufRun* runs, uint32_t nruns,
+                             cudaStream_t st);
 
 struct ChildArgs {
   const Item* items;

@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
     if (ch >= a.nchunks) break;
     const uint32_t pi = a.chunk_plan[ch];
     const Plan& pl = a.plans[pi];
-    if (pl.flags & FLAG_SKIP_SCATTER) continue;  // uniform across the block
+    // uniform across the block; items of the buffered scatter are K3b's
+    if ((pl.flags & FLAG_SKIP_SCATTER) || buffered_scatter_ok(pl, a.vbytes)) continue;
     const Item& it = a.items[pi];
     const uint32_t nbk = pl.nb_pad;
     const unsigned long long* ex = a.excl + ch * nbp;
@@ -504,6 +505,193 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
     }
   }
   if (__syncthreads_or(oob ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
+}
+
+// ------------------------------------------------------------------ K3b
+
+// Buffered scatter for items whose order inside a bucket does not matter
+// (buffered_scatter_ok: no child is partitioned again): the partitioning of LearnedSort 2.0 (Sec. 2.2) and
+// IPS4o (Sec. 2.4), where every bucket has a buffer that is written out when
+// it is full.  Here a buffer is one line of kLineKeys keys in shared memory,
+// lines are aligned to the destination's addresses, and each key claims the
+// next position of its bucket with a shared-memory atomic, so the keys of a
+// bucket do not keep their input order.  A block takes a run of one item's
+// keys; the run's keys of bucket b fill one contiguous region of the
+// destination that starts at the bucket's cursor plus the keys of b in the
+// item before the run (the chunk prefixes, plus a count over the ids of the
+// run's first chunk when the run starts inside it).  Complete lines leave as
+// whole 64-byte writes; only the first and last line of a region are written
+// in part.  Per tile: phase A puts each key that falls in its bucket's
+// buffered line into the buffer and lists the lines that complete; after a
+// barrier the listed lines are written (four lanes per line) and their line
+// ends advanced; after a second barrier phase B places the keys past the
+// buffered line (whole lines straight out, the new partial line into the
+// buffer).  Phase B of one tile and phase A of the next touch different
+// slots, and line ends change only in the flush, so two barriers per tile
+// suffice.  Every global write is checked against the item's range.
+constexpr uint32_t kBufTPB = 512;
+constexpr uint32_t kBufKT = 8;
+constexpr uint32_t kBufTile = kBufTPB * kBufKT;
+constexpr uint32_t kLineKeys = 8;
+constexpr size_t kBufSmem = (size_t)kBufMaxBuckets * (kLineKeys * 8 + 8 + 4 + 4 + 4 + 2);
+
+__global__ void __launch_bounds__(kBufTPB, 2)
+    k_scatter_buffered(PassArgs a, RunParams rp, const BufRun* __restrict__ runs, uint32_t nruns) {
+  pdl_wait();
+  constexpr uint64_t M = ~(uint64_t)(kLineKeys - 1);
+  constexpr uint32_t kLPL = kLineKeys / 2;  // lanes per line (16-byte stores)
+  constexpr uint32_t kLPI = 32 / kLPL;      // lines per warp step
+  constexpr uint32_t kW = kBufTPB / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem);                  // [bucket][kLineKeys]
+  uint64_t* rs = buf + kBufMaxBuckets * kLineKeys;                    // region start (address / 8)
+  uint32_t* cur = reinterpret_cast<uint32_t*>(rs + kBufMaxBuckets);  // keys claimed in the region
+  uint32_t* le = cur + kBufMaxBuckets;                                // end of the buffered line, from rs
+  uint32_t* fe = le + kBufMaxBuckets;                                 // listed line: its old line end
+  uint16_t* fb = reinterpret_cast<uint16_t*>(fe + kBufMaxBuckets);   // listed line: its bucket
+  __shared__ uint32_t s_nfl[2];
+  __shared__ unsigned long long s_run;
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  bool bad = false;
+  for (;;) {
+    __syncthreads();  // the previous run is done with the block's buffers
+    if (threadIdx.x == 0) s_run = atomicAdd(a.chunk_ctr + 1, 1ull);
+    __syncthreads();
+    const uint64_t ri = s_run;
+    if (ri >= nruns) break;
+    const BufRun rn = runs[ri];
+    const Plan& pl = a.plans[rn.plan];
+    // uniform across the block; the stable scatter takes the other items
+    if ((pl.flags & FLAG_SKIP_SCATTER) || !buffered_scatter_ok(pl, a.vbytes)) continue;
+    const Item& it = a.items[rn.plan];
+    const uint32_t nbk = pl.nb_pad;
+    uint64_t* dst = it.buf ? a.outA : a.outB;
+    const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo;
+    const uint16_t* ids = a.ids + it.lo;
+    const uint64_t ab = (uint64_t)(uintptr_t)dst >> 3;  // dst[0] as a key address
+    const uint64_t alo = ab + it.lo, ahi = alo + it.n;    // the item's destination
+    const uint64_t ch = rn.off / a.chunk_keys;            // the run's first chunk (item-relative)
+    const unsigned long long* ex = a.excl + (pl.chunk_begin + ch) * a.nb_pad_max;
+    for (uint32_t b = threadIdx.x; b < nbk; b += kBufTPB) cur[b] = 0;
+    if (threadIdx.x == 0) s_nfl[0] = s_nfl[1] = 0;
+    __syncthreads();
+    for (uint64_t i = ch * a.chunk_keys + threadIdx.x; i < rn.off; i += kBufTPB) {
+      const uint32_t b = ids[i];
+      if (b < nbk) atomicAdd(&cur[b], 1u);
+      else bad = true;
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nbk; b += kBufTPB) {
+      const uint64_t x = ab + a.cursors[pl.cnt_off + b] + ex[b] + cur[b];
+      rs[b] = x;
+      cur[b] = 0;
+      le[b] = (uint32_t)((x & M) + kLineKeys - x);
+    }
+    __syncthreads();
+    uint64_t v[kBufKT];
+    uint32_t bk[kBufKT], rr[kBufKT];
+    auto load_tile = [&](uint64_t t0) {
+      const uint64_t len = rn.len - t0 < kBufTile ? rn.len - t0 : kBufTile;
+#pragma unroll
+      for (int k = 0; k < (int)kBufKT; ++k) {
+        const uint32_t j = k * kBufTPB + threadIdx.x;
+        const bool in = j < len;
+        v[k] = in ? src[rn.off + t0 + j] : 0ull;
+        bk[k] = in ? (uint32_t)ids[rn.off + t0 + j] : 0xFFFFu;
+      }
+    };
+    load_tile(0);
+    uint32_t par = 0;
+    for (uint64_t t0 = 0; t0 < rn.len; t0 += kBufTile, par ^= 1) {
+      uint32_t late = 0;
+#pragma unroll
+      for (int k = 0; k < (int)kBufKT; ++k) {
+        const uint32_t b = bk[k];
+        bool f = false;
+        uint32_t e = 0;
+        rr[k] = 0;
+        if (b < nbk) {
+          const uint32_t r = atomicAdd(&cur[b], 1u);
+          rr[k] = r;
+          e = le[b];
+          if (r < e) {
+            buf[b * kLineKeys + (((uint32_t)rs[b] + r) & (kLineKeys - 1))] = v[k];
+            f = r == e - 1;
+          } else {
+            late |= 1u << k;
+          }
+        } else if (b != 0xFFFFu) {
+          bad = true;  // K1 and K3 disagree
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, f);
+        if (m) {
+          const int ld = __ffs(m) - 1;
+          uint32_t base = 0;
+          if ((int)lane == ld) base = atomicAdd(&s_nfl[par], (uint32_t)__popc(m));
+          base = __shfl_sync(0xFFFFFFFFu, base, ld);
+          if (f) {
+            const uint32_t q = base + __popc(m & lt);
+            fb[q] = (uint16_t)b;
+            fe[q] = e;
+          }
+        }
+      }
+      __syncthreads();
+      // write the completed lines and advance their line ends
+      const uint32_t nf = s_nfl[par];
+      for (uint32_t i = wid * kLPI + lane / kLPL; i < nf; i += kW * kLPI) {
+        const uint32_t b = fb[i];
+        const uint64_t r0 = rs[b];
+        const uint64_t ls = (r0 + fe[i] - 1) & M;
+        const uint32_t q = lane % kLPL;
+        if (q == 0) le[b] = (uint32_t)(((r0 + cur[b]) & M) + kLineKeys - r0);
+        if (ls >= r0) {
+          if (ls >= alo && ls + kLineKeys <= ahi)
+            reinterpret_cast<uint4*>(ls << 3)[q] = reinterpret_cast<const uint4*>(buf + b * kLineKeys)[q];
+          else
+            bad = true;
+        } else {
+          for (uint32_t j = 2 * q; j < 2 * q + 2; ++j) {
+            const uint64_t g = ls + j;
+            if (g < r0) continue;
+            if (g >= alo && g < ahi) *reinterpret_cast<uint64_t*>(g << 3) = buf[b * kLineKeys + j];
+            else bad = true;
+          }
+        }
+      }
+      if (threadIdx.x == 0) s_nfl[par ^ 1] = 0;
+      __syncthreads();
+      // keys past the buffered line: whole lines straight out, the new
+      // partial line into the buffer
+#pragma unroll
+      for (int k = 0; k < (int)kBufKT; ++k) {
+        if (!(late & (1u << k))) continue;
+        const uint32_t b = bk[k];
+        const uint64_t r0 = rs[b];
+        const uint64_t g = r0 + rr[k];
+        if (g < r0 + le[b] - kLineKeys) {
+          if (g >= alo && g < ahi) *reinterpret_cast<uint64_t*>(g << 3) = v[k];
+          else bad = true;
+        } else {
+          buf[b * kLineKeys + (g & (kLineKeys - 1))] = v[k];
+        }
+      }
+      if (t0 + kBufTile < rn.len) load_tile(t0 + kBufTile);
+    }
+    __syncthreads();
+    // the regions' last (partial) lines
+    for (uint32_t i = threadIdx.x; i < nbk * kLineKeys; i += kBufTPB) {
+      const uint32_t b = i / kLineKeys, j = i % kLineKeys;
+      const uint64_t r0 = rs[b], e = r0 + cur[b];
+      const uint64_t g = (e & M) + j;
+      if (g < e && g >= r0) {
+        if (g >= alo && g < ahi) *reinterpret_cast<uint64_t*>(g << 3) = buf[i];
+        else bad = true;
+      }
+    }
+  }
+  if (__syncthreads_or(bad ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_EDEVICE);
 }
 
 // ------------------------------------------------------------------ chunk prefixes
@@ -703,6 +891,9 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     atomicMax(&ls->max_child, tmax);
     atomicAdd(&ls->sumsq_child, sq[0]);
   }
+  const bool refine_children = learned && rp.recurse == LS_RECURSE_REFINE_GLOBAL;
+  const uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
+  const uint64_t mg = (it.kind == KIND_REFINE) ? it.mg : 0;
   if (noprog) {
     // no-progress guard: redo the same range at the next level with the
     // splitter tree (keys stay where they are).
@@ -789,6 +980,11 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   __syncthreads();  // the first exchange's words are read by every thread before they are reused
   k2_exchange<L_N, 5>(nl, tot, sums, s32, s64);
   if (threadIdx.x == 0) {
+    // No child is partitioned again: every child is final, a base case or
+    // a depth-limit span, so no bucket of this item is ever sampled and the
+    // order of keys inside its buckets does not matter (the buffered
+    // scatter may take it).
+    if (tot[L_NEXT] == 0) pl.flags |= FLAG_ORDER_FREE;
     for (int q = 0; q < L_N; ++q) {
       unsigned long long* ctr = (q == L_NEXT)    ? &a.ctr->n_next
                                 : (q == L_SMALL) ? &a.ctr->n_base_small
@@ -812,8 +1008,6 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + nl[q];
   const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.large_cap, a.copy_cap, a.fallback_cap};
   bool ovf = false;
-  uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
-  uint64_t mg = (it.kind == KIND_REFINE) ? it.mg : 0;
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
     uint64_t clo = it.lo + s_start[b];
@@ -856,7 +1050,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
         if (b >= 1) ch.ord_lo = T[b] > it.ord_lo ? T[b] : it.ord_lo;
         if (b < pl.kmax) ch.ord_hi = T[b + 1] - 1;
       }
-      if (learned && rp.recurse == LS_RECURSE_REFINE_GLOBAL) {
+      if (refine_children) {
         ch.kind = KIND_REFINE;
         ch.model = pl.model;
         ch.mk = (uint16_t)(mk + 1);
@@ -2057,6 +2251,17 @@ void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st) {
   if (a.vbytes == 8) launch_k3_vb<8>(a, rp, st);
   else if (a.vbytes == 4) launch_k3_vb<4>(a, rp, st);
   else launch_k3_vb<0>(a, rp, st);
+}
+
+uint32_t buffered_scatter_slots() { return (uint32_t)sm_count() * 2; }
+
+void launch_scatter_buffered(const PassArgs& a, const RunParams& rp, const BufRun* runs, uint32_t nruns,
+                             cudaStream_t st) {
+  if (!nruns) return;
+  static size_t set[64] = {};
+  allow_smem(k_scatter_buffered, kBufSmem, set);
+  const uint32_t grid = nruns < buffered_scatter_slots() ? nruns : buffered_scatter_slots();
+  pdl_launch(k_scatter_buffered, grid, kBufTPB, kBufSmem, st, a, rp, runs, nruns);
 }
 
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {

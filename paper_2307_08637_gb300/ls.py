@@ -30,13 +30,14 @@ EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
     "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_tune_export", "ls_tune_import",
-    "ls_sort_host_batch", "ls_sort_pairs", "ls_workspace_size_pairs",
+    "ls_sort_host_batch", "ls_sort_pairs", "ls_workspace_size_pairs", "ls_last_error_detail", "ls_sample",
 )
 
 
 class LSError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what} failed: {status_string(status)} ({status})")
+        detail = lib().ls_last_error_detail().decode() if status in (LS_ECUDA, LS_ENOMEM) else ""
+        super().__init__(f"{what} failed: {status_string(status)} ({status})" + (f": {detail}" if detail else ""))
         self.status = status
 
 
@@ -199,6 +200,10 @@ def lib() -> C.CDLL:
     L.ls_model_import.restype = C.c_int
     L.ls_status_string.argtypes = [C.c_int]
     L.ls_status_string.restype = C.c_char_p
+    L.ls_last_error_detail.argtypes = []
+    L.ls_last_error_detail.restype = C.c_char_p
+    L.ls_sample.argtypes = [vp, vp, u64, C.c_int, u64, u64, vp, vp]
+    L.ls_sample.restype = C.c_int
     L.ls_autotune.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Params), C.POINTER(TuneReport), vp]
     L.ls_autotune.restype = C.c_int
     L.ls_tune_export.argtypes = [vp, C.c_char_p, C.POINTER(C.c_size_t)]
@@ -435,10 +440,49 @@ def ls_classify(ctx: Context, model: Model, keys, k: int = 0, g: int = 0, mode: 
 def ls_classify_static(model: Model, keys, ids, hist, k: int = 0, g: int = 0, mode: int = LS_CLASSIFY_AUTO,
                        stream=None) -> None:
     """ls_classify into caller-provided outputs, with no device allocation
-    anywhere on the path (for callers that cannot allocate: see ls.h)."""
+    anywhere on the path (for callers that cannot allocate: see ls.h).
+
+    The C entry point trusts its pointers, so the tensors are checked here:
+    keys float64 / uint64 (int64 bit patterns accepted), ids int32 with at
+    least keys.numel() elements (or None), hist int64 with at least model.L
+    elements (or None), all contiguous CUDA tensors on keys' device.  The
+    call runs with that device current, on `stream` or that device's current
+    stream."""
+    import torch
+    if not isinstance(keys, torch.Tensor) or not keys.is_cuda:
+        raise ValueError("keys must be a CUDA tensor")
     dt = _dtype_code(keys)
-    _check(lib().ls_classify_static(C.byref(model), _ptr(keys), keys.numel(), dt, k, g, mode, _ptr(ids),
-                                    _ptr(hist), _stream(stream)), "ls_classify_static")
+    if not keys.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    dev = keys.device
+    for name, t, dtype, need in (("ids", ids, torch.int32, keys.numel()), ("hist", hist, torch.int64, model.L)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on {dev}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {need}")
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        _check(lib().ls_classify_static(C.byref(model), _ptr(keys), keys.numel(), dt, k, g, mode, _ptr(ids),
+                                        _ptr(hist), _stream(st)), "ls_classify_static")
+
+
+def ls_sample(ctx: Context, keys, S: int, seed: int, stream=None):
+    """Sample(A): min(S, n) keys of `keys` drawn with replacement from the
+    counter-based SplitMix64 stream at `seed` (a new tensor, same dtype)."""
+    import torch
+    dt = _dtype_code(keys)
+    if not keys.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    n = keys.numel()
+    out = torch.empty(min(S, n), dtype=keys.dtype, device=keys.device)
+    _check(lib().ls_sample(ctx.handle, _ptr(keys), n, dt, S, seed % 2**64, _ptr(out), _stream(stream)), "ls_sample")
+    return out
 
 
 def ls_fit_grad(ctx: Context, model: Model, sorted_sample, stream=None) -> dict:
