@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
                     help="c2: six 1e8-key arrays (the headline); c4: 4096 segments, batched vs one call per array")
     ap.add_argument("--nseg", type=int, default=4096, help="c4: number of segments")
+    ap.add_argument("--no-c4", action="store_true", help="leave the C4 batch out of the default line")
+    ap.add_argument("--no-c5", action="store_true", help="leave the C5 2e9-key run out of the default line")
+    ap.add_argument("--c5-n", type=float, default=2e9, help="C5 keys")
     return ap.parse_args()
 
 
@@ -363,16 +366,36 @@ def run_ours(args):
         import oracle
 
         oracle.build()
-        x = inputs[0][1]
-        t0 = time.perf_counter()
-        out, rc, _, _, _ = oracle.sort(x, oracle.params())
-        dt = time.perf_counter() - t0
-        assert rc == 0
-        cpu = {"value": x.size / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full {x.size}-key {inputs[0][0]} array (1 of the 6 distributions), single thread",
-               "seconds": dt}
+        # mean of 3 runs on a bounded sample: the first 1e7 keys of three of
+        # the six arrays (the oracle is single-threaded; ~5 s per 1e8 keys)
+        runs = []
+        for d, x in inputs[:3]:
+            xs = x[:min(x.size, 10_000_000)]
+            t0 = time.perf_counter()
+            out, rc, _, _, _ = oracle.sort(xs, oracle.params(basecase_threshold=BASECASE_T))
+            runs.append((xs.size, time.perf_counter() - t0))
+            assert rc == 0
+        cpu = {"value": statistics.mean(k / t for k, t in runs), "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": "mean of 3 runs, each the first 1e7 keys of one array (" +
+                         ", ".join(d for d, _ in inputs[:3]) + "), single thread",
+               "seconds": [t for _, t in runs]}
 
     launches = sum(int(st.kernel_launches) for st in sts_learned)
+    # the other configurations, measured on the same GPU after the headline
+    # (single-rank runs only: the scaling runs repeat the headline alone)
+    c4 = c5 = None
+    if world == 1 and not (args.no_c4 and args.no_c5):
+        del pristine, work
+        ctx.free_workspace()
+        torch.cuda.empty_cache()
+        if not args.no_c4:
+            c4 = c4_measure(lsg, ctx, args, torch, stream, with_cpu=False)
+            ctx.free_workspace()
+            torch.cuda.empty_cache()
+        if not args.no_c5:
+            c5 = c5_measure(lsg, ctx, args, torch, stream)
+            ctx.free_workspace()
+            torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -392,6 +415,8 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": launches,
+        "c4": c4,
+        "c5": c5,
     }
     ctx.close()
     if rank == 0:
@@ -410,27 +435,17 @@ def _oracle_segments(args_tuple):
     return rc
 
 
-def run_c4(args):
+def c4_measure(lsg, ctx, args, torch, stream, with_cpu=True):
     """C4: nseg float64 arrays with log-uniform lengths in [1e3, 1e6], each its
     own distribution with a random affine map; one ls_sort_segmented call
     (every segment's sample, model and partition handled level by level in
     shared launches) against one ls_sort call per array, both with the
     parameters the autotuner picks on a segment of the mean length."""
-    import torch
-
-    rank, world, local = dist_env()
-    if world > 1 and rank != 0:
-        return 0
     dev = 0
-    torch.cuda.set_device(dev)
-    import paper_2307_08637_gb300 as lsg
-
     keys, off, names = datagen.segmented(args.nseg, 4)
     nseg = off.size - 1
     lens = np.diff(off).astype(np.int64)
     n = int(off[-1])
-    stream = torch.cuda.current_stream()
-    ctx = lsg.Context(dev)
     pristine = torch.from_numpy(keys).to(f"cuda:{dev}")
     work = torch.empty_like(pristine)
     mean_len = n / nseg
@@ -463,12 +478,12 @@ def run_c4(args):
         e1.synchronize()
         return e0.elapsed_time(e1), launches
 
-    for _ in range(args.warmup):
+    for _ in range(max(1, min(args.warmup, 3))):
         batched()
     torch.cuda.synchronize()
     with Clocks(dev) as clk:
         bms, bst = [], None
-        for _ in range(args.steps):
+        for _ in range(max(1, min(args.steps, 5))):
             ms, bst = batched()
             bms.append(ms)
     out_b = work.clone()
@@ -479,17 +494,18 @@ def run_c4(args):
     starts = torch.from_numpy(off[1:-1].astype(np.int64) - 1).to(f"cuda:{dev}")
     ok[starts[starts >= 0]] = True
     assert bool(ok.all()), "segmented output not sorted"
+    del o, ok
     looped()  # warm-up of the per-array path
     lms, llaunch = [], 0
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(2):
         ms, llaunch = looped()
         lms.append(ms)
     assert torch.equal(work, out_b), "batched and per-array results differ"
+    del out_b, work, pristine, seg_probe
     b_ms = sum(bms) / len(bms)
     l_ms = sum(lms) / len(lms)
-    # oracle: a bounded sample of segments, one thread and all host cores
     cpu = None
-    if not args.no_cpu:
+    if with_cpu and not args.no_cpu:
         import multiprocessing as mp
         import oracle
 
@@ -511,25 +527,97 @@ def run_c4(args):
         cpu = {"value": nk / t1, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(segs)} of the {nseg} segments ({nk} keys), one thread",
                "all_cores": {"value": nk / tm, "cores": cores, "note": "same segments, spawn pool, one per task"}}
+    return {
+        "workload": f"C4: {nseg} float64 segments, lengths log-uniform in [1e3, 1e6] ({n} keys), "
+                    "distribution per segment from the six of C2, shift U[-1e3,1e3], scale log-U[1e-3,1e3]",
+        "keys": n, "batched": {"value": n / (b_ms / 1e3), "unit": "keys/s", "ms": b_ms,
+                               "gpu_launches": int(bst.kernel_launches)},
+        "per_array_calls": {"value": n / (l_ms / 1e3), "unit": "keys/s", "ms": l_ms, "gpu_launches": llaunch},
+        "batched_speedup": l_ms / b_ms,
+        "params": {"fanout": p.fanout, "basecase_threshold": p.basecase_threshold, "sample_rate": p.sample_rate,
+                   "recurse_model": p.recurse_model,
+                   "chosen_by": f"ls_autotune on segment {probe} ({int(lens[probe])} keys, mean {mean_len:.0f}); "
+                                f"{rep.configs} configurations, {rep.base_ms:.3f} -> {rep.best_ms:.3f} ms"},
+        "cpu_baseline": cpu, "clocks": clk.summary(), "l2": "4.7 GB of keys, larger than L2; no flush",
+    }
+
+
+def c5_measure(lsg, ctx, args, torch, stream):
+    """C5: 2e9 skewed uint64 keys (16 GB), RETRAIN recursion (a new sample and
+    model per bucket), learned partitioner against the splitter tree on the
+    same kernels, with per-pass achieved bandwidth."""
+    dev = 0
+    n = int(args.c5_n)
+    pristine = datagen.skewed_u64_device(n, 5, f"cuda:{dev}").view(torch.int64)
+    work = torch.empty_like(pristine)
+    peak, _ = measured_peak()
+    out = {"workload": f"C5: {n} uint64 keys (piecewise-linear CDF over 64 Dirichlet(0.3) pieces + 1% in 100 "
+                       "lognormal(sigma=2) clusters), RETRAIN recursion, T = 4096",
+           "keys": n, "l2": "16 GB of keys, larger than L2; no flush"}
+    for name, part in (("learned", lsg.LS_PART_AUTO), ("splitter", lsg.LS_PART_SPLITTER)):
+        p = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, basecase_threshold=BASECASE_T,
+                                  recurse_model=lsg.LS_RECURSE_RETRAIN, partitioner=part)
+        ctx.workspace(n, 1, lsg.LS_U64, p)
+        ms, sts = [], []
+        for step in range(3):  # one warm-up, two timed
+            work.copy_(pristine)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = lsg.ls_sort(ctx, work, p, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if step:
+                ms.append(e0.elapsed_time(e1))
+                sts.append(st)
+        w = work.view(torch.int64)
+        o = w ^ (-(2**63))  # u64 order as signed
+        assert bool((o[1:] >= o[:-1]).all()), "C5 output not sorted"
+        del o
+        passes = {}
+        for st in sts:
+            for k, v in st.passes().items():
+                a = passes.setdefault(k, {"ms": 0.0, "keys": 0})
+                a["ms"] += v["ms"] / len(sts)
+                a["keys"] += v["keys"] / len(sts)
+        frac = {}
+        for k, per_key in (("scatter", SCATTER_BYTES_PER_KEY), ("classify", CLASSIFY_BYTES_PER_KEY),
+                           ("base", SCATTER_BYTES_PER_KEY)):
+            if k in passes and passes[k]["ms"] > 0:
+                gbs = per_key * passes[k]["keys"] / (passes[k]["ms"] / 1e3) / 1e9
+                frac[k] = {"gbs": gbs, "frac": gbs / peak}
+        m = sum(ms) / len(ms)
+        out[name] = {"value": n / (m / 1e3), "unit": "keys/s", "ms": m,
+                     "root_decision": int(sts[-1].root_decision), "levels": int(sts[-1].levels_used),
+                     "level1_max_bucket": int(sts[-1].level[0].max_child),
+                     "passes_ms": {k: v["ms"] for k, v in passes.items()}, "pass_roofline": frac}
+        ctx.free_workspace()
+    out["learned_speedup"] = out["splitter"]["ms"] / out["learned"]["ms"]
+    del work, pristine
+    return out
+
+
+def run_c4(args):
+    """The C4 line alone (--workload c4)."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    dev = 0
+    torch.cuda.set_device(dev)
+    import paper_2307_08637_gb300 as lsg
+
+    stream = torch.cuda.current_stream()
+    ctx = lsg.Context(dev)
+    r = c4_measure(lsg, ctx, args, torch, stream)
     line = {
         "metric": "keys/s, batched segmented sort vs one ls_sort call per array (4096 f64 segments), 1 GB300",
-        "value": n / (b_ms / 1e3), "unit": "keys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": b_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"C4: {nseg} float64 segments, lengths log-uniform in [1e3, 1e6] ({n} keys), "
-                               "distribution per segment from the six of C2, shift U[-1e3,1e3], scale log-U[1e-3,1e3]",
-                   "params": {"fanout": p.fanout, "basecase_threshold": p.basecase_threshold,
-                              "sample_rate": p.sample_rate, "recurse_model": p.recurse_model,
-                              "chosen_by": f"ls_autotune on segment {probe} ({int(lens[probe])} keys, mean "
-                                           f"{mean_len:.0f}); {rep.configs} configurations, "
-                                           f"{rep.base_ms:.3f} -> {rep.best_ms:.3f} ms"},
-                   "l2": "4.7 GB of keys, larger than L2; no flush"},
-        "per_array_calls": {"value": n / (l_ms / 1e3), "unit": "keys/s", "ms_per_step": l_ms,
-                            "gpu_launches": llaunch},
-        "batched_speedup": l_ms / b_ms,
-        "gpu_launches": int(bst.kernel_launches),
-        "cpu_baseline": cpu,
-        "clocks": clk.summary(),
+        "value": r["batched"]["value"], "unit": "keys/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["batched"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": r["workload"], "params": r["params"], "l2": r["l2"]},
+        "per_array_calls": r["per_array_calls"], "batched_speedup": r["batched_speedup"],
+        "gpu_launches": r["batched"]["gpu_launches"], "cpu_baseline": r["cpu_baseline"], "clocks": r["clocks"],
     }
     ctx.close()
     print(json.dumps(line), flush=True)
