@@ -137,11 +137,15 @@ typedef struct {
 #define LS_DEC_SPLITTER 2
 #define LS_DEC_SPLITTER_EQ 3
 #define LS_DEC_HOMOGENEOUS 4
+#define LS_DEC_RADIX 5 /* radix split of the bits where the bucket's keys differ (no model,
+                        * no sample): below a REFINE_GLOBAL model, for a bucket the model
+                        * did not split or one past the FP64 refinement limit */
 
 typedef struct {
   uint64_t items, learned, splitter, splitter_eq, homogeneous, noprogress;
   uint64_t base_items, base_keys, fallback_items, fallback_keys;
   uint64_t keys, max_child, sumsq_child, eq_keys;
+  uint64_t radix; /* items partitioned by the radix split */
 } ls_level_stats;
 
 /* Kernel classes timed with LS_FLAG_TIME_PASSES. */

@@ -31,7 +31,7 @@ F64 = 0
 U64 = 1
 PART_AUTO, PART_LEARNED, PART_SPLITTER = 0, 1, 2
 RECURSE_REFINE_GLOBAL, RECURSE_RETRAIN = 0, 1
-DEC_NONE, DEC_LEARNED, DEC_SPLITTER, DEC_SPLITTER_EQ, DEC_HOMOGENEOUS = 0, 1, 2, 3, 4
+DEC_NONE, DEC_LEARNED, DEC_SPLITTER, DEC_SPLITTER_EQ, DEC_HOMOGENEOUS, DEC_RADIX = 0, 1, 2, 3, 4, 5
 MAX_FANOUT = 4096
 MAX_LEVELS = 48
 OK, EINVAL, ENOMEM, ENAN = 0, 1, 2, 3
@@ -120,7 +120,7 @@ class Splitter(C.Structure):
 class LevelStats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "items", "learned", "splitter", "splitter_eq", "homogeneous", "noprogress", "base_items",
-        "base_keys", "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys")]
+        "base_keys", "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys", "radix")]
 
 
 class Trace(C.Structure):

@@ -555,7 +555,7 @@ void lsref_splitter_classify(const lsref_splitter* t, const uint64_t* keys, uint
 
 /* ------------------------------------------------------ the full sort */
 
-enum { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2 };
+enum { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2, KIND_RADIX = 3 };
 
 typedef struct mslot {
   lsref_model m;
@@ -569,7 +569,7 @@ typedef struct {
   uint64_t mg;
   mslot* model;
   uint32_t level;
-  uint32_t mk;
+  uint32_t mk;  /* REFINE: refinement depth k; RADIX: keys agree above this many low bits */
   int kind;
   int is_root;
 } item_t;
@@ -680,13 +680,14 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
     RELEASE_INHERITED();
     return 0;
   }
-  /* Homogeneity check (Sec. 2.2): an all-equal range is already sorted. */
-  uint64_t mn = a[0], mx = a[0];
-  for (uint64_t i = 1; i < n; ++i) {
-    if (a[i] < mn) mn = a[i];
-    if (a[i] > mx) mx = a[i];
-  }
-  if (mn == mx) {
+  /* Homogeneity check (Sec. 2.2): an all-equal range is already sorted.
+   * odiff, the OR over the keys of ord(x) XOR ord(first key), is zero for
+   * an all-equal range; its highest set bit is the highest bit in which two
+   * keys differ (whatever their order), so every key agrees with every
+   * other above bit_length(odiff). */
+  uint64_t odiff = 0;
+  for (uint64_t i = 1; i < n; ++i) odiff |= a[i] ^ a[0];
+  if (odiff == 0) {
     ls->homogeneous += 1;
     if (record_root && c->tr) c->tr->root_decision = LSREF_DEC_HOMOGENEOUS;
     if (it.is_root && c->seg_decision) c->seg_decision[it.segment] = LSREF_DEC_HOMOGENEOUS;
@@ -700,6 +701,15 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
   uint32_t mk = 0;
   uint64_t mg = 0;
   int fresh = 1;
+  /* Radix split (a prediction-less partitioner for buckets the model could
+   * not split, Sec. 2.4's IPS2Ra radix partitioning): the keys agree above
+   * bit `top`; bucket = the bits [s, top) of ord(x), s = max(top - 10, 0). */
+  uint32_t rshift = 0;
+  if (it.kind == KIND_RADIX) {
+    fresh = 0;
+    decision = LSREF_DEC_RADIX;
+    rshift = it.mk > 10 ? it.mk - 10 : 0;
+  }
   if (it.kind == KIND_REFINE) {
     double P = pow_exact(B, it.mk + 1);
     if (P <= REFINE_LIMIT) {
@@ -765,9 +775,17 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
   }
 
   /* Classify every key, histogram, stable scatter (Sec. 2.2 partitioning). */
-  uint32_t nb = (decision == LSREF_DEC_LEARNED) ? B : c->split.nbuckets;
+  uint32_t nb = (decision == LSREF_DEC_LEARNED) ? B
+                : (decision == LSREF_DEC_RADIX) ? (it.mk > rshift ? 1u << (it.mk - rshift) : 2u)
+                                                : c->split.nbuckets;
   memset(c->cnt, 0, nb * sizeof(uint64_t));
-  if (decision == LSREF_DEC_LEARNED) {
+  if (decision == LSREF_DEC_RADIX) {
+    for (uint64_t i = 0; i < n; ++i) {
+      uint32_t b = (uint32_t)((a[i] >> rshift) & (uint64_t)(nb - 1));
+      c->ids[i] = b;
+      c->cnt[b] += 1;
+    }
+  } else if (decision == LSREF_DEC_LEARNED) {
     double P = pow_exact(B, mk + 1);
     double Bg = (double)((uint64_t)B * mg);
     for (uint64_t i = 0; i < n; ++i) {
@@ -810,6 +828,7 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
   ls->items += 1;
   ls->keys += n;
   if (decision == LSREF_DEC_LEARNED) ls->learned += 1;
+  else if (decision == LSREF_DEC_RADIX) ls->radix += 1;
   else if (decision == LSREF_DEC_SPLITTER) ls->splitter += 1;
   else ls->splitter_eq += 1;
   int noprog = 0;
@@ -819,7 +838,7 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
     ls->sumsq_child += sz * sz;
     if (sz == n) noprog = 1;
   }
-  int eq = (decision != LSREF_DEC_LEARNED) && c->split.equality;
+  int eq = (decision == LSREF_DEC_SPLITTER || decision == LSREF_DEC_SPLITTER_EQ) && c->split.equality;
   if (noprog) {
     /* an all-in-one equality bucket is final, not a failed split */
     int only_eq = 0;
@@ -844,7 +863,18 @@ static int process_item(sctx* c, stack_t_* st, item_t it) {
     ch.segment = it.segment;
     ch.level = it.level + 1;
     ch.gidx = it.gidx * nb + bb;
-    if (sz == n) {
+    /* Under REFINE_GLOBAL no bucket below a learned item draws a new sample
+     * (LearnedSort 2.0 trains once, Sec. 2.2): a child the model did not
+     * split (no progress), or one that would refine past the FP64 limit
+     * B^(k+1) > 2^50, takes the radix split on the bits where this item's
+     * keys differ; a radix item's children split the next bits down. */
+    if (decision == LSREF_DEC_RADIX) {
+      ch.kind = KIND_RADIX;
+      ch.mk = rshift;
+    } else if (refine_children && (sz == n || pow_exact(B, mk + 2) > REFINE_LIMIT)) {
+      ch.kind = KIND_RADIX;
+      ch.mk = 64 - (uint32_t)__builtin_clzll(odiff);
+    } else if (sz == n) {
       ch.kind = KIND_FORCE_SPLITTER; /* no-progress guard */
     } else if (refine_children) {
       ch.kind = KIND_REFINE;

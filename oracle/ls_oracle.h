@@ -57,6 +57,7 @@ extern "C" {
 #define LSREF_DEC_SPLITTER 2    /* splitter tree, no equality buckets */
 #define LSREF_DEC_SPLITTER_EQ 3 /* splitter tree with equality buckets */
 #define LSREF_DEC_HOMOGENEOUS 4 /* all keys equal: left as is */
+#define LSREF_DEC_RADIX 5       /* radix split of the bits where the keys differ */
 
 typedef struct {
   uint32_t fanout;             /* B = number of RMI leaves = learned buckets */
@@ -113,6 +114,7 @@ typedef struct {
   uint64_t max_child;      /* largest bucket produced at this level */
   uint64_t sumsq_child;    /* sum of squared bucket sizes */
   uint64_t eq_keys;        /* keys that landed in equality buckets */
+  uint64_t radix;          /* items partitioned by a radix split (no model, no sample) */
 } lsref_level_stats;
 
 typedef struct {

@@ -162,7 +162,9 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.n = n;
   l.L = p->fanout;
   uint32_t eqmax = 2 * p->splitter_fanout - 1;  // 2m+1 buckets, m <= B_s - 1 splitters
-  l.nbc = pow2ceil(std::max<uint32_t>(std::max<uint32_t>(p->fanout, eqmax), 2));
+  // per-item bucket tables hold the learned fanout, the splitter tree with
+  // equality buckets, or a radix split (2^kRadixBits buckets)
+  l.nbc = pow2ceil(std::max<uint32_t>(std::max<uint32_t>(p->fanout, eqmax), 1u << kRadixBits));
   l.cells = 1u << kDirBits;
   uint64_t T = p->basecase_threshold;
   l.icap = n / (T + 1) + nseg + 16;
@@ -369,7 +371,17 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
     pl.dir_off = (uint64_t)i * (L.cells + 1);
     pl.mixed = 0;
     pl.model = -1;
-    bool is_fresh = it.kind != KIND_REFINE;
+    bool is_fresh = it.kind != KIND_REFINE && it.kind != KIND_RADIX;
+    if (it.kind == KIND_RADIX) {
+      // radix split of the bits [s, top) in which the item's keys may differ
+      const uint32_t nb = radix_buckets(it.mk);
+      pl.decision = LS_DEC_RADIX;
+      pl.cls = CLS_RADIX;
+      pl.nb = nb;
+      pl.nb_pad = nb;
+      pl.kmax = nb - 1;
+      pl.dir_shift = radix_shift(it.mk);
+    }
     if (it.kind == KIND_REFINE) {
       double P = pow_exact(p->fanout, it.mk + 1u);
       if (P > kRefineLimit) {

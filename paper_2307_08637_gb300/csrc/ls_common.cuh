@@ -27,8 +27,8 @@ constexpr uint32_t kTileKeys = 4096;                  // keys per partition tile
 constexpr uint32_t kChunkTiles = 16;                  // tiles per chunk (one lookback unit)
 constexpr uint64_t kChunkKeys = (uint64_t)kTileKeys * kChunkTiles;
 
-enum : uint8_t { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2 };
-enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2, CLS_GUESS = 3 };
+enum : uint8_t { KIND_FRESH = 0, KIND_FORCE_SPLITTER = 1, KIND_REFINE = 2, KIND_RADIX = 3 };
+enum : uint8_t { CLS_DIRECT = 0, CLS_TREE = 1, CLS_DIR = 2, CLS_GUESS = 3, CLS_RADIX = 4 };
 enum : uint8_t { FLAG_SKIP_SCATTER = 1, FLAG_HOMOGENEOUS = 2, FLAG_NOPROGRESS = 4, FLAG_ORDER_FREE = 8 };
 
 // One RMI leaf f2^(i)(x) = a (x - x0) + b, clamped to [lo, hi] (Sec. 4).
@@ -63,7 +63,7 @@ struct Item {
   uint64_t mg;             // refine: parent index g inside the model
   uint64_t ord_lo, ord_hi; // every key of the item has ord in [ord_lo, ord_hi]
   uint32_t segment;
-  uint16_t level, mk;      // recursion level; refine depth k below the model
+  uint16_t level, mk;      // recursion level; refine depth k below the model (radix: keys agree above bit mk)
   int32_t model;           // refine: model slot
   uint8_t kind, buf;       // KIND_*; 0 = keys array, 1 = workspace buffer
   uint16_t pad;
@@ -81,7 +81,7 @@ struct Plan {
   uint64_t dir_hi;      // last pivot; keys >= dir_hi are in bucket kmax
   unsigned int mixed;   // K1: 1 when some key of the item differs from its first key
   unsigned int pad0;
-  unsigned long long pad1;
+  unsigned long long odiff;  // K1: OR over the keys of ord(x) ^ ord(first key)
   unsigned long long dups;        // fresh: sample duplicates
   unsigned long long imb;         // fresh: largest sample bucket under the RMI
   double P, Bg;         // refine scale B^(k+1) and offset B g
@@ -123,6 +123,7 @@ struct DevLevelStats {
   unsigned long long items, learned, splitter, splitter_eq, homogeneous, noprogress;
   unsigned long long base_items, base_keys, fallback_items, fallback_keys;
   unsigned long long keys, max_child, sumsq_child, eq_keys;
+  unsigned long long radix;
 };
 static_assert(sizeof(DevLevelStats) == sizeof(ls_level_stats), "stats layout");
 
@@ -198,6 +199,25 @@ __device__ __forceinline__ double model_F(const DModel& m, const Leaf* __restric
   f = dmax(f, l.lo);
   f = dmin(f, l.hi);
   return f;
+}
+
+// True when B^e exceeds the FP64 refinement limit 2^50 (B >= 2; the
+// product stops growing once it is past the limit).
+__host__ __device__ __forceinline__ bool beyond_refine_limit(uint32_t B, uint32_t e) {
+  double P = 1.0;
+  for (uint32_t i = 0; i < e && P <= kRefineLimit; ++i) P = P * (double)B;
+  return P > kRefineLimit;
+}
+
+// Radix split of a bucket whose keys agree above bit `top`: the window of
+// ord bits [shift, top), at most kRadixBits wide.
+constexpr uint32_t kRadixBits = 10;
+__host__ __device__ __forceinline__ uint32_t radix_shift(uint32_t top) {
+  return top > kRadixBits ? top - kRadixBits : 0;
+}
+__host__ __device__ __forceinline__ uint32_t radix_buckets(uint32_t top) {
+  const uint32_t s = radix_shift(top);
+  return top > s ? 1u << (top - s) : 2u;
 }
 
 // Refinement bucket (k levels below the model's item, parent index g):

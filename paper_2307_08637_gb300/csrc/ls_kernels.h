@@ -203,21 +203,24 @@ int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi
                         const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
 
-// Buffered scatter (K3b).  When no child of an item is partitioned again
-// (every child is final, a base case or a depth-limit span: K2 sets
-// FLAG_ORDER_FREE), no bucket of the item is ever sampled, so the order of
-// keys inside its buckets does not matter to any later step: its keys go
-// through per-bucket line buffers with atomic position claims (the buffered
+// Buffered scatter (K3b).  An item none of whose descendants ever draws a
+// sample needs no particular order of the keys inside its buckets: a learned
+// item under REFINE_GLOBAL (its descendants refine the same model or take
+// the radix split), a radix item, or any item none of whose children is
+// partitioned again (K2 sets FLAG_ORDER_FREE).  Its keys go through
+// per-bucket line buffers with atomic position claims (the buffered
 // partitioning of Sec. 2.2 / Sec. 2.4) instead of the stable scatter.
 // Key-only sorts with at most kBufMaxBuckets buckets.  The host plans runs
-// for every candidate (flags are set on the device after planning); each
+// for every candidate (the flag is set on the device after planning); each
 // scatter kernel skips the items that belong to the other.
 constexpr uint32_t kBufMaxBuckets = 1024;
 __host__ __device__ inline bool buffered_scatter_candidate(const Plan& pl, uint32_t vbytes) {
   return vbytes == 0 && pl.nb_pad <= kBufMaxBuckets;
 }
-__host__ __device__ inline bool buffered_scatter_ok(const Plan& pl, uint32_t vbytes) {
-  return buffered_scatter_candidate(pl, vbytes) && (pl.flags & FLAG_ORDER_FREE);
+__host__ __device__ inline bool buffered_scatter_ok(const Plan& pl, const RunParams& rp, uint32_t vbytes) {
+  return buffered_scatter_candidate(pl, vbytes) &&
+         ((pl.flags & FLAG_ORDER_FREE) || pl.decision == LS_DEC_RADIX ||
+          (pl.decision == LS_DEC_LEARNED && rp.recurse == LS_RECURSE_REFINE_GLOBAL));
 }
 // A range of one item's keys taken by one K3b block: keys [off, off + len)
 // of the item (item-relative).

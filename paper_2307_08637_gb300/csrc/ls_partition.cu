@@ -75,6 +75,7 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
     c.kmax = rp.B - 1;
     return;
   }
+  if (c.cls == CLS_RADIX) return;  // no table: the bucket is a bit field of ord
   const uint64_t* T = a.pivots + pl.tab_off;
   for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) sT[j] = T[j];
   if (c.cls == CLS_DIR) {
@@ -125,6 +126,7 @@ __device__ __forceinline__ uint32_t classify_as(uint64_t bits, const Cls& c, con
     return refine_id(m, leaves + m.leaf_off, key_value(bits, DT), c.P, c.Bg, c.B);
   }
   const uint64_t u = ord_of(bits, DT);
+  if (CLS == CLS_RADIX) return (uint32_t)(u >> c.shift) & c.kmax;  // kmax = buckets - 1, a power of two minus 1
   if (CLS == CLS_GUESS) {
     const uint32_t g = guess_bucket(c.fm, static_cast<const FLeaf*>(sAux), c.Pf, c.Bgf, c.kmax, bits, DT);
     return fix_guess(sT, c.nb_pad, c.kmax, g, u);
@@ -149,15 +151,16 @@ __device__ __forceinline__ void hist_add(uint32_t* sH, uint32_t b, bool agg) {
   if (b != 0xFFFFFFFFu) atomicAdd(&sH[b], 1u);
 }
 
-// One chunk of K1: classify, store ids, histogram; OR every key's bits into
-// `diff` against the item's first key (all equal <=> the item is
-// homogeneous) and, when NANCHK, flag NaNs (|bits| above infinity's).
+// One chunk of K1: classify, store ids, histogram; OR every key's ord into
+// `diff` XOR the item's first key's ord (zero <=> the item is homogeneous;
+// its highest bit is the highest bit in which two keys differ) and, when
+// NANCHK, flag NaNs (|bits| above infinity's).
 // K1 keys per thread per step and resident blocks per SM (register budget):
 // the guess classifier is short and gains from more warps; the search
 // classifiers are chains of dependent table reads and gain from more
 // independent keys per thread.
-__host__ __device__ constexpr int k1_kpt(int cls) { return cls == CLS_GUESS ? 8 : 16; }
-__host__ __device__ constexpr int k1_blocks(int cls) { return cls == CLS_GUESS ? 4 : 3; }
+__host__ __device__ constexpr int k1_kpt(int cls) { return (cls == CLS_GUESS || cls == CLS_RADIX) ? 8 : 16; }
+__host__ __device__ constexpr int k1_blocks(int cls) { return (cls == CLS_GUESS || cls == CLS_RADIX) ? 4 : 3; }
 
 template <int CLS, int DT, bool NANCHK>
 __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const uint64_t* sT, const void* sD,
@@ -178,7 +181,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
       for (int k = 0; k < kK1KPT; ++k) {
         const uint64_t bits = v[k];
         if (NANCHK) nan |= (bits & kAbs) > kInf;
-        diff |= bits ^ first;
+        diff |= ord_of(bits, DT) ^ first;
         const uint32_t b = classify_as<CLS, DT>(bits, c, sT, sD, a.models, a.leaves);
         d[k * kTPB] = (uint16_t)b;
         hist_add(sH, b, c.agg);
@@ -190,7 +193,7 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
         if (idx < len) {
           const uint64_t bits = s[k * kTPB];
           if (NANCHK) nan |= (bits & kAbs) > kInf;
-          diff |= bits ^ first;
+          diff |= ord_of(bits, DT) ^ first;
           b = classify_as<CLS, DT>(bits, c, sT, sD, a.models, a.leaves);
           d[k * kTPB] = (uint16_t)b;
         }
@@ -233,7 +236,8 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
     const uint64_t clen = it.n - c0 < a.chunk_keys ? it.n - c0 : a.chunk_keys;
     const uint64_t* keys = it.buf ? a.keysB : a.keysA;
     uint64_t diff = 0;
-    k1_chunk<CLS, DT, NANCHK>(a, c, sT, sD, sH, keys + it.lo + c0, a.ids + it.lo + c0, clen, keys[it.lo], diff, nan);
+    k1_chunk<CLS, DT, NANCHK>(a, c, sT, sD, sH, keys + it.lo + c0, a.ids + it.lo + c0, clen,
+                              ord_of(keys[it.lo], DT), diff, nan);
     __syncthreads();
     uint32_t* row = a.agg + ch * a.nb_pad_max;
     for (uint32_t j = threadIdx.x; j < c.nb_pad; j += blockDim.x) {
@@ -244,8 +248,13 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
         sH[j] = 0;
       }
     }
-    if (__any_sync(0xFFFFFFFFu, diff != 0) && (threadIdx.x & 31) == 0 && !a.plans[pi].mixed)
-      atomicExch(&a.plans[pi].mixed, 1u);
+    unsigned long long d = diff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d |= __shfl_xor_sync(0xFFFFFFFFu, d, o);
+    if ((threadIdx.x & 31) == 0 && d) {
+      if ((a.plans[pi].odiff | d) != a.plans[pi].odiff) atomicOr(&a.plans[pi].odiff, d);
+      if (!a.plans[pi].mixed) atomicExch(&a.plans[pi].mixed, 1u);
+    }
     __syncthreads();
   }
   if (NANCHK && __syncthreads_or(nan ? 1 : 0) && threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)LS_ENAN);
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
     const uint32_t pi = a.chunk_plan[ch];
     const Plan& pl = a.plans[pi];
     // uniform across the block; items of the buffered scatter are K3b's
-    if ((pl.flags & FLAG_SKIP_SCATTER) || buffered_scatter_ok(pl, a.vbytes)) continue;
+    if ((pl.flags & FLAG_SKIP_SCATTER) || buffered_scatter_ok(pl, rp, a.vbytes)) continue;
     const Item& it = a.items[pi];
     const uint32_t nbk = pl.nb_pad;
     const unsigned long long* ex = a.excl + ch * nbp;
@@ -563,7 +572,7 @@ __global__ void __launch_bounds__(kBufTPB, 2)
     const BufRun rn = runs[ri];
     const Plan& pl = a.plans[rn.plan];
     // uniform across the block; the stable scatter takes the other items
-    if ((pl.flags & FLAG_SKIP_SCATTER) || !buffered_scatter_ok(pl, a.vbytes)) continue;
+    if ((pl.flags & FLAG_SKIP_SCATTER) || !buffered_scatter_ok(pl, rp, a.vbytes)) continue;
     const Item& it = a.items[rn.plan];
     const uint32_t nbk = pl.nb_pad;
     uint64_t* dst = it.buf ? a.outA : a.outB;
@@ -854,8 +863,9 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   const unsigned long long* cnt = a.counts + pl.cnt_off;
   bool eq = pl.decision == LS_DEC_SPLITTER_EQ;
   bool learned = pl.decision == LS_DEC_LEARNED;
+  const bool radix = pl.decision == LS_DEC_RADIX;
   const uint64_t* T = a.pivots + pl.tab_off;
-  bool has_T = pl.cls != CLS_DIRECT;
+  bool has_T = pl.cls != CLS_DIRECT && pl.cls != CLS_RADIX;
   uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
   uint32_t b0 = threadIdx.x * per < nb ? threadIdx.x * per : nb;
   uint32_t b1 = b0 + per < nb ? b0 + per : nb;
@@ -886,6 +896,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     atomicAdd(&ls->items, 1ull);
     atomicAdd(&ls->keys, (unsigned long long)it.n);
     if (learned) atomicAdd(&ls->learned, 1ull);
+    else if (radix) atomicAdd(&ls->radix, 1ull);
     else if (eq) atomicAdd(&ls->splitter_eq, 1ull);
     else atomicAdd(&ls->splitter, 1ull);
     atomicMax(&ls->max_child, tmax);
@@ -894,6 +905,13 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   const bool refine_children = learned && rp.recurse == LS_RECURSE_REFINE_GLOBAL;
   const uint32_t mk = (it.kind == KIND_REFINE) ? it.mk : 0;
   const uint64_t mg = (it.kind == KIND_REFINE) ? it.mg : 0;
+  // Under REFINE_GLOBAL no bucket below a learned item draws a new sample
+  // (LearnedSort 2.0 trains once, Sec. 2.2): a child the model did not split
+  // (no progress), or one that would refine past the FP64 limit, takes the
+  // radix split on the bits where this item's keys differ (they all agree
+  // above bit top_bits); a radix item's children split the next bits down.
+  const uint32_t top_bits = pl.odiff ? 64u - (uint32_t)__clzll((long long)pl.odiff) : 0u;
+  const bool radix_past_limit = refine_children && beyond_refine_limit(rp.B, mk + 2);
   if (noprog) {
     // no-progress guard: redo the same range at the next level with the
     // splitter tree (keys stay where they are).
@@ -913,9 +931,14 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
         Item ch = it;
         ch.level = (uint16_t)(level + 1);
         ch.gidx = it.gidx * nb + bb;
-        ch.kind = KIND_FORCE_SPLITTER;
+        if (radix || refine_children) {
+          ch.kind = KIND_RADIX;
+          ch.mk = (uint16_t)(radix ? pl.dir_shift : top_bits);
+        } else {
+          ch.kind = KIND_FORCE_SPLITTER;
+          ch.mk = 0;
+        }
         ch.model = -1;
-        ch.mk = 0;
         ch.mg = 0;
         if (has_T) {
           if (bb >= 1) ch.ord_lo = T[bb] > it.ord_lo ? T[bb] : it.ord_lo;
@@ -1050,7 +1073,12 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
         if (b >= 1) ch.ord_lo = T[b] > it.ord_lo ? T[b] : it.ord_lo;
         if (b < pl.kmax) ch.ord_hi = T[b + 1] - 1;
       }
-      if (refine_children) {
+      if (radix || radix_past_limit) {
+        ch.kind = KIND_RADIX;
+        ch.model = -1;
+        ch.mk = (uint16_t)(radix ? pl.dir_shift : top_bits);
+        ch.mg = 0;
+      } else if (refine_children) {
         ch.kind = KIND_REFINE;
         ch.model = pl.model;
         ch.mk = (uint16_t)(mk + 1);
@@ -2210,6 +2238,7 @@ int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st
   if (a.cls_mask & (1u << CLS_TREE)) launch_k1_cls<CLS_TREE>(a, rp, st), ++n;
   if (a.cls_mask & (1u << CLS_DIR)) launch_k1_cls<CLS_DIR>(a, rp, st), ++n;
   if (a.cls_mask & (1u << CLS_DIRECT)) launch_k1_cls<CLS_DIRECT>(a, rp, st), ++n;
+  if (a.cls_mask & (1u << CLS_RADIX)) launch_k1_cls<CLS_RADIX>(a, rp, st), ++n;
   return n;
 }
 

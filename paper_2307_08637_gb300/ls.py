@@ -21,7 +21,7 @@ LS_F64, LS_U64 = 0, 1
 LS_PART_AUTO, LS_PART_LEARNED, LS_PART_SPLITTER = 0, 1, 2
 LS_RECURSE_REFINE_GLOBAL, LS_RECURSE_RETRAIN = 0, 1
 LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT, LS_CLASSIFY_GUESS = 0, 1, 2, 3, 4
-LS_DEC_NONE, LS_DEC_LEARNED, LS_DEC_SPLITTER, LS_DEC_SPLITTER_EQ, LS_DEC_HOMOGENEOUS = 0, 1, 2, 3, 4
+LS_DEC_NONE, LS_DEC_LEARNED, LS_DEC_SPLITTER, LS_DEC_SPLITTER_EQ, LS_DEC_HOMOGENEOUS, LS_DEC_RADIX = 0, 1, 2, 3, 4, 5
 LS_MAX_FANOUT = 4096
 LS_MAX_LEVELS = 48
 
@@ -105,7 +105,8 @@ class Model(C.Structure):
 
 
 _LEVEL_FIELDS = ("items", "learned", "splitter", "splitter_eq", "homogeneous", "noprogress", "base_items",
-                 "base_keys", "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys")
+                 "base_keys", "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys",
+                 "radix")
 
 
 class LevelStats(C.Structure):

@@ -12,7 +12,9 @@ directly from the method's steps recomputes them on small inputs:
   (REFINE_GLOBAL) or a new sample (RETRAIN);
 * Sec. 2.4: splitter tree, equality buckets (final, never recursed), the
   no-progress guard (a child holding all of its parent's keys is redone with
-  equality buckets).
+  equality buckets; below a REFINE_GLOBAL model, where no bucket resamples,
+  such a child and one past the FP64 refinement limit take a radix split of
+  the bits in which its keys differ instead).
 
 The recursion uses the oracle only for the RMI fit and its bucket function,
 which have their own pins (closed form, numpy.polyfit); sampling, splitter
@@ -33,7 +35,7 @@ GOLD = 0x9E3779B97F4A7C15
 M64 = (1 << 64) - 1
 REFINE_LIMIT = 2 ** 50
 FIELDS = ["items", "learned", "splitter", "splitter_eq", "homogeneous", "noprogress", "base_items", "base_keys",
-          "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys"]
+          "fallback_items", "fallback_keys", "keys", "max_child", "sumsq_child", "eq_keys", "radix"]
 
 
 def splitmix64(z: int) -> int:
@@ -119,8 +121,16 @@ class Model:
             L["homogeneous"] += 1
             self.terminal += n
             return
+        # the highest bit in which two keys differ, from min and max (an
+        # independent route to the oracle's OR of differences)
+        top = int(u.max() ^ u.min()).bit_length()
         B = p.fanout
         fresh = True
+        if kind == "radix":
+            fresh = False
+            decision = "radix"
+            s = max(mk - 10, 0)
+            rnb = 1 << (mk - s) if mk > s else 2
         if kind == "refine" and B ** (mk + 1) <= REFINE_LIMIT:
             fresh = False
             decision = "learned"
@@ -163,7 +173,10 @@ class Model:
                         bs = min(bs, p.auto_splitter_fanout)
                     t, eq = self.splitters(s_ord, bs, False)
                     decision = "splitter"
-        if decision == "learned":
+        if decision == "radix":
+            ids = ((u >> np.uint64(s)) & np.uint64(rnb - 1)).astype(np.int64)
+            nb, eq = rnb, False
+        elif decision == "learned":
             ids, _ = oracle.classify(model, x, B, mk, mg)
             ids = ids.astype(np.int64)
             nb, eq = B, False
@@ -178,6 +191,8 @@ class Model:
         L["keys"] += n
         if decision == "learned":
             L["learned"] += 1
+        elif decision == "radix":
+            L["radix"] += 1
         elif eq:
             L["splitter_eq"] += 1
         else:
@@ -198,9 +213,15 @@ class Model:
                 self.terminal += sz
                 continue
             clo = lo + int(start[b])
-            if sz == n:
+            refine = decision == "learned" and p.recurse_model == oracle.RECURSE_REFINE_GLOBAL
+            if decision == "radix":
+                self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "radix", None, s, 0)
+            elif refine and (sz == n or B ** (mk + 2) > REFINE_LIMIT):
+                # no sample below a REFINE_GLOBAL model: radix split instead
+                self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "radix", None, top, 0)
+            elif sz == n:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "force_splitter", None, 0, 0)
-            elif decision == "learned" and p.recurse_model == oracle.RECURSE_REFINE_GLOBAL:
+            elif refine:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "refine", model, mk + 1, mg * B + b)
             else:
                 self.item(keys, clo, clo + sz, level + 1, gidx * nb + b, "fresh", None, 0, 0)
@@ -288,3 +309,25 @@ def test_level_statistics_of_a_planted_example():
     assert lv[1]["items"] == 1 and lv[1]["keys"] == 3
     assert lv[1]["base_items"] == 2 and lv[1]["base_keys"] == 4
     assert Model(p).run(x)[1] == lv
+
+
+def test_flat_model_region_takes_the_radix_split():
+    """Keys the model cannot tell apart (two distinct values far beyond the
+    sample range share F, the model's input being clamped to the sample's
+    range) make no progress under REFINE_GLOBAL; the bucket is then split on
+    the bits in which its keys differ, with no new sample, and the split
+    separates the two values."""
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.normal(size=3000), np.full(50, 1e300), np.full(50, np.nextafter(1e300, np.inf))])
+    rng.shuffle(x)
+    p = oracle.params(fanout=1000, basecase_threshold=4, partitioner=oracle.PART_LEARNED, sample_rate=0.1,
+                      min_sample=16)
+    out, rc, tr, _, _ = oracle.sort(x, p)
+    assert rc == 0
+    lv = tr.levels()
+    assert sum(l["radix"] for l in lv) >= 1
+    assert all(l["splitter"] == 0 and l["splitter_eq"] == 0 for l in lv)  # no sample below the root
+    m = Model(p)
+    ref, ref_levels = m.run(x)
+    assert ref_levels == lv and m.terminal == x.size
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
