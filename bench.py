@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-c4", action="store_true", help="leave the C4 batch out of the default line")
     ap.add_argument("--no-c5", action="store_true", help="leave the C5 2e9-key run out of the default line")
     ap.add_argument("--c5-n", type=float, default=2e9, help="C5 keys")
+    ap.add_argument("--classify", default="auto", choices=["auto", "guess", "directory", "tree"],
+                    help="pivot-table evaluation mode of the learned classifier (ls_classify_mode)")
     return ap.parse_args()
 
 
@@ -248,9 +250,12 @@ def run_ours(args):
     inputs = gen_inputs(n, rank_seed(args.seed, rank), dists)
     pristine = [torch.from_numpy(x).to(f"cuda:{dev}") for _, x in inputs]
     work = [torch.empty_like(t) for t in pristine]
-    p_learned = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, basecase_threshold=BASECASE_T)
+    cmode = {"auto": lsg.LS_CLASSIFY_AUTO, "guess": lsg.LS_CLASSIFY_GUESS, "directory": lsg.LS_CLASSIFY_DIRECTORY,
+             "tree": lsg.LS_CLASSIFY_TREE}[args.classify]
+    p_learned = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, basecase_threshold=BASECASE_T,
+                                      classify_mode=cmode)
     p_split = lsg.ls_params_default(flags=lsg.LS_FLAG_TIME_PASSES, partitioner=lsg.LS_PART_SPLITTER,
-                                    basecase_threshold=BASECASE_T)
+                                    basecase_threshold=BASECASE_T, classify_mode=cmode)
     ctx.workspace(n, 1, lsg.LS_F64, p_split)  # allocate once, before timing
 
     def barrier():
