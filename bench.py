@@ -103,8 +103,9 @@ def measured_peak():
 
 
 def ncu_traffic():
-    """DRAM bytes per key of the scatter kernel from the committed ncu summary,
-    only while the kernel source is unchanged since the capture."""
+    """DRAM bytes per key of the buffered scatter kernel (K3b) from the
+    committed ncu summary, only while the kernel source is unchanged since
+    the capture."""
     path = os.path.join(ROOT, "profiles", "scatter_traffic.json")
     src = os.path.join(ROOT, "paper_2307_08637_gb300", "csrc", "ls_partition.cu")
     try:
@@ -299,7 +300,8 @@ def run_ours(args):
     k1_gbs = CLASSIFY_BYTES_PER_KEY * k1["keys"] / (k1["ms"] / 1e3) / 1e9 if k1["ms"] > 0 else None
     tr = ncu_traffic()
     roofline = {
-        "kernel": "k_scatter (K3 stable partition scatter)",
+        "kernel": "k_scatter_buffered (K3b buffered partition scatter: every C2 item is learned under "
+                  "REFINE_GLOBAL or a radix split, so the scatter pass is K3b)",
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
         "bytes_per_key": SCATTER_BYTES_PER_KEY,

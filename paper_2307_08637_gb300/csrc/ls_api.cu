@@ -340,7 +340,7 @@ void ord_range(int dt, uint64_t* lo, uint64_t* hi) {
 
 // Plan and run one batch of items (all at the same level).
 ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, bool record_root,
-                    ls_stats* stats) {
+                    ls_stats* stats, cudaEvent_t ev_children = nullptr) {
   const bool check_nan = level0;
   const ls_params* p = s.p;
   Layout& L = s.lay;
@@ -702,6 +702,9 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
                                     pa.excl, nbp_max, st);
   launch_children(ca, s.rp, st);
   s.timer.end();
+  // the level's counters and next items are final once K2 is done: the
+  // host may read them back while the scatters run
+  if (ev_children) CK(cudaEventRecord(ev_children, st));
   s.timer.begin(LS_PASS_SCATTER, batch_keys);
   launch_scatter(pa, s.rp, st);
   launch_scatter_buffered(pa, s.rp, at<BufRun>(s.ws, L.o_bruns), (uint32_t)bruns.size(), st);
@@ -850,6 +853,8 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     CK(cudaStreamSynchronize(st));
   }
 
+  if (!ctx->s_read) CK(cudaStreamCreateWithFlags(&ctx->s_read, cudaStreamNonBlocking));
+  if (!ctx->ev_children) CK(cudaEventCreateWithFlags(&ctx->ev_children, cudaEventDisableTiming));
   bool first = true;
   uint32_t level = 0;
   ls_status result = LS_OK;
@@ -872,13 +877,17 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
         ++b1;
       }
       bool record = first && b0 == 0 && out_stats && cur[0].segment == 0;
-      ls_status r = run_batch(s, cur.data() + b0, (uint32_t)(b1 - b0), level == 0, record, stats);
+      ls_status r = run_batch(s, cur.data() + b0, (uint32_t)(b1 - b0), level == 0, record, stats,
+                              b1 == cur.size() ? ctx->ev_children : nullptr);
       if (r != LS_OK) return r;
       first = false;
       b0 = b1;
     }
     // one readback per level: counters, device status and the first
-    // kPinItems next-level items (K2 wrote them), into page-locked memory
+    // kPinItems next-level items (K2 wrote them), into page-locked memory,
+    // on the side stream once the level's last K2 is done (the scatters
+    // keep the GPU busy meanwhile; the status of the scatters themselves is
+    // read with the final statistics)
     LevelCounters c;
     unsigned int dstat = 0;
     const uint64_t pin_items = std::min<uint64_t>(kPinItems, lay.icap);
@@ -892,11 +901,13 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
         ctx->h_pin_bytes = need;
       }
       char* hp = static_cast<char*>(ctx->h_pin);
-      CK(cudaMemcpyAsync(hp, d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(hp + sizeof(LevelCounters), ctx->d_status, sizeof dstat, cudaMemcpyDeviceToHost, st));
+      cudaStream_t rs = ctx->s_read;
+      CK(cudaStreamWaitEvent(rs, ctx->ev_children, 0));
+      CK(cudaMemcpyAsync(hp, d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, rs));
+      CK(cudaMemcpyAsync(hp + sizeof(LevelCounters), ctx->d_status, sizeof dstat, cudaMemcpyDeviceToHost, rs));
       CK(cudaMemcpyAsync(hp + sizeof(LevelCounters) + 16, at<Item>(ws, lay.o_next), pin_items * sizeof(Item),
-                         cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+                         cudaMemcpyDeviceToHost, rs));
+      CK(cudaStreamSynchronize(rs));
       memcpy(&c, hp, sizeof c);
       memcpy(&dstat, hp + sizeof(LevelCounters), sizeof dstat);
     }
@@ -917,8 +928,8 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
       memcpy(items.data(), static_cast<char*>(ctx->h_pin) + sizeof(LevelCounters) + 16, first * sizeof(Item));
       if (c.n_next > first) {
         CK(cudaMemcpyAsync(items.data() + first, at<Item>(ws, lay.o_next) + first, (c.n_next - first) * sizeof(Item),
-                           cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+                           cudaMemcpyDeviceToHost, ctx->s_read));
+        CK(cudaStreamSynchronize(ctx->s_read));
       }
     }
     ls_status r = finish_spans(s, c);
@@ -939,7 +950,10 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   CK(cudaMemcpyAsync(hs.data(), d_stats, LS_MAX_LEVELS * sizeof(DevLevelStats), cudaMemcpyDeviceToHost, st));
   Plan rp0;
   if (s.root_copied) CK(cudaMemcpyAsync(&rp0, at<Plan>(ws, lay.o_rootplan), sizeof(Plan), cudaMemcpyDeviceToHost, st));
+  unsigned int fstat = 0;  // the last level's scatters and base cases report here
+  CK(cudaMemcpyAsync(&fstat, ctx->d_status, sizeof fstat, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (result == LS_OK && fstat != 0) result = (ls_status)fstat;
   if (s.root_copied) {
     if (s.root_n > 0 && !rp0.mixed) {
       // homogeneity is checked before any model is built (Sec. 2.2): the
@@ -1047,8 +1061,9 @@ void ls_destroy(ls_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_cache) cudaFree(ctx->d_cache);
-  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out})
+  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out, ctx->s_read})
     if (s) cudaStreamDestroy(s);
+  if (ctx->ev_children) cudaEventDestroy(ctx->ev_children);
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
   delete ctx;
 }

@@ -28,9 +28,12 @@ struct ls_ctx {
   // streams of ls_sort_host_batch (created on first use): sort, host->device,
   // device->host
   cudaStream_t s_sort = nullptr, s_in = nullptr, s_out = nullptr;
-  // page-locked host buffer for the per-level readback of the sort
+  // page-locked host buffer for the per-level readback of the sort, the
+  // stream it is read on and the event (end of a level's K2) it waits for
   void* h_pin = nullptr;
   size_t h_pin_bytes = 0;
+  cudaStream_t s_read = nullptr;
+  cudaEvent_t ev_children = nullptr;
   // autotuner results, keyed by dtype * 64 + floor(log2 n)
   std::map<int, ls_tuned_entry> tuned;
   std::mutex tuned_mu;

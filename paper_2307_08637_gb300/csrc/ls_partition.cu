@@ -531,8 +531,9 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
 // run's first chunk when the run starts inside it).  Complete lines leave as
 // whole 64-byte writes; only the first and last line of a region are written
 // in part.  Per tile: phase A puts each key that falls in its bucket's
-// buffered line into the buffer and lists the lines that complete; after a
-// barrier the listed lines are written (four lanes per line) and their line
+// buffered line into the buffer and lists the lines that complete (the key
+// that fills a line's last slot appends it); after a barrier the listed
+// lines are written (four lanes per line) and their line
 // ends advanced; after a second barrier phase B places the keys past the
 // buffered line (whole lines straight out, the new partial line into the
 // buffer).  Phase B of one tile and phase A of the next touch different
@@ -561,7 +562,6 @@ __global__ void __launch_bounds__(kBufTPB, 2)
   __shared__ uint32_t s_nfl[2];
   __shared__ unsigned long long s_run;
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
   bool bad = false;
   for (;;) {
     __syncthreads();  // the previous run is done with the block's buffers
@@ -633,17 +633,10 @@ __global__ void __launch_bounds__(kBufTPB, 2)
         } else if (b != 0xFFFFu) {
           bad = true;  // K1 and K3 disagree
         }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, f);
-        if (m) {
-          const int ld = __ffs(m) - 1;
-          uint32_t base = 0;
-          if ((int)lane == ld) base = atomicAdd(&s_nfl[par], (uint32_t)__popc(m));
-          base = __shfl_sync(0xFFFFFFFFu, base, ld);
-          if (f) {
-            const uint32_t q = base + __popc(m & lt);
-            fb[q] = (uint16_t)b;
-            fe[q] = e;
-          }
+        if (f) {  // about one key in eight: a plain atomic append is cheaper than a warp vote per key
+          const uint32_t q = atomicAdd(&s_nfl[par], 1u);
+          fb[q] = (uint16_t)b;
+          fe[q] = e;
         }
       }
       __syncthreads();
