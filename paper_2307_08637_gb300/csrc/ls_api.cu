@@ -739,8 +739,8 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
     if (c.n_base_small)
       launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st);
     if (c.n_base_large)
-      launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb, s.VA, s.VBb,
-                        s.vb, s.dt, s.st);
+      s.launches += launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb,
+                                      s.VA, s.VBb, s.vb, s.dt, s.st) - 1;
     if (c.n_fallback)
       launch_fallback(at<Span>(s.ws, L.o_fb), c.n_fallback, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st);
     s.timer.end();

@@ -266,8 +266,9 @@ void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st)
 // values of a key-value sort (vb = 4 or 8 bytes; 0 for keys only).
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
                        uint32_t vb, int dt, cudaStream_t st);
-void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
-                       const void* VBuf, uint32_t vb, int dt, cudaStream_t st);
+// Returns the kernels launched (one per span size class).
+int launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                      const void* VBuf, uint32_t vb, int dt, cudaStream_t st);
 void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
                        uint32_t vb, cudaStream_t st);
 void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,

@@ -1772,16 +1772,17 @@ constexpr uint32_t kLargeTPB = 256;
 constexpr int kLargeR = 16;  // keys per thread: spans of up to 4096 keys
 constexpr uint32_t kMaxSlotL = 32;
 
+template <int RR>
 __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
                                                   uint64_t* sk, uint32_t* sc, uint32_t* red) {
   const uint32_t n = s.n, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr uint32_t kW = kLargeTPB / 32;
   const uint32_t R = (n + kLargeTPB - 1) / kLargeTPB;
   const uint64_t* src = (s.buf ? Bbuf : A) + s.lo;
-  uint64_t u[kLargeR];
+  uint64_t u[RR];
   uint32_t hmin = ~0u, hmax = 0;
 #pragma unroll
-  for (int r = 0; r < kLargeR; ++r) {
+  for (int r = 0; r < RR; ++r) {
     const uint32_t i = tid + kLargeTPB * r;
     u[r] = i < n ? ord_of(src[i], dt) : 0ull;
     if (i < n) {
@@ -1806,11 +1807,11 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
     __syncthreads();
   };
   block_minmax(hmin, hmax);
-  uint32_t w[kLargeR];
+  uint32_t w[RR];
   if (hmin == hmax) {  // uniform: one high word, exact low-word extremes
     uint32_t lmin = ~0u, lmax = 0;
 #pragma unroll
-    for (int r = 0; r < kLargeR; ++r)
+    for (int r = 0; r < RR; ++r)
       if (tid + kLargeTPB * r < n) {
         lmin = min(lmin, (uint32_t)u[r]);
         lmax = max(lmax, (uint32_t)u[r]);
@@ -1823,19 +1824,19 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
     }
     const uint32_t sh = __clz(lmax - lmin);
 #pragma unroll
-    for (int r = 0; r < kLargeR; ++r) w[r] = ((uint32_t)u[r] - lmin) << sh;
+    for (int r = 0; r < RR; ++r) w[r] = ((uint32_t)u[r] - lmin) << sh;
   } else {
     const uint64_t base = (uint64_t)hmin << 32;
     const uint32_t sh = __clz(hmax - hmin);
 #pragma unroll
-    for (int r = 0; r < kLargeR; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
+    for (int r = 0; r < RR; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
   }
   const uint32_t NS = kLargeTPB * R;
   for (uint32_t i = tid; i < NS; i += kLargeTPB) sc[i] = 0;
   __syncthreads();
-  uint32_t at[kLargeR], rk[kLargeR];
+  uint32_t at[RR], rk[RR];
 #pragma unroll
-  for (int r = 0; r < kLargeR; ++r) {
+  for (int r = 0; r < RR; ++r) {
     const uint32_t slot = __umulhi(w[r], NS), owner = w[r] >> 24;
     at[r] = (slot - owner * R) * kLargeTPB + owner;
     rk[r] = tid + kLargeTPB * r < n ? atomicAdd(&sc[at[r]], 1u) : 0u;
@@ -1844,7 +1845,7 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
   // exclusive scan of the slot counts in slot order (thread t: slots tR..tR+R-1)
   uint32_t loc = 0, big = 0;
 #pragma unroll
-  for (int q = 0; q < kLargeR; ++q)
+  for (int q = 0; q < RR; ++q)
     if ((uint32_t)q < R) {
       const uint32_t c = sc[q * kLargeTPB + tid];
       loc += c;
@@ -1869,23 +1870,23 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
   if (bmax > kMaxSlotL) return false;  // uniform across the block
   uint32_t run = before + incl - loc;
 #pragma unroll
-  for (int q = 0; q < kLargeR; ++q)
+  for (int q = 0; q < RR; ++q)
     if ((uint32_t)q < R) {
       const uint32_t c = sc[q * kLargeTPB + tid];
       sc[q * kLargeTPB + tid] = run | (c << 16);  // slot start and count
       run += c;
     }
   __syncthreads();
-  uint32_t e[kLargeR];
+  uint32_t e[RR];
 #pragma unroll
-  for (int r = 0; r < kLargeR; ++r) {
+  for (int r = 0; r < RR; ++r) {
     e[r] = tid + kLargeTPB * r < n ? sc[at[r]] : 0u;
     if (tid + kLargeTPB * r < n) sk[(e[r] & 0xFFFFu) + rk[r]] = u[r];
   }
   __syncthreads();
   // a key's place: its slot's start plus the keys of the slot before it
 #pragma unroll
-  for (int r = 0; r < kLargeR; ++r) {
+  for (int r = 0; r < RR; ++r) {
     const uint32_t a0 = e[r] & 0xFFFFu, cn = e[r] >> 16, me = a0 + rk[r];
     uint32_t p = a0;
 #pragma unroll 4
@@ -1897,7 +1898,7 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kLargeR; ++r)
+  for (int r = 0; r < RR; ++r)
     if (tid + kLargeTPB * r < n) sk[e[r]] = u[r];
   __syncthreads();
   for (uint32_t i = tid; i < n; i += kLargeTPB) A[s.lo + i] = unord(sk[i], dt);
@@ -1907,9 +1908,15 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
 
 // Spans of kWarpSortMax+1 .. T keys: the placed block sort, else (clustered
 // spans, or spans above 4096 keys) a bitonic network over P = 2^ceil(log2 n)
-// keys in shared memory.  sk holds cap keys, then 4096 slot words.
-__global__ void __launch_bounds__(kLargeTPB, 2) k_base_large(const Span* spans, uint64_t n, uint64_t* A,
-                                                             const uint64_t* Bbuf, int dt, uint32_t cap) {
+// keys in shared memory.  sk holds cap keys, then the slot words.  One
+// instance per size class (spans in (lo, hi]): RR keys per thread held in
+// registers, so the classes of shorter spans use fewer registers and run
+// more blocks per SM; each instance walks the whole list and takes its own
+// spans.
+template <int RR, int MINB>
+__global__ void __launch_bounds__(kLargeTPB, MINB) k_base_large(const Span* spans, uint64_t n, uint64_t* A,
+                                                                const uint64_t* Bbuf, int dt, uint32_t cap,
+                                                                uint32_t lo, uint32_t hi) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
@@ -1917,7 +1924,8 @@ __global__ void __launch_bounds__(kLargeTPB, 2) k_base_large(const Span* spans, 
   __shared__ uint32_t red[2 * (kLargeTPB / 32)];
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
-    if (s.n <= kLargeTPB * kLargeR && block_placed_sort(s, A, Bbuf, dt, sm, sc, red)) continue;
+    if (s.n <= lo || s.n > hi) continue;  // another class's span (uniform across the block)
+    if (s.n <= kLargeTPB * RR && block_placed_sort<RR>(s, A, Bbuf, dt, sm, sc, red)) continue;
     const uint64_t* src = s.buf ? Bbuf : A;
     uint32_t P = 2;
     while (P < s.n) P <<= 1;
@@ -2315,26 +2323,40 @@ static void launch_large(F* f, const Span* spans, uint64_t n, uint32_t P, size_t
   pdl_launch(f, (unsigned)grid, tpb, sm, st, spans, n, A, Bbuf, VA, VBuf, dt);
 }
 
-void launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
-                       const void* VBuf, uint32_t vb, int dt, cudaStream_t st) {
-  if (!n) return;
+int launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
+                      const void* VBuf, uint32_t vb, int dt, cudaStream_t st) {
+  if (!n) return 0;
   uint32_t P = 2;
   while (P < max_len) P <<= 1;
   if (vb) {  // (key, index) pairs: 12 bytes per slot
     static size_t set8[64] = {}, set4[64] = {};
     if (vb == 8) launch_large(k_base_large_kv<8>, spans, n, P, (size_t)P * 12, st, set8, A, Bbuf, VA, VBuf, dt);
     else launch_large(k_base_large_kv<4>, spans, n, P, (size_t)P * 12, st, set4, A, Bbuf, VA, VBuf, dt);
-    return;
+    return 1;
   }
-  const uint32_t cap = P > kLargeTPB * kLargeR ? P : kLargeTPB * kLargeR;
-  size_t sm = (size_t)cap * 8 + (size_t)kLargeTPB * kLargeR * 4;
-  static size_t set[64] = {};
-  allow_smem(k_base_large, sm, set);
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_base_large, kLargeTPB, sm);
-  if (per < 1) per = 1;
-  uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
-  pdl_launch(k_base_large, (unsigned)grid, kLargeTPB, sm, st, spans, n, A, Bbuf, dt, cap);
+  int launched = 0;
+  // size classes (kWarpSortMax, 1024], (1024, 2048], (2048, max_len]
+  auto run = [&](auto kern, uint32_t rr, uint32_t lo, uint32_t hi, size_t* set) {
+    if (hi <= lo) return;
+    uint32_t Pc = 2;
+    while (Pc < hi) Pc <<= 1;
+    const uint32_t cap = Pc > kLargeTPB * rr ? Pc : kLargeTPB * rr;
+    const size_t sm = (size_t)cap * 8 + (size_t)kLargeTPB * rr * 4;
+    allow_smem(kern, sm, set);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLargeTPB, sm);
+    if (per < 1) per = 1;
+    const uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
+    pdl_launch(kern, (unsigned)grid, kLargeTPB, sm, st, spans, n, A, Bbuf, dt, cap, lo, hi);
+    ++launched;
+  };
+  static size_t set4[64] = {}, set8[64] = {}, set16[64] = {};
+  const uint32_t top = max_len > kWarpSortMax ? max_len : kWarpSortMax;
+  run(k_base_large<4, 4>, 4, kWarpSortMax, top < 1024 ? top : 1024, set4);
+  run(k_base_large<8, 3>, 8, 1024, top < 2048 ? top : 2048, set8);
+  run(k_base_large<16, 2>, 16, 2048, top, set16);
+  (void)P;
+  return launched;
 }
 
 void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
