@@ -116,6 +116,15 @@ typedef struct {
  * floor(log2 n) (of the mean segment length for ls_sort_segmented), when
  * there is one; ls_workspace_size applies the same substitution. */
 #define LS_FLAG_TUNED 2u
+/* ls_params.flags: plan every recursion level on the host (one readback per
+ * level).  By default, when buckets below the root are refined rather than
+ * resampled (REFINE_GLOBAL, partitioner not LS_PART_SPLITTER, keys only,
+ * fanout <= 1024, not LS_CLASSIFY_DIRECTORY), the levels below the root are
+ * planned on the device from a device work queue and run as one CUDA graph
+ * (launched batch by batch from the host when LS_FLAG_TIME_PASSES is set);
+ * buckets that do draw a sample are planned on the host.  Results are
+ * identical either way. */
+#define LS_FLAG_HOST_LEVELS 4u
 
 /* The trained two-layer RMI (all FP64), as exported by ls_fit. */
 typedef struct {
@@ -199,10 +208,13 @@ ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dty
 /* Sort d_keys[0..n) ascending by ord (the sorting problem of Sec. 1-2).
  * d_keys must be 8-byte aligned (LS_EINVAL otherwise).  In place from the
  * caller's view; the library ping-pongs through d_workspace
- * (>= ls_workspace_size bytes, 256-byte aligned).  Stream
- * ordered; the call synchronises `stream` between recursion levels, so it
- * returns after the sort is complete.  out_stats (nullable) receives the
- * decisions and per-level statistics. */
+ * (>= ls_workspace_size bytes, 256-byte aligned).  Stream ordered.  The root
+ * level is planned on the host (it waits once for the root's Alg. 5
+ * decision); the levels below run from a device work queue as one CUDA
+ * graph (see LS_FLAG_HOST_LEVELS for when, and for the per-level host
+ * planner used otherwise); the call returns after the sort is complete,
+ * with one readback of the statistics at the end.  out_stats (nullable)
+ * receives the decisions and per-level statistics. */
 ls_status ls_sort(ls_ctx* ctx, void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p, void* d_workspace,
                   size_t ws_bytes, ls_stats* out_stats, ls_stream_t stream);
 
@@ -294,7 +306,7 @@ ls_status ls_fit_grad(ls_ctx* ctx, const ls_model* model, const void* d_sorted_s
  * pivot tables of the last call, is fully rewritten by each call, and is
  * shared by all calls: calls that overlap on the GPU race, so serialise them.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).
  * Fanouts up to LS_MAX_FANOUT fit; a model that needs more scratch than the
  * array holds is rejected with LS_ENOMEM.  Synchronous on `stream`. */
 ls_status ls_classify_static(const ls_model* model, const void* d_keys, uint64_t n, ls_dtype dtype, uint32_t k,

@@ -18,7 +18,7 @@ from .ls import (  # noqa: F401
     LS_OK, LS_EINVAL, LS_ENOMEM, LS_ENAN, LS_ETIMEOUT, LS_ECUDA, LS_ENOTIMPL, LS_EDEVICE,
     LS_F64, LS_U64, LS_PART_AUTO, LS_PART_LEARNED, LS_PART_SPLITTER, LS_RECURSE_REFINE_GLOBAL,
     LS_RECURSE_RETRAIN, LS_CLASSIFY_AUTO, LS_CLASSIFY_DIRECTORY, LS_CLASSIFY_TREE, LS_CLASSIFY_DIRECT, LS_CLASSIFY_GUESS,
-    LS_FLAG_TIME_PASSES, LS_FLAG_TUNED, PASS_NAMES, PassTime,
+    LS_FLAG_HOST_LEVELS, LS_FLAG_TIME_PASSES, LS_FLAG_TUNED, PASS_NAMES, PassTime,
     LS_DEC_NONE, LS_DEC_LEARNED, LS_DEC_SPLITTER, LS_DEC_SPLITTER_EQ, LS_DEC_HOMOGENEOUS, LS_DEC_RADIX, LS_MAX_FANOUT,
 )
 

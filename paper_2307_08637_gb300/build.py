@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblearnedsort.so")
-SOURCES = ["ls_api.cu", "ls_fit.cu", "ls_partition.cu", "ls_static.cu", "ls_tune.cu"]
+SOURCES = ["ls_api.cu", "ls_fit.cu", "ls_partition.cu", "ls_queue.cu", "ls_static.cu", "ls_tune.cu"]
 HEADERS = ["ls_common.cuh", "ls_kernels.h", "ls_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no FMA contraction anywhere; the model arithmetic also uses

@@ -41,7 +41,6 @@ void lsg::set_error_detail(const char* fmt, ...) {
 
 namespace {
 
-constexpr uint32_t kBatchItems = 2048;
 constexpr uint64_t kPinItems = 4096;  // next-level items read back with the level counters
 constexpr uint32_t kDirBits = 13;
 constexpr size_t kAlign = 256;
@@ -152,7 +151,7 @@ struct Layout {
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
       o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_ids,
-      o_vbuf, o_bruns;
+      o_vbuf, o_bruns, o_bitems, o_hostq, o_reflist, o_bdesc, o_queue;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
 };
@@ -229,6 +228,13 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.brun_cap = kBatchItems + 4096;
   l.o_bruns = take(l.brun_cap * sizeof(BufRun));
   l.o_chunkplan = take(l.chunk_cap * 4);
+  // device-planned levels: the batch's items, items handed back to the
+  // host, the pivot list, the batch descriptor and the queue state
+  l.o_bitems = take((size_t)kBatchItems * sizeof(Item));
+  l.o_hostq = take(l.icap * sizeof(Item));
+  l.o_reflist = take((size_t)kBatchItems * 4);
+  l.o_bdesc = take(sizeof(BatchDesc));
+  l.o_queue = take(sizeof(QueueState));
   l.misc_bytes = 16 * (kBatchItems + 8) * 8;
   l.o_misc = take(l.misc_bytes);
   l.total = off;
@@ -574,7 +580,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   if (any_guess) aux = std::max<uint32_t>(aux, L.L * (uint32_t)sizeof(FLeaf));
 
   // ---- partition passes
-  PassArgs pa;
+  PassArgs pa{};
   pa.items = d_items;
   pa.plans = d_plans;
   pa.nitems = nitems;
@@ -654,7 +660,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   s.launches += launch_classify_hist(pa, s.rp, st);
   s.timer.end();
 
-  ChildArgs ca;
+  ChildArgs ca{};
   ca.items = d_items;
   ca.plans = d_plans;
   ca.nitems = nitems;
@@ -705,11 +711,22 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   // the level's counters and next items are final once K2 is done: the
   // host may read them back while the scatters run
   if (ev_children) CK(cudaEventRecord(ev_children, st));
+  // The stable scatter is launched only when some item may need it: an item
+  // whose decision already makes it order-free (a radix item, or a learned
+  // item under REFINE_GLOBAL) is always taken by K3b.
+  bool need_stable = false;
+  for (uint32_t i = 0; i < nitems && !need_stable; ++i) {
+    const Plan& q = dplans[i];
+    const bool always_buffered =
+        buffered_scatter_candidate(q, s.vb) &&
+        (q.decision == LS_DEC_RADIX || (q.decision == LS_DEC_LEARNED && s.rp.recurse == LS_RECURSE_REFINE_GLOBAL));
+    need_stable = !always_buffered;
+  }
   s.timer.begin(LS_PASS_SCATTER, batch_keys);
-  launch_scatter(pa, s.rp, st);
+  if (need_stable) launch_scatter(pa, s.rp, st);
   launch_scatter_buffered(pa, s.rp, at<BufRun>(s.ws, L.o_bruns), (uint32_t)bruns.size(), st);
   s.timer.end();
-  s.launches += (tiles ? 2 : 1) + (bruns.empty() ? 0 : 1);
+  s.launches += 1 + (tiles && need_stable ? 1 : 0) + (bruns.empty() ? 0 : 1);
   CK(cudaGetLastError());
 
   if (record_root && stats) {
@@ -752,6 +769,311 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
   }
   s.launches += (c.n_base_small > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
   CK(cudaGetLastError());
+  return LS_OK;
+}
+
+// ---- device-planned levels (ls_queue.cu)
+//
+// Every level below the root is planned on the device when no bucket below
+// the root can draw a sample: REFINE_GLOBAL (learned items refine the root's
+// model, the others take the radix split), keys only (K3b takes every item),
+// at most kBufMaxBuckets buckets, a classify mode without the radix
+// directory, and a partitioner that is not the splitter tree everywhere.
+// Items that do draw a sample (below a splitter tree) come back to the host
+// planner.
+bool device_levels_ok(const ls_params* p, uint32_t vb) {
+  return vb == 0 && !(p->flags & LS_FLAG_HOST_LEVELS) && p->recurse_model == LS_RECURSE_REFINE_GLOBAL &&
+         p->partitioner != LS_PART_SPLITTER && p->classify_mode != LS_CLASSIFY_DIRECTORY &&
+         pow2ceil(p->fanout) <= kBufMaxBuckets;
+}
+
+constexpr unsigned long long kMaxLoopIter = 1ull << 16;  // batches of one device loop (a safety bound)
+constexpr size_t kMaxGraphs = 8;                         // graphs kept per context
+
+// The kernels of one device-planned batch on stream st: planner, count
+// reset, exact pivots, K1, chunk prefixes, K2, K3b, the finished spans and
+// the loop control.  h: the graph's loop condition (0 outside a graph).  tm:
+// pass timer (nullptr: untimed).  Returns the kernels launched.
+uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHandle h, PassTimer* tm) {
+  Layout& L = s.lay;
+  const ls_params* p = s.p;
+  const uint32_t nbp = std::max<uint32_t>(pow2ceil(p->fanout), 1u << kRadixBits);
+  BatchDesc* bd = at<BatchDesc>(s.ws, L.o_bdesc);
+  QueueState* q = at<QueueState>(s.ws, L.o_queue);
+  LevelCounters* ctr = at<LevelCounters>(s.ws, L.o_ctr);
+  Item* bitems = at<Item>(s.ws, L.o_bitems);
+  Plan* plans = at<Plan>(s.ws, L.o_plans);
+  unsigned long long* counts = at<unsigned long long>(s.ws, L.o_counts);
+  unsigned long long* cursors = at<unsigned long long>(s.ws, L.o_cursors);
+  uint64_t* pivots = at<uint64_t>(s.ws, L.o_pivots);
+  DModel* models = at<DModel>(s.ws, L.o_models);
+  Leaf* leaves = at<Leaf>(s.ws, L.o_leaves);
+  auto tb = [&](int cls) {
+    if (tm) tm->begin(cls, 0);
+  };
+  auto te = [&]() {
+    if (tm) tm->end();
+  };
+  uint64_t nl = 0;
+
+  PlanArgs pg{};
+  pg.level = at<Item>(s.ws, L.o_cur);
+  pg.next = at<Item>(s.ws, L.o_next);
+  pg.bitems = bitems;
+  pg.plans = plans;
+  pg.hostq = at<Item>(s.ws, L.o_hostq);
+  pg.icap = L.icap;
+  pg.chunk_plan = at<uint32_t>(s.ws, L.o_chunkplan);
+  pg.chunk_cap = L.chunk_cap;
+  pg.segs = at<ChunkSeg>(s.ws, L.o_segs);
+  pg.seg_cap = L.seg_cap;
+  pg.multi = at<uint2>(s.ws, L.o_multi);
+  pg.runs = at<BufRun>(s.ws, L.o_bruns);
+  pg.run_cap = L.brun_cap;
+  pg.reflist = at<uint32_t>(s.ws, L.o_reflist);
+  pg.bd = bd;
+  pg.q = q;
+  pg.ctr = ctr;
+  pg.chunk_ctr = at<unsigned long long>(s.ws, L.o_chunkctr);
+  pg.status = s.ctx->d_status;
+  pg.nbc = L.nbc;
+  pg.cells = L.cells;
+  pg.slots = 2ull * buffered_scatter_slots();
+  tb(LS_PASS_CHILDREN);
+  launch_plan_batch(pg, s.rp, st);
+  launch_zero_counts(bd, plans, counts, st);
+  te();
+  nl += 2;
+
+  tb(LS_PASS_PIVOTS);
+  launch_learned_pivots(plans, bitems, pg.reflist, kBatchItems, pow2ceil(p->fanout), models, leaves, pivots, s.rp, st,
+                        bd);
+  te();
+  nl += 1;
+
+  const bool guess = p->classify_mode == LS_CLASSIFY_AUTO || p->classify_mode == LS_CLASSIFY_GUESS;
+  PassArgs pa{};
+  pa.items = bitems;
+  pa.plans = plans;
+  pa.nitems = kBatchItems;
+  pa.nchunks = L.chunk_cap;  // bounds the grids; the count is the planner's
+  pa.keysA = s.A;
+  pa.keysB = s.Bb;
+  pa.outA = s.A;
+  pa.outB = s.Bb;
+  pa.pivots = pivots;
+  pa.dirs = at<uint16_t>(s.ws, L.o_dirs);
+  pa.models = models;
+  pa.leaves = leaves;
+  pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
+  pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
+  pa.aux_bytes = guess ? std::max<uint32_t>(16, L.L * (uint32_t)sizeof(FLeaf)) : 16;
+  pa.cls_mask = (1u << CLS_DIRECT) | (1u << CLS_RADIX) | (guess ? 1u << CLS_GUESS : 0u) |
+                (p->classify_mode == LS_CLASSIFY_TREE ? 1u << CLS_TREE : 0u);
+  pa.ids = at<uint16_t>(s.ws, L.o_ids);
+  pa.counts = counts;
+  pa.cursors = cursors;
+  pa.agg = at<uint32_t>(s.ws, L.o_agg);
+  pa.excl = at<unsigned long long>(s.ws, L.o_excl);
+  pa.chunk_ctr = pg.chunk_ctr;
+  pa.chunk_plan = pg.chunk_plan;
+  pa.chunk_keys = kChunkKeys;
+  pa.status = s.ctx->d_status;
+  pa.check_nan = 0;
+  pa.nb_pad_max = nbp;
+  pa.dir_cells_max = L.cells;
+  pa.bd = bd;
+  tb(LS_PASS_CLASSIFY);
+  nl += launch_classify_hist(pa, s.rp, st);
+  te();
+
+  ChildArgs ca{};
+  ca.items = bitems;
+  ca.plans = plans;
+  ca.nitems = kBatchItems;  // the grid; the count is the planner's
+  ca.pivots = pivots;
+  ca.counts = counts;
+  ca.cursors = cursors;
+  ca.next = at<Item>(s.ws, L.o_next);
+  ca.next_cap = L.icap;
+  ca.base_small = at<Span>(s.ws, L.o_small);
+  ca.base_large = at<Span>(s.ws, L.o_large);
+  ca.base_cap = L.base_cap;
+  ca.large_cap = L.large_cap;
+  ca.copy = at<Span>(s.ws, L.o_copy);
+  ca.copy_cap = L.copy_cap;
+  ca.fallback = at<Span>(s.ws, L.o_fb);
+  ca.fallback_cap = L.fb_cap;
+  ca.ctr = ctr;
+  ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
+  ca.bd = bd;
+  tb(LS_PASS_CHILDREN);
+  nl += launch_chunk_prefix(pg.segs, (uint32_t)std::min<uint64_t>(L.seg_cap, 1024), pg.multi, 256, plans, pa.agg,
+                            pa.excl, nbp, st, bd);
+  launch_children(ca, s.rp, st);
+  te();
+  nl += 1;
+
+  tb(LS_PASS_SCATTER);
+  launch_scatter_buffered(pa, s.rp, pg.runs, (uint32_t)L.brun_cap, st);
+  te();
+  nl += 1;
+
+  tb(LS_PASS_BASE);
+  nl += launch_spans_device(ctr, ca.base_small, ca.base_large, ca.copy, ca.fallback, L.base_cap,
+                            p->basecase_threshold, s.A, s.Bb, s.dt, st);
+  te();
+  launch_loop_ctl(q, ctr, s.ctx->d_status, h, kMaxLoopIter, st);
+  nl += 1;
+  return nl;
+}
+
+// What a captured graph depends on: the workspace, the keys, the layout and
+// the run parameters (every kernel argument derives from these).
+std::vector<uint64_t> graph_key(const Sorter& s) {
+  const Layout& L = s.lay;
+  const RunParams& r = s.rp;
+  uint64_t sr, df, tau;
+  memcpy(&sr, &r.sample_rate, 8);
+  memcpy(&df, &r.dup_frac, 8);
+  memcpy(&tau, &r.tau, 8);
+  return {(uint64_t)(uintptr_t)s.ws, (uint64_t)(uintptr_t)s.A, (uint64_t)(uintptr_t)s.ctx->d_status, L.n, L.total,
+          L.icap, L.chunk_cap, L.seg_cap, L.brun_cap, L.base_cap, L.large_cap, L.copy_cap, L.fb_cap, L.nbc, L.cells,
+          L.L, r.B, r.bs_max, r.bs_auto, r.T, r.max_depth, r.min_sample, sr, df, tau, r.min_learned_n, r.seed,
+          (uint64_t)(uint32_t)r.partitioner, (uint64_t)(uint32_t)r.recurse, (uint64_t)(uint32_t)r.classify_mode,
+          (uint64_t)(uint32_t)r.dt, r.tile, r.dir_bits};
+}
+
+void drop_graph(ls_graph_entry& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.graph) cudaGraphDestroy(e.graph);
+  e.exec = nullptr;
+  e.graph = nullptr;
+}
+
+// Build (capture) the graph of the device level loop: a while node whose
+// body is one batch.  plain: launch the body's kernels without the
+// programmatic-serialization attribute.  Returns false if any step fails
+// (the error is cleared; the caller launches the batches from the host).
+bool build_graph(Sorter& s, bool plain, ls_graph_entry* out) {
+  ls_ctx* ctx = s.ctx;
+  if (!ctx->s_cap && cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ls_graph_entry e;
+  bool ok = cudaGraphCreate(&e.graph, 0) == cudaSuccess;
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNode_t node = nullptr;
+  union NodeParams {  // the runtime's parameter union has no default constructor
+    cudaGraphNodeParams p;
+    unsigned char raw[sizeof(cudaGraphNodeParams)];
+    NodeParams() { memset(raw, 0, sizeof raw); }
+  } npu;
+  cudaGraphNodeParams& np = npu.p;
+  ok = ok && cudaGraphConditionalHandleCreate(&h, e.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, e.graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+         cudaSuccess;
+    if (ok) {
+      const bool was = t_plain_launch;
+      t_plain_launch = plain;
+      e.body_launches = launch_device_batch(s, ctx->s_cap, h, nullptr);
+      t_plain_launch = was;
+      cudaGraph_t got = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(ctx->s_cap, &got);
+      ok = ce == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(&e.exec, e.graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    drop_graph(e);
+    return false;
+  }
+  *out = e;
+  return true;
+}
+
+// Run the device level loop until the queue is empty; then one readback.
+// handed_back: items that draw a sample (for the host planner).
+ls_status run_device_levels(Sorter& s, std::vector<Item>* handed_back, bool* overflow, unsigned int* dstat) {
+  Layout& L = s.lay;
+  ls_ctx* ctx = s.ctx;
+  cudaStream_t st = s.st;
+  QueueState* q = at<QueueState>(s.ws, L.o_queue);
+  BatchDesc* bd = at<BatchDesc>(s.ws, L.o_bdesc);
+  CK(cudaMemsetAsync(q, 0, sizeof(QueueState), st));
+  ls_graph_entry* ge = nullptr;
+  if (!s.timer.on) {
+    const std::vector<uint64_t> key = graph_key(s);
+    for (ls_graph_entry& e : ctx->graphs)
+      if (e.key == key) ge = &e;
+    if (!ge) {
+      if (ctx->graphs.size() >= kMaxGraphs) {
+        size_t old = 0;
+        for (size_t i = 1; i < ctx->graphs.size(); ++i)
+          if (ctx->graphs[i].last_use < ctx->graphs[old].last_use) old = i;
+        drop_graph(ctx->graphs[old]);
+        ctx->graphs.erase(ctx->graphs.begin() + (long)old);
+      }
+      ls_graph_entry e;
+      if (build_graph(s, false, &e) || build_graph(s, true, &e)) {
+        e.key = key;
+        ctx->graphs.push_back(e);
+        ge = &ctx->graphs.back();
+      }
+    }
+  }
+  uint64_t iters = 0;
+  if (ge) {
+    ge->last_use = ++ctx->graph_clock;
+    CK(cudaGraphLaunch(ge->exec, st));
+  } else {
+    // launched from the host, one batch at a time (pass timing, or no graph)
+    for (;;) {
+      const size_t r0 = s.timer.recs.size();
+      s.launches += launch_device_batch(s, st, 0, s.timer.on ? &s.timer : nullptr);
+      QueueState hq;
+      BatchDesc hb;
+      CK(cudaMemcpyAsync(&hq, q, sizeof hq, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&hb, bd, sizeof hb, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (size_t i = r0; i < s.timer.recs.size(); ++i)
+        if (s.timer.recs[i].cls == LS_PASS_CLASSIFY || s.timer.recs[i].cls == LS_PASS_SCATTER)
+          s.timer.recs[i].keys = hb.keys;
+      if (!hq.cont) break;
+    }
+  }
+  QueueState hq;
+  LevelCounters c;
+  CK(cudaMemcpyAsync(&hq, q, sizeof hq, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&c, at<LevelCounters>(s.ws, L.o_ctr), sizeof c, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(dstat, ctx->d_status, sizeof *dstat, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  iters = hq.iter;
+  if (ge) s.launches += ge->body_launches * iters;
+  *overflow = c.overflow != 0;
+  if (hq.err) {
+    lsg::set_error_detail("device level loop stopped after %llu batches", (unsigned long long)iters);
+    return LS_EDEVICE;
+  }
+  handed_back->clear();
+  const uint64_t nh = std::min<uint64_t>(hq.host_n, L.icap);
+  if (nh) {
+    handed_back->resize(nh);
+    CK(cudaMemcpyAsync(handed_back->data(), at<Item>(s.ws, L.o_hostq), nh * sizeof(Item), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+  }
   return LS_OK;
 }
 
@@ -858,6 +1180,7 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   bool first = true;
   uint32_t level = 0;
   ls_status result = LS_OK;
+  const bool dev_levels = device_levels_ok(p, vb);
   while (!items.empty()) {
     CK(cudaMemsetAsync(d_ctr, 0, sizeof(LevelCounters), st));
     // items of this level are replaced by the device list of the next level,
@@ -882,6 +1205,28 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
       if (r != LS_OK) return r;
       first = false;
       b0 = b1;
+    }
+    if (dev_levels) {
+      // the next level's items and this level's finished spans stay on the
+      // device: the device loop plans and sorts everything below; items
+      // that draw a sample come back and are planned here
+      bool ovf = false;
+      unsigned int dstat = 0;
+      ls_status r = run_device_levels(s, &items, &ovf, &dstat);
+      if (r != LS_OK) return r;
+      if (ovf) {
+        lsg::set_error_detail("workspace list capacity exceeded below level %u", level);
+        return LS_ENOMEM;
+      }
+      if (dstat != 0) {
+        result = (ls_status)dstat;
+        break;
+      }
+      // every item of the device queue is done: no model is referenced
+      s.model_free.clear();
+      for (int m = (int)lay.mcap - 1; m >= 0; --m) s.model_free.push_back(m);
+      ++level;
+      continue;
     }
     // one readback per level: counters, device status and the first
     // kPinItems next-level items (K2 wrote them), into page-locked memory,
@@ -1061,7 +1406,8 @@ void ls_destroy(ls_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_cache) cudaFree(ctx->d_cache);
-  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out, ctx->s_read})
+  for (ls_graph_entry& e : ctx->graphs) drop_graph(e);
+  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out, ctx->s_read, ctx->s_cap})
     if (s) cudaStreamDestroy(s);
   if (ctx->ev_children) cudaEventDestroy(ctx->ev_children);
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -16,6 +17,16 @@ struct ls_tuned_entry {
   double sample_rate = 0.0;
   int32_t recurse_model = 0;
   double ms = 0.0;  // sort time of the winner when it was tuned
+};
+
+// An instantiated CUDA graph of the device level loop (a while node around
+// one batch's kernels), for the workspace, keys array and parameters in key.
+struct ls_graph_entry {
+  std::vector<uint64_t> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t body_launches = 0;  // kernels per loop iteration
+  uint64_t last_use = 0;
 };
 
 struct ls_ctx {
@@ -34,6 +45,11 @@ struct ls_ctx {
   size_t h_pin_bytes = 0;
   cudaStream_t s_read = nullptr;
   cudaEvent_t ev_children = nullptr;
+  // graphs of the device level loop (a few, least recently used first out)
+  // and the stream they are captured on
+  std::vector<ls_graph_entry> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t s_cap = nullptr;
   // autotuner results, keyed by dtype * 64 + floor(log2 n)
   std::map<int, ls_tuned_entry> tuned;
   std::mutex tuned_mu;

@@ -826,15 +826,13 @@ constexpr int kPivotRounds = 96;
 // ones are packed again, so the FP64 pipe (the bound here) runs full warps
 // instead of warps in which a few lanes gallop.  Other blocks search per
 // thread.
-__global__ void __launch_bounds__(kPivotTPB) k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
-                                                              uint32_t nlist, uint32_t nb_pad, const DModel* models,
-                                                              const Leaf* leaves, uint64_t* __restrict__ pivots,
-                                                              RunParams rp) {
-  pdl_wait();
+__device__ __forceinline__ void pivots_block(uint64_t blk, Plan* plans, const Item* items, const uint32_t* list,
+                                             uint32_t nlist, uint32_t nb_pad, const DModel* models,
+                                             const Leaf* leaves, uint64_t* __restrict__ pivots, const RunParams& rp) {
   __shared__ PivotPrep s_prep;
   __shared__ PivotWork s_w[2][kPivotTPB];
   __shared__ uint32_t s_n[2];
-  const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t g = blk * (uint64_t)blockDim.x + threadIdx.x;
   const bool pooled = nb_pad % blockDim.x == 0;
   if (pooled) {  // uniform: the whole block is in range and in one item
     if (g >= (uint64_t)nlist * nb_pad) return;
@@ -898,6 +896,22 @@ __global__ void __launch_bounds__(kPivotTPB) k_learned_pivots(Plan* plans, const
   if (threadIdx.x < s_n[cur]) {
     const PivotWork& x = s_w[cur][threadIdx.x];
     T[x.j] = search_pivot(ev, x.L, x.H, x.t, x.vL, x.vH);
+  }
+}
+
+// Blocks of nb_pad / blockDim.x pivot slots per listed item.  With bd (a
+// device-planned batch) the list length is read on the device and the grid
+// strides over the blocks.
+__global__ void __launch_bounds__(kPivotTPB) k_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
+                                                              uint32_t nlist, uint32_t nb_pad, const DModel* models,
+                                                              const Leaf* leaves, uint64_t* __restrict__ pivots,
+                                                              RunParams rp, const BatchDesc* bd) {
+  pdl_wait();
+  if (bd) nlist = bd->nrefine;
+  const uint64_t nblk = ((uint64_t)nlist * nb_pad + blockDim.x - 1) / blockDim.x;
+  for (uint64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    pivots_block(blk, plans, items, list, nlist, nb_pad, models, leaves, pivots, rp);
+    __syncthreads();  // the block's shared search pool is reused by its next block of slots
   }
 }
 
@@ -1390,12 +1404,20 @@ void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slot
 
 void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,
                            const DModel* models, const Leaf* leaves, uint64_t* pivots, const RunParams& rp,
-                           cudaStream_t st) {
+                           cudaStream_t st, const BatchDesc* bd) {
+  // with bd, nlist bounds the list length read on the device
   if (!nlist) return;
   uint64_t n = (uint64_t)nlist * nb_pad;
   const uint32_t tpb = nb_pad >= kPivotTPB ? kPivotTPB : 128;  // pooled blocks when tpb divides nb_pad
-  pdl_launch(k_learned_pivots, grid_for(n, tpb), tpb, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots,
-             rp);
+  unsigned grid = grid_for(n, tpb);
+  if (bd) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned g8 = (unsigned)(sms > 0 ? sms : 1) * 8;
+    grid = grid < g8 ? grid : g8;
+  }
+  pdl_launch(k_learned_pivots, grid, tpb, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots, rp, bd);
 }
 
 void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,

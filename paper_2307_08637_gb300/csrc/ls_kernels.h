@@ -19,6 +19,9 @@ void set_error_detail(const char* fmt, ...);
 // first statement (pdl_wait) blocks until that kernel has finished and its
 // writes are visible, so the stream order of the data is unchanged and only
 // the launch latency between dependent kernels is hidden.
+// t_plain_launch (this thread) turns the attribute off, e.g. while a graph
+// is captured on a stream where it is not wanted.
+inline thread_local bool t_plain_launch = false;
 template <typename... KArgs, typename... Args>
 inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args... args) {
@@ -31,7 +34,7 @@ inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = t_plain_launch ? 0 : 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
@@ -58,6 +61,34 @@ struct RunParams {
   int32_t dt;             // 0 f64, 1 u64
   uint32_t tile;          // keys per partition tile
   uint32_t dir_bits;      // log2 of directory cells
+};
+
+// ---- device-planned batches (ls_queue.cu)
+// The work of one batch that the planner kernel laid out on the device.
+// Kernels of a device-planned batch read their counts from here (a null
+// pointer: the host passed the counts by value).
+struct BatchDesc {
+  unsigned long long nchunks;     // chunks of the batch
+  unsigned long long chunk_keys;  // keys per chunk
+  unsigned long long keys;        // keys of the batch's items
+  unsigned int nitems;            // items (plans) of the batch
+  unsigned int nsegs, nmulti;     // chunk runs; items with several runs
+  unsigned int nruns;             // buffered-scatter runs
+  unsigned int nrefine;           // items whose exact pivots are searched
+  unsigned int pad;
+};
+
+// The device work queue of the level loop: the current level's items (a
+// prefix of which has been planned), the next level's items (appended by
+// K2), and the items handed back to the host because they draw a sample.
+struct QueueState {
+  unsigned long long cur_n;   // items of the current level
+  unsigned long long head;    // first item of the current level not yet planned
+  unsigned long long host_n;  // items handed back to the host
+  unsigned long long iter;    // loop iterations so far
+  unsigned int cont;          // 1 while work remains (mirrors the graph's loop condition)
+  unsigned int err;           // 1: the loop stopped at its iteration limit
+  unsigned long long pad[2];
 };
 
 // ---- generic helpers (ls_partition.cu)
@@ -128,7 +159,7 @@ void launch_fmodel_for_fit(const FitArgs& a, cudaStream_t st);
 // list of plan indices; thread per (item, j < nb_pad).
 void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,
                            const DModel* models, const Leaf* leaves, uint64_t* pivots, const RunParams& rp,
-                           cudaStream_t st);
+                           cudaStream_t st, const BatchDesc* bd = nullptr);  // bd: list length from the device
 // Sample-bucket maximum under the RMI (imbalance test) for fit candidates.
 void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,
                       cudaStream_t st, uint64_t* launches);
@@ -145,6 +176,9 @@ void launch_fit_grad(const DModel* model, const Leaf* leaves, const uint64_t* sa
                      double* pred, double* resid, double* grad_a, double* grad_b, double* grad_root,
                      void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t fit_grad_scratch_bytes(uint64_t S, uint32_t L);
+
+// Items per batch (per-item tables in the workspace are sized for this many).
+constexpr uint32_t kBatchItems = 2048;
 
 // ---- partition passes (ls_partition.cu)
 struct PassArgs {
@@ -179,7 +213,13 @@ struct PassArgs {
   int check_nan;
   uint32_t nb_pad_max;
   uint32_t dir_cells_max;
+  const BatchDesc* bd;          // device-planned batch: counts from here (nullptr: nchunks / chunk_keys above)
 };
+// Chunk count and chunk size of the batch a kernel works on.
+__host__ __device__ inline uint64_t batch_chunks(const PassArgs& a) { return a.bd ? a.bd->nchunks : a.nchunks; }
+__host__ __device__ inline uint64_t batch_chunk_keys(const PassArgs& a) {
+  return a.bd ? a.bd->chunk_keys : a.chunk_keys;
+}
 int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st);  // returns launches
 // A batch with fewer chunks than this gets smaller chunks (about two per
 // resident K1/K3 block on a 152-SM part; a constant so that workspace sizes
@@ -200,7 +240,8 @@ struct ChunkSeg {
 // run count per such item), a scan of the run totals and the carries.
 // Returns launches.
 int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
-                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st);
+                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st,
+                        const BatchDesc* bd = nullptr);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
 
 // Buffered scatter (K3b).  An item none of whose descendants ever draws a
@@ -234,7 +275,38 @@ static_assert(sizeof(BufRun) == 32, "BufRun layout");
 // runs per block).
 uint32_t buffered_scatter_slots();
 void launch_scatter_buffered(const PassArgs& a, const RunParams& rp, const BufRun* runs, uint32_t nruns,
-                             cudaStream_t st);
+                             cudaStream_t st);  // a.bd: the run count is read from the device
+
+// The planner of a device-planned batch (ls_queue.cu).
+struct PlanArgs {
+  Item* level;                   // the current level's items (cur_n of them)
+  const Item* next;              // the next level's items, appended by K2 (n_next of them)
+  Item* bitems;                  // the batch's items
+  Plan* plans;                   // the batch's plans
+  Item* hostq;                   // items handed back to the host
+  uint64_t icap;                 // capacity of level, next and hostq
+  uint32_t* chunk_plan;          // per chunk: its item in the batch
+  uint64_t chunk_cap;
+  ChunkSeg* segs;                // runs of kSegChunks chunks
+  uint64_t seg_cap;
+  uint2* multi;                  // items with several chunk runs: (first run, runs)
+  BufRun* runs;                  // buffered-scatter runs
+  uint64_t run_cap;
+  uint32_t* reflist;             // items whose exact pivots are searched
+  BatchDesc* bd;
+  QueueState* q;
+  LevelCounters* ctr;
+  unsigned long long* chunk_ctr;  // the scatters' work counters (zeroed)
+  unsigned int* status;
+  uint32_t nbc;                  // per-item stride of the count / cursor / pivot tables
+  uint32_t cells;                // directory cells per item
+  uint64_t slots;                // buffered-scatter run slots (two per resident block)
+};
+void launch_plan_batch(const PlanArgs& a, const RunParams& rp, cudaStream_t st);
+void launch_zero_counts(const BatchDesc* bd, const Plan* plans, unsigned long long* counts, cudaStream_t st);
+// max_iter bounds the loop; h = 0 outside a graph (the flag in q is read by the host).
+void launch_loop_ctl(QueueState* q, LevelCounters* ctr, const unsigned int* status, cudaGraphConditionalHandle h,
+                     unsigned long long max_iter, cudaStream_t st);
 
 struct ChildArgs {
   const Item* items;
@@ -255,6 +327,7 @@ struct ChildArgs {
   uint64_t fallback_cap;
   LevelCounters* ctr;
   DevLevelStats* stats;
+  const BatchDesc* bd;  // device-planned batch: item count from here (the grid covers kBatchItems)
 };
 void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st);
 
@@ -273,6 +346,11 @@ void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_
                        uint32_t vb, cudaStream_t st);
 void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
                      int dt, cudaStream_t st);
+// The same for keys only, with the span count read from the device (dn);
+// n_max bounds it (grid sizing).  Returns the kernels launched.
+int launch_spans_device(const LevelCounters* ctr, const Span* small, const Span* large, const Span* copy,
+                        const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A, uint64_t* Bbuf, int dt,
+                        cudaStream_t st);
 
 // ls_classify helpers
 void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,

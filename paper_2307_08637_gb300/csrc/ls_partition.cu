@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
   int32_t aux_model = -1;
   Cls c;
   bool nan = false;
-  for (uint64_t ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
+  const uint64_t nch = batch_chunks(a), ckeys = batch_chunk_keys(a);
+  for (uint64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
     const uint32_t pi = a.chunk_plan[ch];
     if (a.plans[pi].cls != CLS) continue;  // uniform across the block
     if (pi != cur) {
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(kTPB, k1_blocks(CLS)) k_classify_hist(PassArgs
     }
     const Item& it = a.items[pi];
     const Plan& pl = a.plans[pi];
-    const uint64_t c0 = (ch - pl.chunk_begin) * a.chunk_keys;
-    const uint64_t clen = it.n - c0 < a.chunk_keys ? it.n - c0 : a.chunk_keys;
+    const uint64_t c0 = (ch - pl.chunk_begin) * ckeys;
+    const uint64_t clen = it.n - c0 < ckeys ? it.n - c0 : ckeys;
     const uint64_t* keys = it.buf ? a.keysB : a.keysA;
     uint64_t diff = 0;
     k1_chunk<CLS, DT, NANCHK>(a, c, sT, sD, sH, keys + it.lo + c0, a.ids + it.lo + c0, clen,
@@ -338,11 +339,12 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
   const unsigned lt = (1u << lane) - 1u;
   for (uint32_t j = threadIdx.x; j < (kW / 2) * nbp; j += TPB) wcnt[j] = 0;
   bool oob = false;
+  const uint64_t nch = batch_chunks(a), ckeys = batch_chunk_keys(a);
   for (int par = 0;; par ^= 1) {
     if (threadIdx.x == 0) s_chunk[par] = atomicAdd(a.chunk_ctr, 1ull);
     __syncthreads();
     const uint64_t ch = s_chunk[par];
-    if (ch >= a.nchunks) break;
+    if (ch >= nch) break;
     const uint32_t pi = a.chunk_plan[ch];
     const Plan& pl = a.plans[pi];
     // uniform across the block; items of the buffered scatter are K3b's
@@ -355,8 +357,8 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
       sCnt[b] = 0;
       sLs[b] = 0;
     }
-    const uint64_t c0 = (ch - pl.chunk_begin) * a.chunk_keys;
-    const uint64_t clen = it.n - c0 < a.chunk_keys ? it.n - c0 : a.chunk_keys;
+    const uint64_t c0 = (ch - pl.chunk_begin) * ckeys;
+    const uint64_t clen = it.n - c0 < ckeys ? it.n - c0 : ckeys;
     const uint64_t* src = (it.buf ? a.keysB : a.keysA) + it.lo + c0;
     const uint16_t* idin = a.ids + it.lo + c0;
     uint64_t* dst = it.buf ? a.outA : a.outB;
@@ -563,6 +565,8 @@ __global__ void __launch_bounds__(kBufTPB, 2)
   __shared__ unsigned long long s_run;
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   bool bad = false;
+  const uint64_t ckeys = batch_chunk_keys(a);
+  if (a.bd) nruns = a.bd->nruns;
   for (;;) {
     __syncthreads();  // the previous run is done with the block's buffers
     if (threadIdx.x == 0) s_run = atomicAdd(a.chunk_ctr + 1, 1ull);
@@ -580,12 +584,12 @@ __global__ void __launch_bounds__(kBufTPB, 2)
     const uint16_t* ids = a.ids + it.lo;
     const uint64_t ab = (uint64_t)(uintptr_t)dst >> 3;  // dst[0] as a key address
     const uint64_t alo = ab + it.lo, ahi = alo + it.n;    // the item's destination
-    const uint64_t ch = rn.off / a.chunk_keys;            // the run's first chunk (item-relative)
+    const uint64_t ch = rn.off / ckeys;                   // the run's first chunk (item-relative)
     const unsigned long long* ex = a.excl + (pl.chunk_begin + ch) * a.nb_pad_max;
     for (uint32_t b = threadIdx.x; b < nbk; b += kBufTPB) cur[b] = 0;
     if (threadIdx.x == 0) s_nfl[0] = s_nfl[1] = 0;
     __syncthreads();
-    for (uint64_t i = ch * a.chunk_keys + threadIdx.x; i < rn.off; i += kBufTPB) {
+    for (uint64_t i = ch * ckeys + threadIdx.x; i < rn.off; i += kBufTPB) {
       const uint32_t b = ids[i];
       if (b < nbk) atomicAdd(&cur[b], 1u);
       else bad = true;
@@ -703,21 +707,24 @@ __global__ void __launch_bounds__(kBufTPB, 2)
 // run's first row when the item has several runs (that row is read only by
 // the thread that owns the column, before it is written).
 __global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans, uint32_t* agg,
-                               unsigned long long* __restrict__ excl, uint32_t nbp) {
+                               unsigned long long* __restrict__ excl, uint32_t nbp, const BatchDesc* bd) {
   pdl_wait();
-  const ChunkSeg sg = segs[blockIdx.x];
-  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
-  if (b >= plans[sg.plan].nb_pad) return;
-  uint32_t v[kSegChunks];
+  const uint32_t ns = bd ? bd->nsegs : gridDim.x;
+  for (uint32_t si = blockIdx.x; si < ns; si += gridDim.x) {
+    const ChunkSeg sg = segs[si];
+    const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+    if (b >= plans[sg.plan].nb_pad) continue;
+    uint32_t v[kSegChunks];
 #pragma unroll
-  for (uint32_t j = 0; j < kSegChunks; ++j) v[j] = j < sg.nch ? agg[(sg.c0 + j) * nbp + b] : 0u;
-  unsigned long long run = 0;
+    for (uint32_t j = 0; j < kSegChunks; ++j) v[j] = j < sg.nch ? agg[(sg.c0 + j) * nbp + b] : 0u;
+    unsigned long long run = 0;
 #pragma unroll
-  for (uint32_t j = 0; j < kSegChunks; ++j) {
-    if (j < sg.nch) excl[(sg.c0 + j) * nbp + b] = run;
-    run += v[j];
+    for (uint32_t j = 0; j < kSegChunks; ++j) {
+      if (j < sg.nch) excl[(sg.c0 + j) * nbp + b] = run;
+      run += v[j];
+    }
+    agg[sg.c0 * nbp + b] = (uint32_t)run;  // at most kSegChunks * kChunkKeys
   }
-  agg[sg.c0 * nbp + b] = (uint32_t)run;  // at most kSegChunks * kChunkKeys
 }
 
 // Carry scan: for each item with several runs and each bucket column, the
@@ -725,37 +732,44 @@ __global__ void k_chunk_prefix(const ChunkSeg* __restrict__ segs, const Plan* __
 // the run's first row becomes the keys of that bucket in the item's earlier
 // runs).  One thread per column; the loads of eight runs are issued together.
 __global__ void k_run_scan(const uint2* __restrict__ multi, const ChunkSeg* __restrict__ segs,
-                           const Plan* __restrict__ plans, uint32_t* agg, uint32_t nbp) {
+                           const Plan* __restrict__ plans, uint32_t* agg, uint32_t nbp, const BatchDesc* bd) {
   pdl_wait();
-  const uint2 mi = multi[blockIdx.x];  // (first run, number of runs)
-  const ChunkSeg f = segs[mi.x];
-  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
-  if (b >= plans[f.plan].nb_pad) return;
-  const uint64_t c0 = f.c0;
-  uint32_t run = 0;
-  for (uint32_t r0 = 0; r0 < mi.y; r0 += 8) {
-    uint32_t t[8];
+  const uint32_t nm = bd ? bd->nmulti : gridDim.x;
+  for (uint32_t mi_ = blockIdx.x; mi_ < nm; mi_ += gridDim.x) {
+    const uint2 mi = multi[mi_];  // (first run, number of runs)
+    const ChunkSeg f = segs[mi.x];
+    const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+    if (b >= plans[f.plan].nb_pad) continue;
+    const uint64_t c0 = f.c0;
+    uint32_t run = 0;
+    for (uint32_t r0 = 0; r0 < mi.y; r0 += 8) {
+      uint32_t t[8];
 #pragma unroll
-    for (uint32_t k = 0; k < 8; ++k)
-      t[k] = r0 + k < mi.y ? agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] : 0u;
+      for (uint32_t k = 0; k < 8; ++k)
+        t[k] = r0 + k < mi.y ? agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] : 0u;
 #pragma unroll
-    for (uint32_t k = 0; k < 8; ++k) {
-      if (r0 + k < mi.y) agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] = run;
-      run += t[k];
+      for (uint32_t k = 0; k < 8; ++k) {
+        if (r0 + k < mi.y) agg[(c0 + (uint64_t)(r0 + k) * kSegChunks) * nbp + b] = run;
+        run += t[k];
+      }
     }
   }
 }
 
 // Carry pass: add each run's carry (from k_run_scan) to its chunks.
 __global__ void k_chunk_carry(const ChunkSeg* __restrict__ segs, const Plan* __restrict__ plans,
-                              const uint32_t* __restrict__ agg, unsigned long long* __restrict__ excl, uint32_t nbp) {
+                              const uint32_t* __restrict__ agg, unsigned long long* __restrict__ excl, uint32_t nbp,
+                              const BatchDesc* bd) {
   pdl_wait();
-  const ChunkSeg sg = segs[blockIdx.x];
-  if (blockIdx.x == sg.first) return;
-  const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
-  if (b >= plans[sg.plan].nb_pad) return;
-  const unsigned long long carry = agg[sg.c0 * nbp + b];
-  for (uint32_t j = 0; j < sg.nch; ++j) excl[(sg.c0 + j) * nbp + b] += carry;
+  const uint32_t ns = bd ? bd->nsegs : gridDim.x;
+  for (uint32_t si = blockIdx.x; si < ns; si += gridDim.x) {
+    const ChunkSeg sg = segs[si];
+    if (si == sg.first) continue;
+    const uint32_t b = blockIdx.y * blockDim.x + threadIdx.x;
+    if (b >= plans[sg.plan].nb_pad) continue;
+    const unsigned long long carry = agg[sg.c0 * nbp + b];
+    for (uint32_t j = 0; j < sg.nch; ++j) excl[(sg.c0 + j) * nbp + b] += carry;
+  }
 }
 
 // ------------------------------------------------------------------ K2
@@ -820,12 +834,14 @@ enum { L_NEXT = 0, L_SMALL, L_LARGE, L_COPY, L_FALLBACK, L_N };
 __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams rp) {
   pdl_wait();
   uint32_t pi = blockIdx.x;
+  if (a.bd && pi >= a.bd->nitems) return;  // device-planned batch: the grid covers the largest batch
   const Item& it = a.items[pi];
   Plan& pl = a.plans[pi];
   __shared__ uint32_t s32[kK2Warps * L_N];
   __shared__ unsigned long long s64[kK2Warps * 6];
   __shared__ unsigned long long smax[kK2Warps];
   __shared__ unsigned long long s_base[L_N];
+  __shared__ uint32_t s_bb, s_nf[kK2Threads + 1];
   uint32_t level = it.level;
   uint32_t cl = level + 1 < LS_MAX_LEVELS ? level + 1 : LS_MAX_LEVELS - 1;
   DevLevelStats* ls = a.stats + (level < LS_MAX_LEVELS ? level : LS_MAX_LEVELS - 1);
@@ -872,7 +888,10 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     sc1[0] += (uint32_t)sz;
     mxc = sz > mxc ? sz : mxc;
     sq[0] += sz * sz;
-    if (sz == it.n && !(eq && (b & 1))) sq[1] = 1;
+    if (sz == it.n && !(eq && (b & 1))) {
+      sq[1] = 1;
+      s_bb = b;  // the one bucket that holds the whole item
+    }
   }
   for (int d = 16; d > 0; d >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, mxc, d);
@@ -911,9 +930,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     if (threadIdx.x == 0) {
       pl.flags |= FLAG_SKIP_SCATTER | FLAG_NOPROGRESS;
       atomicAdd(&ls->noprogress, 1ull);
-      uint32_t bb = 0;
-      for (uint32_t b = 0; b < nb; ++b)
-        if (cnt[b] == it.n) bb = b;
+      const uint32_t bb = s_bb;
       if (level + 1 > rp.max_depth) {
         atomicAdd(&cs->fallback_items, 1ull);
         atomicAdd(&cs->fallback_keys, (unsigned long long)it.n);
@@ -961,6 +978,46 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     if (threadIdx.x == 0) s_start[nb] = it.n;
   }
   __syncthreads();
+  // s_nf[t]: the first non-final bucket at or after thread t's range (nb if
+  // none), so that a run of final buckets finds its end without a serial
+  // walk over the run
+  if (dest == 1) {
+    uint32_t f = nb;
+    for (uint32_t b = b0; b < b1; ++b)
+      if (!s_fin[b]) {
+        f = b;
+        break;
+      }
+    s_nf[threadIdx.x] = f;
+    if (threadIdx.x == 0) s_nf[kK2Threads] = nb;
+    __syncthreads();
+    if (threadIdx.x < 32) {  // suffix minimum, one warp over kK2Threads / 32 entries per lane
+      constexpr uint32_t kPer = kK2Threads / 32;
+      uint32_t loc[kPer], m = nb;
+#pragma unroll
+      for (int i = kPer - 1; i >= 0; --i) {
+        m = min(m, s_nf[threadIdx.x * kPer + i]);
+        loc[i] = m;
+      }
+      uint32_t suf = m;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_down_sync(0xFFFFFFFFu, suf, d);
+        if (threadIdx.x + d < 32) suf = min(suf, o);
+      }
+      uint32_t after = __shfl_down_sync(0xFFFFFFFFu, suf, 1);
+      if (threadIdx.x == 31) after = nb;
+#pragma unroll
+      for (int i = 0; i < (int)kPer; ++i) s_nf[threadIdx.x * kPer + i] = min(loc[i], after);
+    }
+    __syncthreads();
+  }
+  // end of the run of final buckets that starts at b (b in this thread's range)
+  auto run_end = [&](uint32_t b) {
+    for (uint32_t e = b + 1; e < b1; ++e)
+      if (!s_fin[e]) return e;
+    return s_nf[threadIdx.x + 1];
+  };
   // count list entries: base case / fallback / next level per non-final
   // bucket; one copy run per maximal run of final buckets (only when the
   // destination is the workspace buffer)
@@ -971,8 +1028,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     if (eq && (b & 1)) eqk += sz;
     if (s_fin[b]) {
       if (dest == 1 && (b == 0 || !s_fin[b - 1])) {
-        uint32_t e = b + 1;
-        while (e < nb && s_fin[e]) ++e;
+        const uint32_t e = run_end(b);
         uint64_t len = s_start[e] - s_start[b];
         nl[L_COPY] += (uint32_t)((len + kCopyPiece - 1) / kCopyPiece);
       }
@@ -1029,8 +1085,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     uint64_t clo = it.lo + s_start[b];
     if (s_fin[b]) {
       if (dest == 1 && (b == 0 || !s_fin[b - 1])) {
-        uint32_t e = b + 1;
-        while (e < nb && s_fin[e]) ++e;
+        const uint32_t e = run_end(b);
         uint64_t len = s_start[e] - s_start[b];
         for (uint64_t off = 0; off < len; off += kCopyPiece) {
           uint64_t pl_len = len - off < kCopyPiece ? len - off : kCopyPiece;
@@ -1366,8 +1421,9 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
 }
 
 __global__ void __launch_bounds__(kTPB, 4) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
-                                                     int dt) {
+                                                     int dt, const unsigned long long* dn) {
   pdl_wait();
+  if (dn) n = *dn;  // span count written on the device
   __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
   __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
   const unsigned wid = threadIdx.x >> 5;
@@ -1916,8 +1972,10 @@ __device__ __forceinline__ bool block_placed_sort(const Span& s, uint64_t* A, co
 template <int RR, int MINB>
 __global__ void __launch_bounds__(kLargeTPB, MINB) k_base_large(const Span* spans, uint64_t n, uint64_t* A,
                                                                 const uint64_t* Bbuf, int dt, uint32_t cap,
-                                                                uint32_t lo, uint32_t hi) {
+                                                                uint32_t lo, uint32_t hi,
+                                                                const unsigned long long* dn) {
   pdl_wait();
+  if (dn) n = *dn;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem);
   uint32_t* sc = reinterpret_cast<uint32_t*>(sm + cap);
@@ -1937,8 +1995,10 @@ __global__ void __launch_bounds__(kLargeTPB, MINB) k_base_large(const Span* span
   }
 }
 
-__global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf) {
+__global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
+                             const unsigned long long* dn) {
   pdl_wait();
+  if (dn) n = *dn;
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
     for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) A[s.lo + i] = Bbuf[s.lo + i];
@@ -1949,8 +2009,9 @@ __global__ void k_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const u
 // the other buffer (bitonic runs of 2048 in shared memory, then merge-path
 // passes), leaving the result in A.
 __global__ void __launch_bounds__(1024) k_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
-                                                   int dt) {
+                                                   int dt, const unsigned long long* dn) {
   pdl_wait();
+  if (dn) n = *dn;
   __shared__ uint64_t sm[kSortChunk];
   for (uint64_t w = blockIdx.x; w < n; w += gridDim.x) {
     Span s = spans[w];
@@ -2244,13 +2305,16 @@ int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st
 }
 
 int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
-                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st) {
+                        const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st,
+                        const BatchDesc* bd) {
+  // with bd the counts are read on the device and nsegs / nmulti bound the
+  // grids (each block strides over the runs)
   if (!nsegs) return 0;
   const unsigned cols = (nbp + kTPB - 1) / kTPB;
-  pdl_launch(k_chunk_prefix, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp);
+  pdl_launch(k_chunk_prefix, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp, bd);
   if (!nmulti) return 1;
-  pdl_launch(k_run_scan, dim3(nmulti, cols), kTPB, 0, st, multi, segs, plans, agg, nbp);
-  pdl_launch(k_chunk_carry, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp);
+  pdl_launch(k_run_scan, dim3(nmulti, cols), kTPB, 0, st, multi, segs, plans, agg, nbp, bd);
+  pdl_launch(k_chunk_carry, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp, bd);
   return 3;
 }
 
@@ -2311,7 +2375,8 @@ void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_
   if (blocks > cap) blocks = cap;
   if (vb == 8) pdl_launch(k_base_small_kv<8>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
   else if (vb == 4) pdl_launch(k_base_small_kv<4>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
-  else pdl_launch(k_base_small, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt);
+  else pdl_launch(k_base_small, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt,
+                  static_cast<const unsigned long long*>(nullptr));
 }
 
 template <typename F>
@@ -2321,6 +2386,34 @@ static void launch_large(F* f, const Span* spans, uint64_t n, uint32_t P, size_t
   uint32_t tpb = P >= 1024 ? 1024 : (P < 64 ? 64 : P);
   uint64_t grid = n < (uint64_t)sm_count() * 8 ? n : (uint64_t)sm_count() * 8;
   pdl_launch(f, (unsigned)grid, tpb, sm, st, spans, n, A, Bbuf, VA, VBuf, dt);
+}
+
+// Keys-only block base case in three size classes, (kWarpSortMax, 1024],
+// (1024, 2048], (2048, max_len]; n bounds the grid, dn (when set) holds the
+// span count on the device.
+static int launch_large_classes(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf,
+                                int dt, const unsigned long long* dn, cudaStream_t st) {
+  int launched = 0;
+  auto run = [&](auto kern, uint32_t rr, uint32_t lo, uint32_t hi, size_t* set) {
+    if (hi <= lo) return;
+    uint32_t Pc = 2;
+    while (Pc < hi) Pc <<= 1;
+    const uint32_t cap = Pc > kLargeTPB * rr ? Pc : kLargeTPB * rr;
+    const size_t sm = (size_t)cap * 8 + (size_t)kLargeTPB * rr * 4;
+    allow_smem(kern, sm, set);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLargeTPB, sm);
+    if (per < 1) per = 1;
+    const uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
+    pdl_launch(kern, (unsigned)grid, kLargeTPB, sm, st, spans, n, A, Bbuf, dt, cap, lo, hi, dn);
+    ++launched;
+  };
+  static size_t set4[64] = {}, set8[64] = {}, set16[64] = {};
+  const uint32_t top = max_len > kWarpSortMax ? max_len : kWarpSortMax;
+  run(k_base_large<4, 4>, 4, kWarpSortMax, top < 1024 ? top : 1024, set4);
+  run(k_base_large<8, 3>, 8, 1024, top < 2048 ? top : 2048, set8);
+  run(k_base_large<16, 2>, 16, 2048, top, set16);
+  return launched;
 }
 
 int launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
@@ -2334,29 +2427,7 @@ int launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t*
     else launch_large(k_base_large_kv<4>, spans, n, P, (size_t)P * 12, st, set4, A, Bbuf, VA, VBuf, dt);
     return 1;
   }
-  int launched = 0;
-  // size classes (kWarpSortMax, 1024], (1024, 2048], (2048, max_len]
-  auto run = [&](auto kern, uint32_t rr, uint32_t lo, uint32_t hi, size_t* set) {
-    if (hi <= lo) return;
-    uint32_t Pc = 2;
-    while (Pc < hi) Pc <<= 1;
-    const uint32_t cap = Pc > kLargeTPB * rr ? Pc : kLargeTPB * rr;
-    const size_t sm = (size_t)cap * 8 + (size_t)kLargeTPB * rr * 4;
-    allow_smem(kern, sm, set);
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLargeTPB, sm);
-    if (per < 1) per = 1;
-    const uint64_t grid = n < (uint64_t)sm_count() * per ? n : (uint64_t)sm_count() * per;
-    pdl_launch(kern, (unsigned)grid, kLargeTPB, sm, st, spans, n, A, Bbuf, dt, cap, lo, hi);
-    ++launched;
-  };
-  static size_t set4[64] = {}, set8[64] = {}, set16[64] = {};
-  const uint32_t top = max_len > kWarpSortMax ? max_len : kWarpSortMax;
-  run(k_base_large<4, 4>, 4, kWarpSortMax, top < 1024 ? top : 1024, set4);
-  run(k_base_large<8, 3>, 8, 1024, top < 2048 ? top : 2048, set8);
-  run(k_base_large<16, 2>, 16, 2048, top, set16);
-  (void)P;
-  return launched;
+  return launch_large_classes(spans, n, max_len, A, Bbuf, dt, nullptr, st);
 }
 
 void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
@@ -2365,7 +2436,8 @@ void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_
   uint64_t grid = n < (uint64_t)sm_count() * 16 ? n : (uint64_t)sm_count() * 16;
   if (vb == 8) pdl_launch(k_copy_spans_kv<8>, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf);
   else if (vb == 4) pdl_launch(k_copy_spans_kv<4>, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf);
-  else pdl_launch(k_copy_spans, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf);
+  else pdl_launch(k_copy_spans, (unsigned)grid, kTPB, 0, st, spans, n, A, Bbuf,
+                  static_cast<const unsigned long long*>(nullptr));
 }
 
 void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
@@ -2374,7 +2446,24 @@ void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
   uint64_t grid = n < (uint64_t)sm_count() * 2 ? n : (uint64_t)sm_count() * 2;
   if (vb == 8) pdl_launch(k_fallback_kv<8>, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
   else if (vb == 4) pdl_launch(k_fallback_kv<4>, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
-  else pdl_launch(k_fallback, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, dt);
+  else pdl_launch(k_fallback, (unsigned)grid, 1024, 0, st, spans, n, A, Bbuf, dt,
+                  static_cast<const unsigned long long*>(nullptr));
+}
+
+int launch_spans_device(const LevelCounters* ctr, const Span* small, const Span* large, const Span* copy,
+                        const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A, uint64_t* Bbuf, int dt,
+                        cudaStream_t st) {
+  const uint64_t sms = (uint64_t)sm_count();
+  const uint64_t cap = n_max ? n_max : 1;
+  const uint64_t gs = cap < sms * 16 ? cap : sms * 16;
+  pdl_launch(k_base_small, (unsigned)gs, kTPB, 0, st, small, cap, A, static_cast<const uint64_t*>(Bbuf), dt,
+             &ctr->n_base_small);
+  int launched = 1 + launch_large_classes(large, cap, max_len, A, Bbuf, dt, &ctr->n_base_large, st);
+  pdl_launch(k_copy_spans, (unsigned)gs, kTPB, 0, st, copy, cap, A, static_cast<const uint64_t*>(Bbuf),
+             &ctr->n_copy);
+  const uint64_t gf = cap < sms * 2 ? cap : sms * 2;
+  pdl_launch(k_fallback, (unsigned)gf, 1024, 0, st, fallback, cap, A, Bbuf, dt, &ctr->n_fallback);
+  return launched + 2;
 }
 
 void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st) {

@@ -115,6 +115,7 @@ class LevelStats(C.Structure):
 
 LS_FLAG_TIME_PASSES = 1
 LS_FLAG_TUNED = 2
+LS_FLAG_HOST_LEVELS = 4
 PASS_NAMES = ("sample", "fit", "pivots", "classify", "children", "scatter", "base", "copy")
 
 
