@@ -39,6 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 SCATTER_BYTES_PER_KEY = 16  # K3 reads each key once and writes it once
 CLASSIFY_BYTES_PER_KEY = 8  # K1 reads each key once
 BASECASE_T = 4096           # buckets of <= 4096 keys go to the shared-memory base case
+TUNE_SEGS = 512             # C4: segments the autotuner times the segmented sort on
 
 
 def parse():
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-splitter", action="store_true")
+    ap.add_argument("--no-device-levels", action="store_true",
+                    help="leave out the C2 sorts with the levels below the root planned on the device")
     ap.add_argument("--dists", default=",".join(DISTS), help="comma-separated subset (profiling runs)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
                     help="c2: six 1e8-key arrays (the headline); c4: 4096 segments, batched vs one call per array")
@@ -353,6 +356,26 @@ def run_ours(args):
                  "level1_max_bucket": {d: int(sts_s[i].level[0].max_child) for i, (d, _) in enumerate(inputs)},
                  "level1_bucket_sumsq": {d: int(sts_s[i].level[0].sumsq_child) for i, (d, _) in enumerate(inputs)}}
 
+    # the same sorts with the levels below the root planned on the device
+    # (device work queue, one CUDA graph per array: captured in the first
+    # untimed round, then reused)
+    devlv = None
+    if not args.no_device_levels:
+        p_dev = lsg.ls_params_default(flags=lsg.LS_FLAG_DEVICE_LEVELS, basecase_threshold=BASECASE_T,
+                                      classify_mode=cmode)
+        time_sorts(lsg, ctx, work, pristine, p_dev, torch, stream)
+        ms_d, sts_d = [], []
+        for _ in range(max(1, min(args.steps, 3))):
+            ms, sts = time_sorts(lsg, ctx, work, pristine, p_dev, torch, stream)
+            ms_d.append(sum(ms))
+            sts_d += sts
+        d_ms = max_over_ranks(sum(ms_d) / len(ms_d), world, f"cuda:{dev}")
+        devlv = {"value": job_keys_per_s(world, keys_per_step, d_ms), "unit": "keys/s", "ms_per_step": d_ms,
+                 "vs_host_planned": step_ms / d_ms,
+                 "level_loop": sorted({int(st.level_loop) for st in sts_d}),
+                 "device_batches_per_sort": sum(int(st.device_batches) for st in sts_d) / len(sts_d),
+                 "gpu_launches_per_sort": sum(int(st.kernel_launches) for st in sts_d) / len(sts_d)}
+
     e2e = None
     if not args.no_e2e:
         # the public host API: ls_sort_host_batch over the step's six arrays
@@ -430,6 +453,7 @@ def run_ours(args):
                    "wall_s_timed_region_incl_restores": wall},
         "roofline": roofline,
         "splitter": split,
+        "device_levels": devlv,
         "per_dist": per_dist,
         "passes_ms_per_step": {k: v["ms"] / prof_steps for k, v in passes.items()},
         "cpu_baseline": cpu,
@@ -465,15 +489,14 @@ def c4_measure(lsg, ctx, args, torch, stream, with_cpu=True):
     dev = 0
     keys, off, names = datagen.segmented(args.nseg, 4)
     nseg = off.size - 1
-    lens = np.diff(off).astype(np.int64)
     n = int(off[-1])
     pristine = torch.from_numpy(keys).to(f"cuda:{dev}")
     work = torch.empty_like(pristine)
-    mean_len = n / nseg
-    probe = int(np.argmin(np.abs(lens - mean_len)))
-    seg_probe = pristine[int(off[probe]):int(off[probe + 1])].clone()
+    # parameters tuned on the segmented form itself (the first TUNE_SEGS
+    # segments: the lengths are i.i.d., so their mix is the batch's)
+    tseg = min(TUNE_SEGS, nseg)
     base = lsg.ls_params_default()
-    tuned, rep = lsg.ls_autotune(ctx, seg_probe, base)
+    tuned, rep = lsg.ls_autotune_segmented(ctx, pristine[:int(off[tseg])], off[:tseg + 1], base)
     p = lsg.ls_params_default(fanout=tuned.fanout, basecase_threshold=tuned.basecase_threshold,
                               sample_rate=tuned.sample_rate, recurse_model=tuned.recurse_model)
     ctx.workspace(n, nseg, lsg.LS_F64, p)
@@ -522,7 +545,7 @@ def c4_measure(lsg, ctx, args, torch, stream, with_cpu=True):
         ms, llaunch = looped()
         lms.append(ms)
     assert torch.equal(work, out_b), "batched and per-array results differ"
-    del out_b, work, pristine, seg_probe
+    del out_b, work, pristine
     b_ms = sum(bms) / len(bms)
     l_ms = sum(lms) / len(lms)
     cpu = None
@@ -557,7 +580,7 @@ def c4_measure(lsg, ctx, args, torch, stream, with_cpu=True):
         "batched_speedup": l_ms / b_ms,
         "params": {"fanout": p.fanout, "basecase_threshold": p.basecase_threshold, "sample_rate": p.sample_rate,
                    "recurse_model": p.recurse_model,
-                   "chosen_by": f"ls_autotune on segment {probe} ({int(lens[probe])} keys, mean {mean_len:.0f}); "
+                   "chosen_by": f"ls_autotune_segmented on the first {tseg} segments ({int(off[tseg])} keys); "
                                 f"{rep.configs} configurations, {rep.base_ms:.3f} -> {rep.best_ms:.3f} ms"},
         "cpu_baseline": cpu, "clocks": clk.summary(), "l2": "4.7 GB of keys, larger than L2; no flush",
     }

@@ -116,15 +116,18 @@ typedef struct {
  * floor(log2 n) (of the mean segment length for ls_sort_segmented), when
  * there is one; ls_workspace_size applies the same substitution. */
 #define LS_FLAG_TUNED 2u
-/* ls_params.flags: plan every recursion level on the host (one readback per
- * level).  By default, when buckets below the root are refined rather than
- * resampled (REFINE_GLOBAL, partitioner not LS_PART_SPLITTER, keys only,
- * fanout <= 1024, not LS_CLASSIFY_DIRECTORY), the levels below the root are
- * planned on the device from a device work queue and run as one CUDA graph
- * (launched batch by batch from the host when LS_FLAG_TIME_PASSES is set);
- * buckets that do draw a sample are planned on the host.  Results are
+/* ls_params.flags: plan the recursion levels below the root on the device.
+ * Without it every level is planned on the host (one readback per level,
+ * overlapped with the level's scatter).  With it, when buckets below the
+ * root are refined rather than resampled (REFINE_GLOBAL, partitioner not
+ * LS_PART_SPLITTER, keys only, fanout <= 1024, not LS_CLASSIFY_DIRECTORY),
+ * the levels below the root come from a device work queue and run as one
+ * CUDA graph (launched batch by batch from the host when
+ * LS_FLAG_TIME_PASSES is set), with one readback at the end; buckets that
+ * do draw a sample are planned on the host.  The graph is captured once per
+ * (keys, workspace, parameters) and kept in the context.  Results are
  * identical either way. */
-#define LS_FLAG_HOST_LEVELS 4u
+#define LS_FLAG_DEVICE_LEVELS 4u
 
 /* The trained two-layer RMI (all FP64), as exported by ls_fit. */
 typedef struct {
@@ -186,7 +189,16 @@ typedef struct {
   double ms_total;              /* host-observed time of the call (stats only) */
   uint64_t kernel_launches;     /* kernels this call launched */
   ls_pass_time pass[LS_NPASS];  /* filled when LS_FLAG_TIME_PASSES is set */
+  uint64_t device_batches;      /* batches planned by the device work queue */
+  int32_t level_loop;           /* how the levels below the root ran: LS_LOOP_* */
+  int32_t reserved;
 } ls_stats;
+
+/* ls_stats.level_loop */
+#define LS_LOOP_HOST 0          /* planned on the host, one readback per level (default) */
+#define LS_LOOP_DEVICE 1        /* device work queue, batches launched from the host */
+#define LS_LOOP_GRAPH 2         /* device work queue in one CUDA graph (while node) */
+#define LS_LOOP_GRAPH_PDL 3     /* the same, with programmatic dependent launches in the graph */
 
 typedef struct ls_ctx ls_ctx;
 
@@ -208,12 +220,10 @@ ls_status ls_workspace_size(ls_ctx* ctx, uint64_t n, uint32_t nseg, ls_dtype dty
 /* Sort d_keys[0..n) ascending by ord (the sorting problem of Sec. 1-2).
  * d_keys must be 8-byte aligned (LS_EINVAL otherwise).  In place from the
  * caller's view; the library ping-pongs through d_workspace
- * (>= ls_workspace_size bytes, 256-byte aligned).  Stream ordered.  The root
- * level is planned on the host (it waits once for the root's Alg. 5
- * decision); the levels below run from a device work queue as one CUDA
- * graph (see LS_FLAG_HOST_LEVELS for when, and for the per-level host
- * planner used otherwise); the call returns after the sort is complete,
- * with one readback of the statistics at the end.  out_stats (nullable)
+ * (>= ls_workspace_size bytes, 256-byte aligned).  Stream ordered; the
+ * host plans each level from a readback of the previous one (or, with
+ * LS_FLAG_DEVICE_LEVELS, the device plans the levels below the root), so
+ * the call returns after the sort is complete.  out_stats (nullable)
  * receives the decisions and per-level statistics. */
 ls_status ls_sort(ls_ctx* ctx, void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* p, void* d_workspace,
                   size_t ws_bytes, ls_stats* out_stats, ls_stream_t stream);
@@ -317,7 +327,9 @@ ls_status ls_classify_static(const ls_model* model, const void* d_keys, uint64_t
  * base-case threshold T and the recursion mode are chosen by timing ls_sort
  * on copies of the caller's keys: coordinate descent over the candidate
  * lists below, starting from *base, each configuration timed as the median
- * of three sorts after one warm-up sort (CUDA events on `stream`).
+ * of five sorts after one warm-up sort (CUDA events on `stream`); a
+ * candidate replaces the current configuration only when it is at least 5 %
+ * faster, so that timing noise does not decide.
  *   fanout             256, 512, 1000, 1024, 2048
  *   basecase_threshold 1024, 2048, 4096, 8192
  *   sample_rate        0.0025, 0.005, 0.01, 0.02
@@ -335,6 +347,17 @@ typedef struct {
 
 ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* base,
                       ls_params* out, ls_tune_report* report, ls_stream_t stream);
+
+/* ls_autotune for a batch of segments (the form ls_sort_segmented sorts):
+ * each candidate is timed on ls_sort_segmented of copies of d_keys[0 ..
+ * h_offsets[nseg]) split at h_offsets (host array, h_offsets[0] = 0), so
+ * the choice reflects the batch's mix of segment lengths.  The winner is
+ * stored under floor(log2) of the mean segment length, where
+ * ls_sort_segmented with LS_FLAG_TUNED finds it.  Same conventions as
+ * ls_autotune. */
+ls_status ls_autotune_segmented(ls_ctx* ctx, const void* d_keys, const uint64_t* h_offsets, uint32_t nseg,
+                                ls_dtype dtype, const ls_params* base, ls_params* out, ls_tune_report* report,
+                                ls_stream_t stream);
 
 /* The context's tuning table as text, one entry per line:
  *   "<dtype> <log2n> <fanout> <basecase_threshold> <sample_rate> <recurse_model> <ms>\n"

@@ -324,6 +324,8 @@ struct Sorter {
   uint32_t nseg = 0;
   bool root_copied = false;  // the root's plan waits in the workspace for the final readback
   uint64_t root_n = 0;
+  uint64_t device_batches = 0;      // batches planned by the device work queue
+  int32_t level_loop = LS_LOOP_HOST;  // the last form the levels below the root ran in
 
   int alloc_model() {
     if (model_free.empty()) return -1;
@@ -772,17 +774,17 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
   return LS_OK;
 }
 
-// ---- device-planned levels (ls_queue.cu)
+// ---- device-planned levels (ls_queue.cu), LS_FLAG_DEVICE_LEVELS
 //
-// Every level below the root is planned on the device when no bucket below
-// the root can draw a sample: REFINE_GLOBAL (learned items refine the root's
+// Every level below the root is planned on the device when asked for and no
+// bucket below the root can draw a sample: REFINE_GLOBAL (learned items refine the root's
 // model, the others take the radix split), keys only (K3b takes every item),
 // at most kBufMaxBuckets buckets, a classify mode without the radix
 // directory, and a partitioner that is not the splitter tree everywhere.
 // Items that do draw a sample (below a splitter tree) come back to the host
 // planner.
 bool device_levels_ok(const ls_params* p, uint32_t vb) {
-  return vb == 0 && !(p->flags & LS_FLAG_HOST_LEVELS) && p->recurse_model == LS_RECURSE_REFINE_GLOBAL &&
+  return vb == 0 && (p->flags & LS_FLAG_DEVICE_LEVELS) && p->recurse_model == LS_RECURSE_REFINE_GLOBAL &&
          p->partitioner != LS_PART_SPLITTER && p->classify_mode != LS_CLASSIFY_DIRECTORY &&
          pow2ceil(p->fanout) <= kBufMaxBuckets;
 }
@@ -790,13 +792,60 @@ bool device_levels_ok(const ls_params* p, uint32_t vb) {
 constexpr unsigned long long kMaxLoopIter = 1ull << 16;  // batches of one device loop (a safety bound)
 constexpr size_t kMaxGraphs = 8;                         // graphs kept per context
 
-// The kernels of one device-planned batch on stream st: planner, count
-// reset, exact pivots, K1, chunk prefixes, K2, K3b, the finished spans and
-// the loop control.  h: the graph's loop condition (0 outside a graph).  tm:
-// pass timer (nullptr: untimed).  Returns the kernels launched.
-uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHandle h, PassTimer* tm) {
+// Where the kernels of one batch go: straight to a stream (launched from
+// the host), or into the body of the level-loop graph being captured, with
+// the optional groups in if nodes (their conditions set by the planner and
+// the batch-end kernel).
+struct BatchSink {
+  cudaStream_t st = nullptr;   // stream of the kernels outside if nodes
+  cudaStream_t aux = nullptr;  // capture of if-node bodies (graph only)
+  bool graph = false;
+  bool ok = true;
+  LoopHandles h{};
+  // Run fn(stream) under the condition hh (plain launch outside a graph).
+  template <class F>
+  uint64_t cond(cudaGraphConditionalHandle hh, F fn) {
+    if (!graph) return fn(st);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (!ok || cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess) {
+      ok = false;
+      return 0;
+    }
+    union NodeParams {  // the runtime's parameter union has no default constructor
+      cudaGraphNodeParams p;
+      unsigned char raw[sizeof(cudaGraphNodeParams)];
+      NodeParams() { memset(raw, 0, sizeof raw); }
+    } u;
+    u.p.type = cudaGraphNodeTypeConditional;
+    u.p.conditional.handle = hh;
+    u.p.conditional.type = cudaGraphCondTypeIf;
+    u.p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &u.p) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(aux, u.p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      ok = false;
+      return 0;
+    }
+    const uint64_t n = fn(aux);
+    cudaGraph_t got = nullptr;
+    if (cudaStreamEndCapture(aux, &got) != cudaSuccess) ok = false;
+    return n;
+  }
+};
+
+// The kernels of one device-planned batch: planner, count reset, exact
+// pivots, K1, chunk prefixes, K2, K3b, the batch-end kernel and the
+// finished spans.  tm: pass timer (nullptr: untimed).  Returns the kernels
+// launched (in a graph: the kernels of the body, if nodes included).
+uint64_t launch_device_batch(Sorter& s, BatchSink& k, PassTimer* tm) {
   Layout& L = s.lay;
   const ls_params* p = s.p;
+  cudaStream_t st = k.st;
   const uint32_t nbp = std::max<uint32_t>(pow2ceil(p->fanout), 1u << kRadixBits);
   BatchDesc* bd = at<BatchDesc>(s.ws, L.o_bdesc);
   QueueState* q = at<QueueState>(s.ws, L.o_queue);
@@ -840,18 +889,24 @@ uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHan
   pg.cells = L.cells;
   pg.slots = 2ull * buffered_scatter_slots();
   tb(LS_PASS_CHILDREN);
-  launch_plan_batch(pg, s.rp, st);
+  launch_plan_batch(pg, s.rp, k.h, st);
   launch_zero_counts(bd, plans, counts, st);
   te();
   nl += 2;
 
   tb(LS_PASS_PIVOTS);
-  launch_learned_pivots(plans, bitems, pg.reflist, kBatchItems, pow2ceil(p->fanout), models, leaves, pivots, s.rp, st,
-                        bd);
+  nl += k.cond(k.h.pivots, [&](cudaStream_t cs) {
+    launch_learned_pivots(plans, bitems, pg.reflist, kBatchItems, pow2ceil(p->fanout), models, leaves, pivots, s.rp,
+                          cs, bd);
+    return (uint64_t)1;
+  });
   te();
-  nl += 1;
 
   const bool guess = p->classify_mode == LS_CLASSIFY_AUTO || p->classify_mode == LS_CLASSIFY_GUESS;
+  // queue items hold more than T keys, so the direct FP64 classifier (items
+  // below 4 B keys) is needed only when T + 1 < 4 B or when it is the mode
+  const bool direct = p->classify_mode == LS_CLASSIFY_DIRECT || (uint64_t)p->basecase_threshold + 1 < 4ull * p->fanout;
+  if (k.graph && direct != (k.h.has_direct != 0)) k.ok = false;
   PassArgs pa{};
   pa.items = bitems;
   pa.plans = plans;
@@ -868,8 +923,6 @@ uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHan
   pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
   pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
   pa.aux_bytes = guess ? std::max<uint32_t>(16, L.L * (uint32_t)sizeof(FLeaf)) : 16;
-  pa.cls_mask = (1u << CLS_DIRECT) | (1u << CLS_RADIX) | (guess ? 1u << CLS_GUESS : 0u) |
-                (p->classify_mode == LS_CLASSIFY_TREE ? 1u << CLS_TREE : 0u);
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
   pa.counts = counts;
   pa.cursors = cursors;
@@ -884,7 +937,16 @@ uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHan
   pa.dir_cells_max = L.cells;
   pa.bd = bd;
   tb(LS_PASS_CLASSIFY);
-  nl += launch_classify_hist(pa, s.rp, st);
+  auto k1 = [&](uint32_t mask) {
+    return [&, mask](cudaStream_t cs) {
+      PassArgs a = pa;
+      a.cls_mask = mask;
+      return (uint64_t)launch_classify_hist(a, s.rp, cs);
+    };
+  };
+  nl += k.cond(k.h.k1, k1(guess ? 1u << CLS_GUESS : p->classify_mode == LS_CLASSIFY_TREE ? 1u << CLS_TREE : 0u));
+  if (direct) nl += k.cond(k.h.direct, k1(1u << CLS_DIRECT));
+  nl += k.cond(k.h.radix, k1(1u << CLS_RADIX));
   te();
 
   ChildArgs ca{};
@@ -907,9 +969,12 @@ uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHan
   ca.ctr = ctr;
   ca.stats = at<DevLevelStats>(s.ws, L.o_stats);
   ca.bd = bd;
+  const uint32_t segs_grid = (uint32_t)std::min<uint64_t>(L.seg_cap, 1024);
   tb(LS_PASS_CHILDREN);
-  nl += launch_chunk_prefix(pg.segs, (uint32_t)std::min<uint64_t>(L.seg_cap, 1024), pg.multi, 256, plans, pa.agg,
-                            pa.excl, nbp, st, bd);
+  nl += launch_chunk_prefix(pg.segs, segs_grid, pg.multi, 256, plans, pa.agg, pa.excl, nbp, st, bd, 1);
+  nl += k.cond(k.h.multi, [&](cudaStream_t cs) {
+    return (uint64_t)launch_chunk_prefix(pg.segs, segs_grid, pg.multi, 256, plans, pa.agg, pa.excl, nbp, cs, bd, 2);
+  });
   launch_children(ca, s.rp, st);
   te();
   nl += 1;
@@ -917,14 +982,21 @@ uint64_t launch_device_batch(Sorter& s, cudaStream_t st, cudaGraphConditionalHan
   tb(LS_PASS_SCATTER);
   launch_scatter_buffered(pa, s.rp, pg.runs, (uint32_t)L.brun_cap, st);
   te();
-  nl += 1;
+  launch_batch_end(q, ctr, s.ctx->d_status, k.h, kMaxLoopIter, st);
+  nl += 2;
 
   tb(LS_PASS_BASE);
-  nl += launch_spans_device(ctr, ca.base_small, ca.base_large, ca.copy, ca.fallback, L.base_cap,
-                            p->basecase_threshold, s.A, s.Bb, s.dt, st);
+  auto spans = [&](int which) {
+    return [&, which](cudaStream_t cs) {
+      return (uint64_t)launch_spans_device(which, ctr, ca.base_small, ca.base_large, ca.copy, ca.fallback, L.base_cap,
+                                           p->basecase_threshold, s.A, s.Bb, s.dt, cs);
+    };
+  };
+  nl += k.cond(k.h.small, spans(SPANS_SMALL));
+  nl += k.cond(k.h.large, spans(SPANS_LARGE));
+  nl += k.cond(k.h.copy, spans(SPANS_COPY));
+  nl += k.cond(k.h.fallback, spans(SPANS_FALLBACK));
   te();
-  launch_loop_ctl(q, ctr, s.ctx->d_status, h, kMaxLoopIter, st);
-  nl += 1;
   return nl;
 }
 
@@ -979,18 +1051,34 @@ bool build_graph(Sorter& s, bool plain, ls_graph_entry* out) {
     np.conditional.size = 1;
     ok = cudaGraphAddNode(&node, e.graph, nullptr, nullptr, 0, &np) == cudaSuccess;
   }
+  if (ok && !ctx->s_cap_aux && cudaStreamCreateWithFlags(&ctx->s_cap_aux, cudaStreamNonBlocking) != cudaSuccess)
+    ok = false;
   if (ok) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    ok = cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
-         cudaSuccess;
+    BatchSink k;
+    k.st = ctx->s_cap;
+    k.aux = ctx->s_cap_aux;
+    k.graph = true;
+    k.h.in_graph = 1;
+    k.h.loop = h;
+    // every handle must belong to one if node: the direct classifier's only
+    // when the batch can use it
+    const ls_params* p = s.p;
+    k.h.has_direct = p->classify_mode == LS_CLASSIFY_DIRECT || (uint64_t)p->basecase_threshold + 1 < 4ull * p->fanout;
+    for (cudaGraphConditionalHandle* c : {&k.h.pivots, &k.h.k1, &k.h.radix, &k.h.multi, &k.h.small, &k.h.large,
+                                          &k.h.copy, &k.h.fallback})
+      ok = ok && cudaGraphConditionalHandleCreate(c, body, 0, 0) == cudaSuccess;
+    if (k.h.has_direct) ok = ok && cudaGraphConditionalHandleCreate(&k.h.direct, body, 0, 0) == cudaSuccess;
+    ok = ok && cudaStreamBeginCaptureToGraph(ctx->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+                   cudaSuccess;
     if (ok) {
       const bool was = t_plain_launch;
       t_plain_launch = plain;
-      e.body_launches = launch_device_batch(s, ctx->s_cap, h, nullptr);
+      e.body_launches = launch_device_batch(s, k, nullptr);
       t_plain_launch = was;
       cudaGraph_t got = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(ctx->s_cap, &got);
-      ok = ce == cudaSuccess && cudaGetLastError() == cudaSuccess;
+      ok = k.ok && ce == cudaSuccess && cudaGetLastError() == cudaSuccess;
     }
   }
   ok = ok && cudaGraphInstantiate(&e.exec, e.graph, 0) == cudaSuccess;
@@ -999,6 +1087,7 @@ bool build_graph(Sorter& s, bool plain, ls_graph_entry* out) {
     drop_graph(e);
     return false;
   }
+  e.pdl = !plain;
   *out = e;
   return true;
 }
@@ -1039,9 +1128,11 @@ ls_status run_device_levels(Sorter& s, std::vector<Item>* handed_back, bool* ove
     CK(cudaGraphLaunch(ge->exec, st));
   } else {
     // launched from the host, one batch at a time (pass timing, or no graph)
+    BatchSink k;
+    k.st = st;
     for (;;) {
       const size_t r0 = s.timer.recs.size();
-      s.launches += launch_device_batch(s, st, 0, s.timer.on ? &s.timer : nullptr);
+      s.launches += launch_device_batch(s, k, s.timer.on ? &s.timer : nullptr);
       QueueState hq;
       BatchDesc hb;
       CK(cudaMemcpyAsync(&hq, q, sizeof hq, cudaMemcpyDeviceToHost, st));
@@ -1061,6 +1152,8 @@ ls_status run_device_levels(Sorter& s, std::vector<Item>* handed_back, bool* ove
   CK(cudaStreamSynchronize(st));
   iters = hq.iter;
   if (ge) s.launches += ge->body_launches * iters;
+  s.device_batches += iters;
+  s.level_loop = ge ? (ge->pdl ? LS_LOOP_GRAPH_PDL : LS_LOOP_GRAPH) : LS_LOOP_DEVICE;
   *overflow = c.overflow != 0;
   if (hq.err) {
     lsg::set_error_detail("device level loop stopped after %llu batches", (unsigned long long)iters);
@@ -1326,6 +1419,8 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     stats->pass[LS_PASS_BASE].keys += stats->level[l].base_keys + stats->level[l].fallback_keys;
   stats->status = result;
   stats->kernel_launches = s.launches;
+  stats->device_batches = s.device_batches;
+  stats->level_loop = s.level_loop;
   ctx->launches += s.launches;
   stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return result;
@@ -1407,7 +1502,7 @@ void ls_destroy(ls_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_cache) cudaFree(ctx->d_cache);
   for (ls_graph_entry& e : ctx->graphs) drop_graph(e);
-  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out, ctx->s_read, ctx->s_cap})
+  for (cudaStream_t s : {ctx->s_sort, ctx->s_in, ctx->s_out, ctx->s_read, ctx->s_cap, ctx->s_cap_aux})
     if (s) cudaStreamDestroy(s);
   if (ctx->ev_children) cudaEventDestroy(ctx->ev_children);
   if (ctx->h_pin) cudaFreeHost(ctx->h_pin);

@@ -26,6 +26,7 @@ struct ls_graph_entry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t body_launches = 0;  // kernels per loop iteration
+  bool pdl = false;            // captured with programmatic dependent launches
   uint64_t last_use = 0;
 };
 
@@ -49,7 +50,7 @@ struct ls_ctx {
   // and the stream they are captured on
   std::vector<ls_graph_entry> graphs;
   uint64_t graph_clock = 0;
-  cudaStream_t s_cap = nullptr;
+  cudaStream_t s_cap = nullptr, s_cap_aux = nullptr;
   // autotuner results, keyed by dtype * 64 + floor(log2 n)
   std::map<int, ls_tuned_entry> tuned;
   std::mutex tuned_mu;

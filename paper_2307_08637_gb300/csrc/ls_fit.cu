@@ -1409,15 +1409,12 @@ void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
   if (!nlist) return;
   uint64_t n = (uint64_t)nlist * nb_pad;
   const uint32_t tpb = nb_pad >= kPivotTPB ? kPivotTPB : 128;  // pooled blocks when tpb divides nb_pad
-  unsigned grid = grid_for(n, tpb);
-  if (bd) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned g8 = (unsigned)(sms > 0 ? sms : 1) * 8;
-    grid = grid < g8 ? grid : g8;
-  }
-  pdl_launch(k_learned_pivots, grid, tpb, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots, rp, bd);
+  // one block per block of slots of the largest list (blocks past the
+  // device-side list end return at once): the search rounds of a block are
+  // synchronised, so blocks are scheduled as slots free up rather than
+  // strided over
+  pdl_launch(k_learned_pivots, grid_for(n, tpb), tpb, 0, st, plans, items, list, nlist, nb_pad, models, leaves, pivots,
+             rp, bd);
 }
 
 void launch_imbalance(const FitArgs& a, uint64_t* pivots, unsigned long long* cnt_pool, const RunParams& rp,

@@ -239,9 +239,10 @@ struct ChunkSeg {
 // per run, then, for the items spanning several runs (multi: first run and
 // run count per such item), a scan of the run totals and the carries.
 // Returns launches.
+// parts: 1 the run pass, 2 the carry scan and pass over items with several runs.
 int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
                         const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st,
-                        const BatchDesc* bd = nullptr);
+                        const BatchDesc* bd = nullptr, int parts = 3);
 void launch_scatter(const PassArgs& a, const RunParams& rp, cudaStream_t st);
 
 // Buffered scatter (K3b).  An item none of whose descendants ever draws a
@@ -302,11 +303,25 @@ struct PlanArgs {
   uint32_t cells;                // directory cells per item
   uint64_t slots;                // buffered-scatter run slots (two per resident block)
 };
-void launch_plan_batch(const PlanArgs& a, const RunParams& rp, cudaStream_t st);
+// Conditions of the level-loop graph: the while node (loop) and if nodes
+// around the kernels a batch may not need.  All zero outside a graph.
+struct LoopHandles {
+  unsigned int in_graph;              // 1: the batch runs inside the graph and sets these
+  unsigned int has_direct;            // the graph has an if node for the direct classifier
+  cudaGraphConditionalHandle loop;    // another batch follows
+  cudaGraphConditionalHandle pivots;  // some item's exact pivots are searched
+  cudaGraphConditionalHandle k1;      // some item uses the table classifier (guess or tree)
+  cudaGraphConditionalHandle direct;  // some item uses the direct FP64 classifier
+  cudaGraphConditionalHandle radix;   // some item takes the radix split
+  cudaGraphConditionalHandle multi;   // some item has several chunk runs
+  cudaGraphConditionalHandle small, large, copy, fallback;  // span lists that are not empty
+};
+void launch_plan_batch(const PlanArgs& a, const RunParams& rp, const LoopHandles& h, cudaStream_t st);
 void launch_zero_counts(const BatchDesc* bd, const Plan* plans, unsigned long long* counts, cudaStream_t st);
-// max_iter bounds the loop; h = 0 outside a graph (the flag in q is read by the host).
-void launch_loop_ctl(QueueState* q, LevelCounters* ctr, const unsigned int* status, cudaGraphConditionalHandle h,
-                     unsigned long long max_iter, cudaStream_t st);
+// After the batch's scatter: the loop condition and the span conditions.
+// max_iter bounds the loop; the flag in q is what the host reads outside a graph.
+void launch_batch_end(QueueState* q, const LevelCounters* ctr, const unsigned int* status, const LoopHandles& h,
+                      unsigned long long max_iter, cudaStream_t st);
 
 struct ChildArgs {
   const Item* items;
@@ -346,11 +361,13 @@ void launch_copy_spans(const Span* spans, uint64_t n, uint64_t* A, const uint64_
                        uint32_t vb, cudaStream_t st);
 void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf, void* VA, void* VBuf, uint32_t vb,
                      int dt, cudaStream_t st);
-// The same for keys only, with the span count read from the device (dn);
-// n_max bounds it (grid sizing).  Returns the kernels launched.
-int launch_spans_device(const LevelCounters* ctr, const Span* small, const Span* large, const Span* copy,
-                        const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A, uint64_t* Bbuf, int dt,
-                        cudaStream_t st);
+// The same for keys only, with the span counts read from the device
+// (the level counters); n_max bounds them (grid sizing).  which: SPANS_*.
+// Returns the kernels launched.
+enum { SPANS_SMALL = 1, SPANS_LARGE = 2, SPANS_COPY = 4, SPANS_FALLBACK = 8 };
+int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* large,
+                        const Span* copy, const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A,
+                        uint64_t* Bbuf, int dt, cudaStream_t st);
 
 // ls_classify helpers
 void launch_direct_classify(const DModel* m, const Leaf* leaves, const uint64_t* keys, uint64_t n, int dt, double P,

@@ -2306,16 +2306,17 @@ int launch_classify_hist(const PassArgs& a, const RunParams& rp, cudaStream_t st
 
 int launch_chunk_prefix(const ChunkSeg* segs, uint32_t nsegs, const uint2* multi, uint32_t nmulti,
                         const Plan* plans, uint32_t* agg, unsigned long long* excl, uint32_t nbp, cudaStream_t st,
-                        const BatchDesc* bd) {
+                        const BatchDesc* bd, int parts) {
   // with bd the counts are read on the device and nsegs / nmulti bound the
   // grids (each block strides over the runs)
   if (!nsegs) return 0;
   const unsigned cols = (nbp + kTPB - 1) / kTPB;
-  pdl_launch(k_chunk_prefix, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp, bd);
-  if (!nmulti) return 1;
+  int n = 0;
+  if (parts & 1) pdl_launch(k_chunk_prefix, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp, bd), ++n;
+  if (!nmulti || !(parts & 2)) return n;
   pdl_launch(k_run_scan, dim3(nmulti, cols), kTPB, 0, st, multi, segs, plans, agg, nbp, bd);
   pdl_launch(k_chunk_carry, dim3(nsegs, cols), kTPB, 0, st, segs, plans, agg, excl, nbp, bd);
-  return 3;
+  return n + 2;
 }
 
 template <int TPB, int QM, int VB>
@@ -2450,20 +2451,30 @@ void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
                   static_cast<const unsigned long long*>(nullptr));
 }
 
-int launch_spans_device(const LevelCounters* ctr, const Span* small, const Span* large, const Span* copy,
-                        const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A, uint64_t* Bbuf, int dt,
-                        cudaStream_t st) {
+int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* large,
+                        const Span* copy, const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A,
+                        uint64_t* Bbuf, int dt, cudaStream_t st) {
   const uint64_t sms = (uint64_t)sm_count();
   const uint64_t cap = n_max ? n_max : 1;
   const uint64_t gs = cap < sms * 16 ? cap : sms * 16;
-  pdl_launch(k_base_small, (unsigned)gs, kTPB, 0, st, small, cap, A, static_cast<const uint64_t*>(Bbuf), dt,
-             &ctr->n_base_small);
-  int launched = 1 + launch_large_classes(large, cap, max_len, A, Bbuf, dt, &ctr->n_base_large, st);
-  pdl_launch(k_copy_spans, (unsigned)gs, kTPB, 0, st, copy, cap, A, static_cast<const uint64_t*>(Bbuf),
-             &ctr->n_copy);
-  const uint64_t gf = cap < sms * 2 ? cap : sms * 2;
-  pdl_launch(k_fallback, (unsigned)gf, 1024, 0, st, fallback, cap, A, Bbuf, dt, &ctr->n_fallback);
-  return launched + 2;
+  int launched = 0;
+  if (which & SPANS_SMALL) {
+    pdl_launch(k_base_small, (unsigned)gs, kTPB, 0, st, small, cap, A, static_cast<const uint64_t*>(Bbuf), dt,
+               &ctr->n_base_small);
+    ++launched;
+  }
+  if (which & SPANS_LARGE) launched += launch_large_classes(large, cap, max_len, A, Bbuf, dt, &ctr->n_base_large, st);
+  if (which & SPANS_COPY) {
+    pdl_launch(k_copy_spans, (unsigned)gs, kTPB, 0, st, copy, cap, A, static_cast<const uint64_t*>(Bbuf),
+               &ctr->n_copy);
+    ++launched;
+  }
+  if (which & SPANS_FALLBACK) {
+    const uint64_t gf = cap < sms * 2 ? cap : sms * 2;
+    pdl_launch(k_fallback, (unsigned)gf, 1024, 0, st, fallback, cap, A, Bbuf, dt, &ctr->n_fallback);
+    ++launched;
+  }
+  return launched;
 }
 
 void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st) {

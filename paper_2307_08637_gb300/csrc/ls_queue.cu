@@ -22,9 +22,10 @@ static_assert(kBatchItems == 2 * kPlanTPB, "the planner holds two items per thre
 constexpr int kPlanWarps = kPlanTPB / 32;
 
 // Block-wide exclusive scan (thread order) of K values per thread; every
-// thread gets the totals.  sh holds kPlanWarps * K words.
+// thread gets the totals.  One barrier: each warp scans the warp totals
+// itself.  sh holds kPlanWarps * K words and is not reused by the caller.
 template <int K>
-__device__ void plan_scan(uint32_t (&v)[K], uint32_t (&tot)[K], uint32_t* sh) {
+__device__ __forceinline__ void plan_scan(uint32_t (&v)[K], uint32_t (&tot)[K], uint32_t* sh) {
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t inc[K];
 #pragma unroll
@@ -41,27 +42,20 @@ __device__ void plan_scan(uint32_t (&v)[K], uint32_t (&tot)[K], uint32_t* sh) {
 #pragma unroll
     for (int k = 0; k < K; ++k) sh[wid * K + k] = inc[k];
   __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      uint32_t x = sh[lane * K + k];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (lane >= (unsigned)d) x += o;
-      }
-      sh[lane * K + k] = x;  // inclusive over warps
-    }
-  }
-  __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const uint32_t before = wid > 0 ? sh[(wid - 1) * K + k] : 0u;
-    tot[k] = sh[(kPlanWarps - 1) * K + k];
-    v[k] = inc[k] - v[k] + before;
+    uint32_t x = sh[lane * K + k];  // warp `lane`'s total (kPlanWarps == 32)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= (unsigned)d) x += o;
+    }
+    const uint32_t before = __shfl_sync(0xFFFFFFFFu, x, (wid + 31) & 31);
+    tot[k] = __shfl_sync(0xFFFFFFFFu, x, 31);
+    v[k] = inc[k] - v[k] + (wid > 0 ? before : 0u);
   }
-  __syncthreads();  // sh is reused by the next scan
 }
+static_assert(kPlanWarps == 32, "plan_scan scans one warp total per lane");
 
 __device__ __forceinline__ uint32_t pow2ceil_dev(uint32_t x) { return x <= 1 ? 1u : 1u << (32 - __clz(x - 1)); }
 
@@ -76,12 +70,20 @@ __device__ __forceinline__ double pow_refine(uint32_t B, uint32_t e) {
 // One batch of the current level: switch levels when the current one is
 // exhausted, take up to kBatchItems items, hand back those that draw a
 // sample, and lay out the batch for its kernels.  One block.
-__global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams rp) {
+__global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams rp, LoopHandles hs) {
   pdl_wait();
-  __shared__ uint32_t sh[kPlanWarps * 5];
+  __shared__ uint32_t sh1[kPlanWarps], sh7[kPlanWarps * 7];
   __shared__ unsigned long long s_sum[kPlanWarps];
   QueueState* q = a.q;
   uint64_t cur_n = q->cur_n, head = q->head;
+  // the previous batch's spans have been sorted (the spans of the levels
+  // planned on the host before the first batch are sorted with it)
+  if (q->iter > 0 && threadIdx.x == 0) {
+    a.ctr->n_base_small = 0;
+    a.ctr->n_base_large = 0;
+    a.ctr->n_copy = 0;
+    a.ctr->n_fallback = 0;
+  }
   if (head >= cur_n) {  // uniform: the level is done, the next one becomes current
     uint64_t nn = a.ctr->n_next;
     if (nn > a.icap) nn = a.icap;  // K2 has flagged the overflow; the loop stops after this batch
@@ -99,8 +101,9 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
   }
   const uint32_t k = (uint32_t)(cur_n - head < kBatchItems ? cur_n - head : kBatchItems);
   const uint32_t B = rp.B;
-  // 1. keep the items planned here (refine and radix items), hand back the rest
-  Item mine[2];
+  // 1. keep the items planned here (refine and radix items), hand back the
+  // rest; the kept ones keep their order
+  Item its[2];
   bool kp[2] = {false, false};
   uint32_t keep[1] = {0}, nk1[1];
   unsigned long long nsum = 0;
@@ -108,8 +111,8 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
   for (int j = 0; j < 2; ++j) {
     const uint32_t idx = 2 * threadIdx.x + j;
     if (idx >= k) continue;
-    mine[j] = a.level[head + idx];
-    const Item& it = mine[j];
+    its[j] = a.level[head + idx];
+    const Item& it = its[j];
     kp[j] = it.kind == KIND_RADIX || (it.kind == KIND_REFINE && !beyond_refine_limit(B, (uint32_t)it.mk + 1u));
     if (kp[j]) {
       keep[0] += 1;
@@ -120,16 +123,9 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
       else atomicExch(&a.ctr->overflow, 1ull);
     }
   }
-  plan_scan<1>(keep, nk1, sh);
-  {
-    uint32_t o = keep[0];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      if (kp[j]) a.bitems[o++] = mine[j];
-  }
   for (int d = 16; d > 0; d >>= 1) nsum += __shfl_xor_sync(0xFFFFFFFFu, nsum, d);
   if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = nsum;
-  __syncthreads();  // kept items and warp sums are visible to the block
+  plan_scan<1>(keep, nk1, sh1);  // its barrier also publishes s_sum
   unsigned long long bkeys = 0;
   for (int w = 0; w < kPlanWarps; ++w) bkeys += s_sum[w];
   const uint32_t nk = nk1[0];
@@ -140,16 +136,14 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
   // buffered-scatter runs: about an equal share of the run slots, at least a tile
   const uint64_t share = (bkeys + a.slots - 1) / a.slots;
   const uint64_t target = share > kTileKeys ? share : (uint64_t)kTileKeys;
-  // 2. per kept item: chunks, chunk runs, multi-run flag, pivot search, scatter runs
-  uint32_t v[5] = {0, 0, 0, 0, 0}, tot[5];
-  Item its[2];
+  // 2. per kept item: chunks, chunk runs, multi-run flag, pivot search,
+  // scatter runs; and the classifiers the batch uses
+  uint32_t v[7] = {0, 0, 0, 0, 0, 0, 0}, tot[7];
   uint32_t nc[2] = {0, 0}, nr[2] = {0, 0};
   bool refine[2] = {false, false};
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const uint32_t i = 2 * threadIdx.x + j;
-    if (i >= nk) continue;
-    its[j] = a.bitems[i];
+    if (!kp[j]) continue;
     const uint64_t n = its[j].n;
     nc[j] = (uint32_t)((n + ck - 1) / ck);
     nr[j] = (uint32_t)((n + target - 1) / target);
@@ -159,8 +153,10 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
     v[2] += nc[j] > kSegChunks;
     v[3] += refine[j];
     v[4] += nr[j];
+    v[5] += its[j].kind == KIND_REFINE && !refine[j];
+    v[6] += its[j].kind == KIND_RADIX;
   }
-  plan_scan<5>(v, tot, sh);
+  plan_scan<7>(v, tot, sh7);
   const bool fits = tot[0] <= a.chunk_cap && tot[1] <= a.seg_cap && tot[4] <= a.run_cap;
   if (!fits) {  // cannot happen with the workspace's capacities; stop the loop with an error
     if (threadIdx.x == 0) {
@@ -169,15 +165,23 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
       a.bd->nchunks = 0;
       a.bd->nsegs = a.bd->nmulti = a.bd->nruns = a.bd->nrefine = 0;
       q->head = head + k;
+      if (hs.in_graph) {
+        cudaGraphSetConditional(hs.pivots, 0);
+        cudaGraphSetConditional(hs.k1, 0);
+        if (hs.has_direct) cudaGraphSetConditional(hs.direct, 0);
+        cudaGraphSetConditional(hs.radix, 0);
+        cudaGraphSetConditional(hs.multi, 0);
+      }
     }
     return;
   }
-  // 3. plans, chunk map, chunk runs, scatter runs, pivot list
+  // 3. items, plans, chunk map, chunk runs, scatter runs, pivot list
+  uint32_t i = keep[0];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const uint32_t i = 2 * threadIdx.x + j;
-    if (i >= nk) continue;
+    if (!kp[j]) continue;
     const Item& it = its[j];
+    a.bitems[i] = it;
     Plan pl;
     memset(&pl, 0, sizeof pl);
     pl.chunk_begin = v[0];
@@ -234,6 +238,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
     v[2] += nc[j] > kSegChunks;
     v[3] += refine[j];
     v[4] += nr[j];
+    ++i;
   }
   if (threadIdx.x == 0) {
     BatchDesc d;
@@ -250,6 +255,13 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
     a.chunk_ctr[0] = 0;
     a.chunk_ctr[1] = 0;
     q->head = head + k;
+    if (hs.in_graph) {  // inside the graph: skip the kernels this batch does not need
+      cudaGraphSetConditional(hs.pivots, tot[3] > 0);
+      cudaGraphSetConditional(hs.k1, tot[3] > 0);
+      if (hs.has_direct) cudaGraphSetConditional(hs.direct, tot[5] > 0);
+      cudaGraphSetConditional(hs.radix, tot[6] > 0);
+      cudaGraphSetConditional(hs.multi, tot[2] > 0);
+    }
   }
 }
 
@@ -263,16 +275,12 @@ __global__ void k_zero_counts(const BatchDesc* bd, const Plan* plans, unsigned l
   }
 }
 
-// End of a batch: its finished spans have been sorted, so the span lists
-// start again; continue while items remain, no list overflowed, the device
-// status is clean and the iteration limit is not reached.
-__global__ void k_loop_ctl(QueueState* q, LevelCounters* ctr, const unsigned int* status,
-                           cudaGraphConditionalHandle h, unsigned long long max_iter) {
+// End of a batch, after its scatter: continue while items remain, no list
+// overflowed, the device status is clean and the iteration limit is not
+// reached; inside the graph, also say which span lists the batch filled.
+__global__ void k_batch_end(QueueState* q, const LevelCounters* ctr, const unsigned int* status, LoopHandles hs,
+                            unsigned long long max_iter) {
   pdl_wait();
-  ctr->n_base_small = 0;
-  ctr->n_base_large = 0;
-  ctr->n_copy = 0;
-  ctr->n_fallback = 0;
   const bool err = ctr->overflow != 0 || *status != 0;
   const unsigned long long it = q->iter + 1;
   q->iter = it;
@@ -282,13 +290,19 @@ __global__ void k_loop_ctl(QueueState* q, LevelCounters* ctr, const unsigned int
     q->err = 1;
   }
   q->cont = c;
-  if (h) cudaGraphSetConditional(h, c);
+  if (hs.in_graph) {
+    cudaGraphSetConditional(hs.small, ctr->n_base_small > 0);
+    cudaGraphSetConditional(hs.large, ctr->n_base_large > 0);
+    cudaGraphSetConditional(hs.copy, ctr->n_copy > 0);
+    cudaGraphSetConditional(hs.fallback, ctr->n_fallback > 0);
+    cudaGraphSetConditional(hs.loop, c);
+  }
 }
 
 }  // namespace
 
-void launch_plan_batch(const PlanArgs& a, const RunParams& rp, cudaStream_t st) {
-  pdl_launch(k_plan_batch, 1, kPlanTPB, 0, st, a, rp);
+void launch_plan_batch(const PlanArgs& a, const RunParams& rp, const LoopHandles& h, cudaStream_t st) {
+  pdl_launch(k_plan_batch, 1, kPlanTPB, 0, st, a, rp, h);
 }
 
 void launch_zero_counts(const BatchDesc* bd, const Plan* plans, unsigned long long* counts, cudaStream_t st) {
@@ -298,9 +312,9 @@ void launch_zero_counts(const BatchDesc* bd, const Plan* plans, unsigned long lo
   pdl_launch(k_zero_counts, (unsigned)(sms > 0 ? sms : 1) * 4, 256, 0, st, bd, plans, counts);
 }
 
-void launch_loop_ctl(QueueState* q, LevelCounters* ctr, const unsigned int* status, cudaGraphConditionalHandle h,
-                     unsigned long long max_iter, cudaStream_t st) {
-  pdl_launch(k_loop_ctl, 1, 1, 0, st, q, ctr, status, h, max_iter);
+void launch_batch_end(QueueState* q, const LevelCounters* ctr, const unsigned int* status, const LoopHandles& h,
+                      unsigned long long max_iter, cudaStream_t st) {
+  pdl_launch(k_batch_end, 1, 1, 0, st, q, ctr, status, h, max_iter);
 }
 
 }  // namespace lsg

@@ -24,6 +24,12 @@ const uint32_t kFanouts[] = {256, 512, 1000, 1024, 2048};
 const uint32_t kThresholds[] = {1024, 2048, 4096, 8192};
 const double kRates[] = {0.0025, 0.005, 0.01, 0.02};
 const int32_t kRecurse[] = {LS_RECURSE_REFINE_GLOBAL, LS_RECURSE_RETRAIN};
+// A candidate replaces the current configuration only when it is faster by
+// this fraction: single sorts of a tuning array are short, and changes
+// within the timing noise would otherwise decide (and a choice that wins by
+// noise on one array can lose on the batched form it is tuned for).
+constexpr double kMinGain = 0.05;
+constexpr int kTimedReps = 5;  // timed sorts per configuration (median), after one warm-up
 
 struct Scratch {
   void* keys = nullptr;
@@ -34,10 +40,12 @@ struct Scratch {
   }
 };
 
-// Median of three timed sorts of a fresh copy of d_keys (after one warm-up
-// sort), in ms; negative on failure (*st gets the failing status).
-double time_config(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params& p, Scratch& s,
-                   size_t ws_bytes, cudaStream_t stream, ls_status* st) {
+// Median of kTimedReps timed sorts of a fresh copy of d_keys (after one
+// warm-up sort), in ms; negative on failure (*st gets the failing status).
+// h_off (nullable): the segments of a segmented sort (nseg + 1 offsets).
+double time_config(ls_ctx* ctx, const void* d_keys, uint64_t n, const uint64_t* h_off, uint32_t nseg,
+                   ls_dtype dtype, const ls_params& p, Scratch& s, size_t ws_bytes, cudaStream_t stream,
+                   ls_status* st) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) {
     *st = LS_ECUDA;
@@ -48,15 +56,17 @@ double time_config(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, 
     *st = LS_ECUDA;
     return -1.0;
   }
-  double t[3] = {0, 0, 0};
+  double t[kTimedReps] = {};
   *st = LS_OK;
-  for (int rep = 0; rep < 4 && *st == LS_OK; ++rep) {
+  for (int rep = 0; rep <= kTimedReps && *st == LS_OK; ++rep) {
     if (cudaMemcpyAsync(s.keys, d_keys, n * 8, cudaMemcpyDeviceToDevice, stream) != cudaSuccess) {
       *st = LS_ECUDA;
       break;
     }
     cudaEventRecord(e0, stream);
-    ls_status r = ls_sort(ctx, s.keys, n, dtype, &p, s.ws, ws_bytes, nullptr, stream);
+    ls_status r = h_off ? ls_sort_segmented(ctx, s.keys, h_off, nseg, dtype, &p, s.ws, ws_bytes, nullptr, nullptr,
+                                            stream)
+                        : ls_sort(ctx, s.keys, n, dtype, &p, s.ws, ws_bytes, nullptr, stream);
     cudaEventRecord(e1, stream);
     if (r != LS_OK) {
       *st = r;
@@ -73,17 +83,17 @@ double time_config(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (*st != LS_OK) return -1.0;
-  std::sort(t, t + 3);
-  return t[1];
+  std::sort(t, t + kTimedReps);
+  return t[kTimedReps / 2];
 }
 
-}  // namespace
-
-extern "C" {
-
-ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* base,
-                      ls_params* out, ls_tune_report* report, ls_stream_t stream) {
+// Coordinate descent over the candidate lists for one array (h_off null)
+// or one batch of segments; the table key is floor(log2) of the array's
+// length or of the mean segment length.
+ls_status tune(ls_ctx* ctx, const void* d_keys, uint64_t n, const uint64_t* h_off, uint32_t nseg, ls_dtype dtype,
+               const ls_params* base, ls_params* out, ls_tune_report* report, ls_stream_t stream) {
   if (!ctx || !base || !out || (!d_keys && n) || (dtype != LS_F64 && dtype != LS_U64) || n < 2) return LS_EINVAL;
+  const uint32_t wseg = h_off ? nseg : 1u;
   ls_params cur = *base;
   cur.flags &= ~LS_FLAG_TUNED;  // time what is asked, not an earlier entry
   cur.flags &= ~LS_FLAG_TIME_PASSES;
@@ -99,12 +109,12 @@ ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtyp
           probe.recurse_model = m;
           probe.basecase_threshold = cur.basecase_threshold;
           size_t b = 0;
-          ls_status v = ls_workspace_size(ctx, n, 1, dtype, &probe, &b);
+          ls_status v = ls_workspace_size(ctx, n, wseg, dtype, &probe, &b);
           if (v != LS_OK) return v;
           ws_max = std::max(ws_max, b);
           for (uint32_t T : kThresholds) {
             probe.basecase_threshold = T;
-            v = ls_workspace_size(ctx, n, 1, dtype, &probe, &b);
+            v = ls_workspace_size(ctx, n, wseg, dtype, &probe, &b);
             if (v != LS_OK) return v;
             ws_max = std::max(ws_max, b);
           }
@@ -116,16 +126,16 @@ ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtyp
   if (cudaMalloc(&s.keys, n * 8) != cudaSuccess) return LS_ENOMEM;
   if (cudaMalloc(&s.ws, ws_max) != cudaSuccess) return LS_ENOMEM;
   ls_status sv = LS_OK;
-  double best = time_config(ctx, d_keys, n, dtype, cur, s, ws_max, st, &sv);
+  double best = time_config(ctx, d_keys, n, h_off, nseg, dtype, cur, s, ws_max, st, &sv);
   if (best < 0.0) return sv;
   const double base_ms = best;
   uint32_t configs = 1;
   auto consider = [&](const ls_params& cand) -> ls_status {
     ls_status r = LS_OK;
-    double ms = time_config(ctx, d_keys, n, dtype, cand, s, ws_max, st, &r);
+    double ms = time_config(ctx, d_keys, n, h_off, nseg, dtype, cand, s, ws_max, st, &r);
     if (ms < 0.0) return r;
     ++configs;
-    if (ms < best) {
+    if (ms < best * (1.0 - kMinGain)) {
       best = ms;
       cur = cand;
     }
@@ -168,7 +178,7 @@ ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtyp
     e.recurse_model = cur.recurse_model;
     e.ms = best;
     std::lock_guard<std::mutex> lk(ctx->tuned_mu);
-    ctx->tuned[ls_tune_key(dtype, n)] = e;
+    ctx->tuned[ls_tune_key(dtype, h_off ? n / nseg : n)] = e;
   }
   if (report) {
     report->configs = configs;
@@ -176,6 +186,25 @@ ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtyp
     report->best_ms = best;
   }
   return LS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ls_status ls_autotune(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, const ls_params* base,
+                      ls_params* out, ls_tune_report* report, ls_stream_t stream) {
+  return tune(ctx, d_keys, n, nullptr, 0, dtype, base, out, report, stream);
+}
+
+ls_status ls_autotune_segmented(ls_ctx* ctx, const void* d_keys, const uint64_t* h_offsets, uint32_t nseg,
+                                ls_dtype dtype, const ls_params* base, ls_params* out, ls_tune_report* report,
+                                ls_stream_t stream) {
+  if (!h_offsets || nseg == 0) return LS_EINVAL;
+  for (uint32_t i = 0; i < nseg; ++i)
+    if (h_offsets[i + 1] < h_offsets[i]) return LS_EINVAL;
+  if (h_offsets[0] != 0) return LS_EINVAL;  // the timed copies cover keys [0, h_offsets[nseg])
+  return tune(ctx, d_keys, h_offsets[nseg], h_offsets, nseg, dtype, base, out, report, stream);
 }
 
 ls_status ls_tune_export(ls_ctx* ctx, char* buf, size_t* bytes) {

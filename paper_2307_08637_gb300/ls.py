@@ -29,7 +29,8 @@ LS_MAX_LEVELS = 48
 EXPORTS = (
     "ls_params_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_sort", "ls_sort_segmented",
     "ls_sort_host", "ls_fit", "ls_classify", "ls_fit_grad", "ls_last_device_status", "ls_model_export",
-    "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_tune_export", "ls_tune_import",
+    "ls_model_import", "ls_status_string", "ls_classify_static", "ls_autotune", "ls_autotune_segmented",
+    "ls_tune_export", "ls_tune_import",
     "ls_sort_host_batch", "ls_sort_pairs", "ls_workspace_size_pairs", "ls_last_error_detail", "ls_sample",
 )
 
@@ -115,7 +116,8 @@ class LevelStats(C.Structure):
 
 LS_FLAG_TIME_PASSES = 1
 LS_FLAG_TUNED = 2
-LS_FLAG_HOST_LEVELS = 4
+LS_FLAG_DEVICE_LEVELS = 4
+LS_LOOP_HOST, LS_LOOP_DEVICE, LS_LOOP_GRAPH, LS_LOOP_GRAPH_PDL = 0, 1, 2, 3
 PASS_NAMES = ("sample", "fit", "pivots", "classify", "children", "scatter", "base", "copy")
 
 
@@ -140,6 +142,9 @@ class Stats(C.Structure):
         ("ms_total", C.c_double),
         ("kernel_launches", C.c_uint64),
         ("pass_", PassTime * len(PASS_NAMES)),
+        ("device_batches", C.c_uint64),
+        ("level_loop", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
     def passes(self) -> dict:
@@ -208,6 +213,9 @@ def lib() -> C.CDLL:
     L.ls_sample.restype = C.c_int
     L.ls_autotune.argtypes = [vp, vp, u64, C.c_int, C.POINTER(Params), C.POINTER(Params), C.POINTER(TuneReport), vp]
     L.ls_autotune.restype = C.c_int
+    L.ls_autotune_segmented.argtypes = [vp, vp, C.POINTER(C.c_uint64), C.c_uint32, C.c_int, C.POINTER(Params),
+                                        C.POINTER(Params), C.POINTER(TuneReport), vp]
+    L.ls_autotune_segmented.restype = C.c_int
     L.ls_tune_export.argtypes = [vp, C.c_char_p, C.POINTER(C.c_size_t)]
     L.ls_tune_export.restype = C.c_int
     L.ls_tune_import.argtypes = [vp, C.c_char_p]
@@ -535,6 +543,23 @@ def ls_autotune(ctx: Context, keys, base: Params | None = None, stream=None) -> 
     rc = lib().ls_autotune(ctx.handle, _ptr(keys), keys.numel(), _dtype_code(keys), C.byref(base), C.byref(out),
                            C.byref(rep), _stream(stream))
     _check(rc, "ls_autotune")
+    return out, rep
+
+
+def ls_autotune_segmented(ctx: Context, keys, offsets, base: Params | None = None,
+                          stream=None) -> tuple[Params, TuneReport]:
+    """ls_autotune for the segmented form: candidates are timed on
+    ls_sort_segmented of copies of keys[:offsets[-1]] split at `offsets`
+    (offsets[0] = 0); the winner is stored for the mean segment length."""
+    base = base or ls_params_default()
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    if off.ndim != 1 or off.size < 2 or int(off[-1]) > keys.numel():
+        raise ValueError("offsets must be nseg + 1 non-decreasing values within the keys")
+    out = Params()
+    rep = TuneReport()
+    rc = lib().ls_autotune_segmented(ctx.handle, _ptr(keys), off.ctypes.data_as(C.POINTER(C.c_uint64)), off.size - 1,
+                                     _dtype_code(keys), C.byref(base), C.byref(out), C.byref(rep), _stream(stream))
+    _check(rc, "ls_autotune_segmented")
     return out, rep
 
 

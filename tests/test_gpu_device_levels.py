@@ -1,6 +1,7 @@
-"""Levels planned on the device (the device work queue run as one CUDA graph),
-the same queue launched batch by batch from the host (pass timing), and
-levels planned on the host (LS_FLAG_HOST_LEVELS): the three forms must give
+"""Levels planned on the device (LS_FLAG_DEVICE_LEVELS: the device work queue
+run as one CUDA graph), the same queue launched batch by batch from the host
+(with pass timing), and levels planned on the host (the default): the three
+forms must give
 the oracle's sorted output and per-level statistics bit for bit.  The cases
 cover deep refinement chains, the radix split, the depth-limit fallback,
 items handed back to the host planner (buckets below a splitter tree draw
@@ -19,7 +20,15 @@ if not torch.cuda.is_available():
 
 import paper_2307_08637_gb300 as lsg  # noqa: E402
 
-FORMS = {"graph": 0, "host_iterated": lsg.LS_FLAG_TIME_PASSES, "host_planned": lsg.LS_FLAG_HOST_LEVELS}
+FORMS = {"graph": lsg.LS_FLAG_DEVICE_LEVELS, "host_iterated": lsg.LS_FLAG_DEVICE_LEVELS | lsg.LS_FLAG_TIME_PASSES,
+         "host_planned": 0}
+LOOPS = {"graph": (lsg.LS_LOOP_GRAPH, lsg.LS_LOOP_GRAPH_PDL), "host_iterated": (lsg.LS_LOOP_DEVICE,),
+         "host_planned": (lsg.LS_LOOP_HOST,)}
+
+
+def _check_form(name, st):
+    assert st.level_loop in LOOPS[name], (name, st.level_loop)
+    assert (st.device_batches > 0) == (name != "host_planned"), (name, st.device_batches)
 
 
 @pytest.fixture(scope="module")
@@ -40,6 +49,7 @@ def _check(ctx, x, **kw):
         assert bad.size == 0, (name, "sorted output differs", bad[:5])
         assert st.root_decision == tr.root_decision, name
         assert st.levels() == tr.levels(), (name, st.levels(), tr.levels())
+        _check_form(name, st)
     return tr
 
 
@@ -48,6 +58,14 @@ def test_device_levels_f64(ctx, dist):
     x = datagen.generate(dist, 1_500_000, 21)
     tr = _check(ctx, x, basecase_threshold=512)
     assert tr.levels_used >= 3
+
+
+@pytest.mark.parametrize("dist", ["normal", "exponential"])
+def test_device_levels_bench_parameters(ctx, dist):
+    """The bench's parameters (B = 1000, T = 4096: no item of the queue
+    uses the direct classifier)."""
+    x = datagen.generate(dist, 6_000_000, 25)
+    _check(ctx, x, basecase_threshold=4096)
 
 
 def test_device_levels_deep_small_fanout(ctx):
@@ -91,6 +109,7 @@ def test_device_levels_segmented(ctx):
         assert np.array_equal(d.cpu().numpy().view(np.uint64), out.view(np.uint64)), name
         assert np.array_equal(np.asarray(gdec), dec), name
         assert st.levels() == tr.levels(), name
+        _check_form(name, st)
 
 
 def test_device_levels_graph_reused(ctx):
@@ -100,11 +119,14 @@ def test_device_levels_graph_reused(ctx):
     out, rc, tr, _, _ = oracle.sort(x, oracle.params())
     d = torch.from_numpy(x).to("cuda:0")
     ws = ctx.workspace(x.size, 1, lsg.LS_F64, lsg.ls_params_default())
+    p = lsg.ls_params_default(flags=lsg.LS_FLAG_DEVICE_LEVELS)
     for _ in range(3):
         d.copy_(torch.from_numpy(x))
-        st = lsg.ls_sort(ctx, d, lsg.ls_params_default(), workspace=ws)
+        st = lsg.ls_sort(ctx, d, p, workspace=ws)
         assert np.array_equal(d.cpu().numpy().view(np.uint64), out.view(np.uint64))
         assert st.levels() == tr.levels()
+        _check_form("graph", st)
     e = torch.from_numpy(x).to("cuda:0")
-    lsg.ls_sort(ctx, e, lsg.ls_params_default(), workspace=ws)
+    st = lsg.ls_sort(ctx, e, p, workspace=ws)
     assert np.array_equal(e.cpu().numpy().view(np.uint64), out.view(np.uint64))
+    _check_form("graph", st)

@@ -66,6 +66,35 @@ def test_autotune_then_tuned_sort_matches_oracle(tmp_path):
     ctx.close()
 
 
+def test_autotune_segmented_then_tuned_segmented_sort_matches_oracle():
+    """The segmented tuner times ls_sort_segmented on the caller's batch and
+    stores the winner under the mean segment length, where a segmented sort
+    flagged TUNED finds it."""
+    ctx = lsg.Context(0)
+    keys, off, _ = datagen.segmented(96, 8, lo=1000, hi=2e5)
+    d = torch.from_numpy(keys).to("cuda:0")
+    before = d.clone()
+    tuned, rep = lsg.ls_autotune_segmented(ctx, d, off, lsg.ls_params_default())
+    torch.cuda.synchronize()
+    assert torch.equal(d, before)
+    assert tuned.fanout in FANOUTS and tuned.basecase_threshold in THRESHOLDS and tuned.sample_rate in RATES
+    assert 0 < rep.best_ms <= rep.base_ms
+    recs = lsg.tune_text_to_json(lsg.ls_tune_export(ctx))
+    mean = int(off[-1]) // (off.size - 1)
+    assert [(r["dtype"], r["log2n"]) for r in recs] == [(lsg.LS_F64, mean.bit_length() - 1)]
+    st, dec = lsg.ls_sort_segmented(ctx, d, off, lsg.ls_params_default(flags=lsg.LS_FLAG_TUNED))
+    out, rc, tr, odec = oracle.sort_segmented(keys, off, oracle.params(
+        fanout=tuned.fanout, basecase_threshold=tuned.basecase_threshold, sample_rate=tuned.sample_rate,
+        recurse_model=tuned.recurse_model))
+    assert rc == 0
+    assert np.array_equal(d.cpu().numpy().view(np.uint64), out.view(np.uint64))
+    assert np.array_equal(np.asarray(dec), odec)
+    assert st.levels() == tr.levels()
+    with pytest.raises(ValueError):
+        lsg.ls_autotune_segmented(ctx, d, np.array([0, keys.size + 1], dtype=np.uint64))
+    ctx.close()
+
+
 def test_tuned_flag_without_entry_uses_given_params():
     ctx = lsg.Context(0)
     x = datagen.generate("normal", 300_000, 4)
