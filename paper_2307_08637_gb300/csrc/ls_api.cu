@@ -150,7 +150,7 @@ struct Layout {
   size_t total = 0;
   size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
-      o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_ids,
+      o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_fclamps, o_ids,
       o_vbuf, o_bruns, o_bitems, o_hostq, o_reflist, o_bdesc, o_queue;
   size_t stmp_elems = 0;
   size_t misc_bytes = 0;
@@ -205,6 +205,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.o_leafcnt = take(l.mcap * l.L * 4);
   l.o_fmodels = take(l.mcap * sizeof(FModel));
   l.o_fleaves = take(l.mcap * l.L * sizeof(FLeaf));
+  l.o_fclamps = take(l.mcap * l.L * sizeof(FClamp));
   l.o_samp0 = take(l.scap * 8);
   l.o_samp1 = take(l.scap * 8);
   l.o_rpart = take(8 * l.rchunk_cap * 8);
@@ -500,7 +501,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
     s.timer.end();
     s.launches += 2;
     if (!cand.empty()) {
-      FitArgs fa;
+      FitArgs fa{};
       fa.plans = d_plans;
       fa.items = d_items;
       fa.cand = d_cand;
@@ -526,6 +527,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
       fa.leaf_cnt = at<uint32_t>(s.ws, L.o_leafcnt);
       fa.fmodels = at<FModel>(s.ws, L.o_fmodels);
       fa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
+      fa.fclamps = at<FClamp>(s.ws, L.o_fclamps);
       if (fa.total_rchunks > L.rchunk_cap || fa.lchunk_bound > L.lchunk_cap) return LS_ENOMEM;
       s.timer.begin(LS_PASS_FIT, cand_soff.back());
       launch_fit(fa, s.rp, st, &s.launches);
@@ -579,7 +581,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   }
   uint32_t aux = 16;
   if (any_dir) aux = std::max<uint32_t>(aux, ((L.cells + 1) * 2 + 15) & ~15u);
-  if (any_guess) aux = std::max<uint32_t>(aux, L.L * (uint32_t)sizeof(FLeaf));
+  if (any_guess) aux = std::max<uint32_t>(aux, L.L * (uint32_t)(sizeof(FLeaf) + sizeof(FClamp)));
 
   // ---- partition passes
   PassArgs pa{};
@@ -619,6 +621,7 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   pa.dir_cells_max = L.cells;
   pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
   pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
+  pa.fclamps = at<FClamp>(s.ws, L.o_fclamps);
   pa.aux_bytes = aux;
   pa.cls_mask = cls_mask;
   pa.valsA = s.VA;
@@ -922,7 +925,8 @@ uint64_t launch_device_batch(Sorter& s, BatchSink& k, PassTimer* tm) {
   pa.leaves = leaves;
   pa.fmodels = at<FModel>(s.ws, L.o_fmodels);
   pa.fleaves = at<FLeaf>(s.ws, L.o_fleaves);
-  pa.aux_bytes = guess ? std::max<uint32_t>(16, L.L * (uint32_t)sizeof(FLeaf)) : 16;
+  pa.fclamps = at<FClamp>(s.ws, L.o_fclamps);
+  pa.aux_bytes = guess ? std::max<uint32_t>(16, L.L * (uint32_t)(sizeof(FLeaf) + sizeof(FClamp))) : 16;
   pa.ids = at<uint16_t>(s.ws, L.o_ids);
   pa.counts = counts;
   pa.cursors = cursors;
@@ -1743,7 +1747,7 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
   const uint64_t* sorted = segmented_sort_u64(samp0, samp1, misc + 5 * M, misc + 6 * M, 1, scp[1], S, st,
                                               &s.launches);
   launch_dups(f, sorted, st);
-  FitArgs fa;
+  FitArgs fa{};
   fa.plans = d_plans;
   fa.items = d_items;
   fa.cand = reinterpret_cast<uint32_t*>(misc + 2 * M);
@@ -1769,6 +1773,7 @@ ls_status ls_fit(ls_ctx* ctx, const void* d_keys, uint64_t n, ls_dtype dtype, co
   fa.leaf_cnt = at<uint32_t>(ws, lay.o_leafcnt);
   fa.fmodels = at<FModel>(ws, lay.o_fmodels);
   fa.fleaves = at<FLeaf>(ws, lay.o_fleaves);
+  fa.fclamps = at<FClamp>(ws, lay.o_fclamps);
   launch_fit(fa, s.rp, st, &s.launches);
   uint64_t* pivots = at<uint64_t>(ws, lay.o_pivots);
   unsigned long long* counts = at<unsigned long long>(ws, lay.o_counts);

@@ -55,6 +55,8 @@ struct FModel {
   uint64_t leaf_off;  // offset into the FLeaf pool (same as the FP64 leaves)
 };
 typedef float4 FLeaf;
+// FP32 image of a leaf's monotone clamps [lo, hi] (Sec. 4).
+typedef float2 FClamp;
 
 // A range of keys still to be partitioned (a bucket of the previous level).
 struct Item {
@@ -291,15 +293,22 @@ __device__ __forceinline__ float key_to_float(uint64_t bits, int dt) {
 }
 
 // Bucket guess from the FP32 model image (leaves in shared memory), for
-// refinement scale P and offset Bg; clamped to [0, kmax].
-__device__ __forceinline__ uint32_t guess_bucket(const FModel& m, const FLeaf* __restrict__ fl, float Pf, float Bgf,
-                                                 uint32_t kmax, uint64_t bits, int dt) {
+// refinement scale P and offset Bg; clamped to [0, kmax].  fc (nullable):
+// the leaves' clamps, without which refined guesses (P = B^2 and beyond)
+// are often several buckets off where a clamp binds.
+__device__ __forceinline__ uint32_t guess_bucket(const FModel& m, const FLeaf* __restrict__ fl,
+                                                 const FClamp* __restrict__ fc, float Pf, float Bgf, uint32_t kmax,
+                                                 uint64_t bits, int dt) {
   float x = key_to_float(bits, dt);
   x = fminf(fmaxf(x, m.xminf), m.xmaxf);
   float r = __fmaf_rn(m.raL, x - m.rx0f, m.rbL);
   int li = (int)fminf(fmaxf(floorf(r), 0.0f), (float)(m.L - 1));
   FLeaf l = fl[li];
   float F = __fmaf_rn(l.y, x - l.x, l.z);
+  if (fc) {
+    const FClamp c = fc[li];
+    F = fminf(fmaxf(F, c.x), c.y);
+  }
   float t = floorf(__fmaf_rn(F, Pf, -Bgf));
   t = fminf(fmaxf(t, 0.0f), (float)kmax);  // NaN-free inputs: the model image is finite
   return (uint32_t)t;

@@ -1307,11 +1307,12 @@ __global__ void k_grad_root_finish(uint64_t S, uint64_t nch, GradScratch g, doub
 
 // FP32 image of model slot `slot`: thread per leaf, one extra for the root.
 __device__ __forceinline__ void fmodel_one(const DModel* models, const Leaf* leaves, int32_t slot, uint32_t i,
-                                           uint32_t L, FModel* fm, FLeaf* fl) {
+                                           uint32_t L, FModel* fm, FLeaf* fl, FClamp* fc) {
   const DModel& m = models[slot];
   if (i < L) {
     Leaf l = leaves[m.leaf_off + i];
     fl[m.leaf_off + i] = make_float4(__double2float_rn(l.x0), __double2float_rn(l.a), __double2float_rn(l.b), 0.0f);
+    if (fc) fc[m.leaf_off + i] = make_float2(__double2float_rn(l.lo), __double2float_rn(l.hi));
   } else if (i == L) {
     FModel f;
     f.xminf = __double2float_rn(m.xmin);
@@ -1326,12 +1327,12 @@ __device__ __forceinline__ void fmodel_one(const DModel* models, const Leaf* lea
 }
 
 __global__ void k_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots,
-                         uint32_t L, FModel* fm, FLeaf* fl) {
+                         uint32_t L, FModel* fm, FLeaf* fl, FClamp* fc) {
   pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= (uint64_t)nslots * (L + 1)) return;
   uint32_t c = (uint32_t)(g / (L + 1)), i = (uint32_t)(g % (L + 1));
-  fmodel_one(models, leaves, slots[c], i, L, fm, fl);
+  fmodel_one(models, leaves, slots[c], i, L, fm, fl, fc);
 }
 
 __global__ void k_fmodel_fit(FitArgs a) {
@@ -1339,7 +1340,7 @@ __global__ void k_fmodel_fit(FitArgs a) {
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (g >= (uint64_t)a.ncand * (a.L + 1)) return;
   uint32_t c = (uint32_t)(g / (a.L + 1)), i = (uint32_t)(g % (a.L + 1));
-  fmodel_one(a.models, a.leaves, a.plans[a.cand[c]].model, i, a.L, a.fmodels, a.fleaves);
+  fmodel_one(a.models, a.leaves, a.plans[a.cand[c]].model, i, a.L, a.fmodels, a.fleaves, a.fclamps);
 }
 
 }  // namespace
@@ -1397,9 +1398,9 @@ void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t
 }
 
 void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
-                   FModel* fm, FLeaf* fl, cudaStream_t st) {
+                   FModel* fm, FLeaf* fl, cudaStream_t st, FClamp* fc) {
   if (!nslots) return;
-  pdl_launch(k_fmodel, grid_for((uint64_t)nslots * (L + 1)), kTPB, 0, st, models, leaves, slots, nslots, L, fm, fl);
+  pdl_launch(k_fmodel, grid_for((uint64_t)nslots * (L + 1)), kTPB, 0, st, models, leaves, slots, nslots, L, fm, fl, fc);
 }
 
 void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list, uint32_t nlist, uint32_t nb_pad,

@@ -147,12 +147,13 @@ struct FitArgs {
   uint32_t* leaf_cnt;          // per model slot * L (sample points per leaf)
   FModel* fmodels;             // per model slot: FP32 image header
   FLeaf* fleaves;              // per model slot * L: FP32 image leaves
+  FClamp* fclamps;             // per model slot * L: FP32 image of the leaves' clamps
 };
 void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches);
 
 // FP32 images of the models of one slot list (used for bucket guesses).
 void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
-                   FModel* fm, FLeaf* fl, cudaStream_t st);
+                   FModel* fm, FLeaf* fl, cudaStream_t st, FClamp* fc = nullptr);
 void launch_fmodel_for_fit(const FitArgs& a, cudaStream_t st);
 
 // Exact learned pivots for items whose plan has decision candidate LEARNED:
@@ -196,7 +197,8 @@ struct PassArgs {
   const Leaf* leaves;
   const FModel* fmodels;
   const FLeaf* fleaves;
-  uint32_t aux_bytes;           // shared-memory bytes for a directory or FP32 leaves
+  const FClamp* fclamps;        // the leaves' clamps (beside the FP32 leaves)
+  uint32_t aux_bytes;           // shared-memory bytes for a directory or the FP32 leaves and clamps
   uint32_t cls_mask;            // bit c set when some item of the batch uses classifier c
   uint16_t* ids;                // per key (same offsets as the keys): bucket id written by K1, read by K3
   unsigned long long* counts;   // per plan: nb counts

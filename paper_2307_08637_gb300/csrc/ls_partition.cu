@@ -86,8 +86,13 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
     c.fm = a.fmodels[pl.model];
     if (aux_model != pl.model) {
       const FLeaf* F = a.fleaves + c.fm.leaf_off;
+      const FClamp* C = a.fclamps + c.fm.leaf_off;
       FLeaf* sF = static_cast<FLeaf*>(sAux);
-      for (uint32_t j = threadIdx.x; j < c.fm.L; j += blockDim.x) sF[j] = F[j];
+      FClamp* sC = reinterpret_cast<FClamp*>(sF + c.fm.L);
+      for (uint32_t j = threadIdx.x; j < c.fm.L; j += blockDim.x) {
+        sF[j] = F[j];
+        sC[j] = C[j];
+      }
       aux_model = pl.model;
     }
   }
@@ -128,7 +133,9 @@ __device__ __forceinline__ uint32_t classify_as(uint64_t bits, const Cls& c, con
   const uint64_t u = ord_of(bits, DT);
   if (CLS == CLS_RADIX) return (uint32_t)(u >> c.shift) & c.kmax;  // kmax = buckets - 1, a power of two minus 1
   if (CLS == CLS_GUESS) {
-    const uint32_t g = guess_bucket(c.fm, static_cast<const FLeaf*>(sAux), c.Pf, c.Bgf, c.kmax, bits, DT);
+    const FLeaf* sF = static_cast<const FLeaf*>(sAux);
+    const uint32_t g = guess_bucket(c.fm, sF, reinterpret_cast<const FClamp*>(sF + c.fm.L), c.Pf, c.Bgf, c.kmax, bits,
+                                    DT);
     return fix_guess(sT, c.nb_pad, c.kmax, g, u);
   }
   const uint32_t b = (CLS == CLS_DIR)
@@ -2140,7 +2147,7 @@ __global__ void k_table_classify(const Plan* plan, const uint64_t* pivots, const
       uint64_t bits = keys[i];
       uint64_t u = ord_of(bits, dt);
       if (pl.cls == CLS_GUESS) {
-        b = fix_bucket(sT, nb_pad, pl.kmax, guess_bucket(fm, sF, Pf, Bgf, pl.kmax, bits, dt), u);
+        b = fix_bucket(sT, nb_pad, pl.kmax, guess_bucket(fm, sF, nullptr, Pf, Bgf, pl.kmax, bits, dt), u);
       } else {
         b = (pl.cls == CLS_DIR) ? pivot_count_dir(sT, sD, pl.dir_lo, pl.dir_hi, pl.dir_shift, pl.kmax, u)
                                 : pivot_count(sT, nb_pad, u);
