@@ -145,10 +145,10 @@ RunParams make_rp(const ls_params* p, int dt) {
 struct Layout {
   uint64_t n = 0;
   uint32_t L = 0, nbc = 0, cells = 0;
-  uint64_t icap = 0, scap = 0, mcap = 0, base_cap = 0, large_cap = 0, copy_cap = 0, fb_cap = 0;
+  uint64_t icap = 0, scap = 0, mcap = 0, base_cap = 0, mid_cap = 0, large_cap = 0, copy_cap = 0, fb_cap = 0;
   uint64_t rchunk_cap = 0, lchunk_cap = 0, chunk_cap = 0, seg_cap = 0, brun_cap = 0;
   size_t total = 0;
-  size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_large, o_copy, o_fb,
+  size_t o_buf, o_cur, o_next, o_plans, o_counts, o_cursors, o_pivots, o_dirs, o_small, o_mid, o_large, o_copy, o_fb,
       o_models, o_leaves, o_leafcnt, o_samp0, o_samp1, o_rpart, o_lstart, o_lcnt, o_lpre, o_lpart, o_leafof,
       o_stmp, o_stats, o_ctr, o_rootplan, o_misc, o_agg, o_excl, o_segs, o_multi, o_chunkctr, o_chunkplan, o_fmodels, o_fleaves, o_fclamps, o_ids,
       o_vbuf, o_bruns, o_bitems, o_hostq, o_reflist, o_bdesc, o_queue;
@@ -171,6 +171,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.scap = std::max<uint64_t>(smax, 64ull * p->min_sample) + 1024;
   l.mcap = 1024 + n / 65536;
   l.base_cap = n / 2 + 1024;
+  l.mid_cap = n / (kWarpSmallMax + 1) + 1024;
   l.large_cap = n / (kWarpSortMax + 1) + 1024;
   l.copy_cap = n / 2 + l.icap + 64 * 1024;  // <= one run of final buckets per non-final child + item
   l.fb_cap = n / (T + 1) + 1024;
@@ -197,6 +198,7 @@ Layout compute_layout(uint64_t n, uint32_t nseg, const ls_params* p, uint32_t vb
   l.o_pivots = take((size_t)kBatchItems * l.nbc * 8);
   l.o_dirs = take((size_t)kBatchItems * (l.cells + 1) * 2);
   l.o_small = take(l.base_cap * sizeof(Span));
+  l.o_mid = take(l.mid_cap * sizeof(Span));
   l.o_large = take(l.large_cap * sizeof(Span));
   l.o_copy = take(l.copy_cap * sizeof(Span));
   l.o_fb = take(l.fb_cap * sizeof(Span));
@@ -675,8 +677,10 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
   ca.next = at<Item>(s.ws, L.o_next);
   ca.next_cap = L.icap;
   ca.base_small = at<Span>(s.ws, L.o_small);
+  ca.base_mid = at<Span>(s.ws, L.o_mid);
   ca.base_large = at<Span>(s.ws, L.o_large);
   ca.base_cap = L.base_cap;
+  ca.mid_cap = L.mid_cap;
   ca.large_cap = L.large_cap;
   ca.copy = at<Span>(s.ws, L.o_copy);
   ca.copy_cap = L.copy_cap;
@@ -756,10 +760,12 @@ ls_status run_batch(Sorter& s, const Item* items, uint32_t nitems, bool level0, 
 // Sort / copy the finished spans of one level.
 ls_status finish_spans(Sorter& s, const LevelCounters& c) {
   Layout& L = s.lay;
-  if (c.n_base_small || c.n_base_large || c.n_fallback) {
+  if (c.n_base_small || c.n_base_mid || c.n_base_large || c.n_fallback) {
     s.timer.begin(LS_PASS_BASE, 0);
     if (c.n_base_small)
-      launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st);
+      launch_base_small(at<Span>(s.ws, L.o_small), c.n_base_small, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st, false);
+    if (c.n_base_mid)
+      launch_base_small(at<Span>(s.ws, L.o_mid), c.n_base_mid, s.A, s.Bb, s.VA, s.VBb, s.vb, s.dt, s.st, true);
     if (c.n_base_large)
       s.launches += launch_base_large(at<Span>(s.ws, L.o_large), c.n_base_large, s.p->basecase_threshold, s.A, s.Bb,
                                       s.VA, s.VBb, s.vb, s.dt, s.st) - 1;
@@ -772,7 +778,7 @@ ls_status finish_spans(Sorter& s, const LevelCounters& c) {
     launch_copy_spans(at<Span>(s.ws, L.o_copy), c.n_copy, s.A, s.Bb, s.VA, s.VBb, s.vb, s.st);
     s.timer.end();
   }
-  s.launches += (c.n_base_small > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
+  s.launches += (c.n_base_small > 0) + (c.n_base_mid > 0) + (c.n_base_large > 0) + (c.n_copy > 0) + (c.n_fallback > 0);
   CK(cudaGetLastError());
   return LS_OK;
 }
@@ -963,8 +969,10 @@ uint64_t launch_device_batch(Sorter& s, BatchSink& k, PassTimer* tm) {
   ca.next = at<Item>(s.ws, L.o_next);
   ca.next_cap = L.icap;
   ca.base_small = at<Span>(s.ws, L.o_small);
+  ca.base_mid = at<Span>(s.ws, L.o_mid);
   ca.base_large = at<Span>(s.ws, L.o_large);
   ca.base_cap = L.base_cap;
+  ca.mid_cap = L.mid_cap;
   ca.large_cap = L.large_cap;
   ca.copy = at<Span>(s.ws, L.o_copy);
   ca.copy_cap = L.copy_cap;
@@ -992,7 +1000,8 @@ uint64_t launch_device_batch(Sorter& s, BatchSink& k, PassTimer* tm) {
   tb(LS_PASS_BASE);
   auto spans = [&](int which) {
     return [&, which](cudaStream_t cs) {
-      return (uint64_t)launch_spans_device(which, ctr, ca.base_small, ca.base_large, ca.copy, ca.fallback, L.base_cap,
+      return (uint64_t)launch_spans_device(which, ctr, ca.base_small, ca.base_mid, ca.base_large, ca.copy, ca.fallback,
+                                           L.base_cap,
                                            p->basecase_threshold, s.A, s.Bb, s.dt, cs);
     };
   };
@@ -1014,7 +1023,8 @@ std::vector<uint64_t> graph_key(const Sorter& s) {
   memcpy(&df, &r.dup_frac, 8);
   memcpy(&tau, &r.tau, 8);
   return {(uint64_t)(uintptr_t)s.ws, (uint64_t)(uintptr_t)s.A, (uint64_t)(uintptr_t)s.ctx->d_status, L.n, L.total,
-          L.icap, L.chunk_cap, L.seg_cap, L.brun_cap, L.base_cap, L.large_cap, L.copy_cap, L.fb_cap, L.nbc, L.cells,
+          L.icap, L.chunk_cap, L.seg_cap, L.brun_cap, L.base_cap, L.mid_cap, L.large_cap, L.copy_cap, L.fb_cap, L.nbc,
+          L.cells,
           L.L, r.B, r.bs_max, r.bs_auto, r.T, r.max_depth, r.min_sample, sr, df, tau, r.min_learned_n, r.seed,
           (uint64_t)(uint32_t)r.partitioner, (uint64_t)(uint32_t)r.recurse, (uint64_t)(uint32_t)r.classify_mode,
           (uint64_t)(uint32_t)r.dt, r.tile, r.dir_bits};
@@ -1232,7 +1242,7 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
   uint64_t olo, ohi;
   ord_range(dtype, &olo, &ohi);
   std::vector<Item> items;
-  std::vector<Span> small, large;
+  std::vector<Span> small, mid, large;
   ls_level_stats root_base;
   memset(&root_base, 0, sizeof root_base);
   for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
@@ -1240,7 +1250,7 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     if (len <= 1) continue;
     if (len <= p->basecase_threshold) {
       Span sp{h_off[sgi], (uint32_t)len, 0u};
-      (len <= kWarpSortMax ? small : large).push_back(sp);
+      (len <= kWarpSmallMax ? small : len <= kWarpSortMax ? mid : large).push_back(sp);
       root_base.base_items += 1;
       root_base.base_keys += len;
       continue;
@@ -1258,14 +1268,16 @@ ls_status sort_impl(ls_ctx* ctx, uint64_t* d_keys, const uint64_t* h_off, uint32
     it.ord_hi = ohi;
     items.push_back(it);
   }
-  if (!small.empty() || !large.empty()) {
+  if (!small.empty() || !mid.empty() || !large.empty()) {
     CK(cudaMemcpyAsync(at<Span>(ws, lay.o_small), small.data(), small.size() * sizeof(Span), cudaMemcpyHostToDevice,
                        st));
+    CK(cudaMemcpyAsync(at<Span>(ws, lay.o_mid), mid.data(), mid.size() * sizeof(Span), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(at<Span>(ws, lay.o_large), large.data(), large.size() * sizeof(Span), cudaMemcpyHostToDevice,
                        st));
     LevelCounters c;
     memset(&c, 0, sizeof c);
     c.n_base_small = small.size();
+    c.n_base_mid = mid.size();
     c.n_base_large = large.size();
     ls_status r = finish_spans(s, c);
     if (r != LS_OK) return r;

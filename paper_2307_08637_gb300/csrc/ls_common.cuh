@@ -22,6 +22,7 @@ constexpr uint64_t kOrdMinF64 = 0x000FFFFFFFFFFFFFull; // ord(-inf)
 constexpr uint64_t kOrdMaxF64 = 0xFFF0000000000000ull; // ord(+inf)
 constexpr uint32_t kMaxBaseCase = 8192;               // largest shared-memory base case
 constexpr uint32_t kWarpSortMax = 256;                // warp-register base case size
+constexpr uint32_t kWarpSmallMax = 128;               // spans up to this size: the warp base case's short class
 constexpr uint32_t kSortChunk = 2048;                 // segmented sample sort chunk
 constexpr uint32_t kTileKeys = 4096;                  // keys per partition tile (256 threads x 16)
 constexpr uint32_t kChunkTiles = 16;                  // tiles per chunk (one lookback unit)
@@ -118,6 +119,7 @@ struct LevelCounters {
   unsigned long long n_copy;       // spans to copy from the buffer
   unsigned long long n_fallback;   // spans past max_depth
   unsigned long long overflow;     // a list ran out of capacity
+  unsigned long long n_base_mid;   // spans for the warp base case's long class (kWarpSmallMax, kWarpSortMax]
 };
 
 // Device-side level statistics (mirrors ls_level_stats field order).

@@ -335,8 +335,10 @@ struct ChildArgs {
   Item* next;
   uint64_t next_cap;
   Span* base_small;
+  Span* base_mid;
   Span* base_large;
   uint64_t base_cap;
+  uint64_t mid_cap;
   uint64_t large_cap;
   Span* copy;
   uint64_t copy_cap;
@@ -354,8 +356,9 @@ void launch_link_copy(const void* src, void* dst, size_t bytes, cudaStream_t st)
 
 // Base cases, copies home and the depth-limit fallback.  VA / VBuf / vb:
 // values of a key-value sort (vb = 4 or 8 bytes; 0 for keys only).
+// mid: the list of spans longer than kWarpSmallMax keys (its own kernel instance).
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
-                       uint32_t vb, int dt, cudaStream_t st);
+                       uint32_t vb, int dt, cudaStream_t st, bool mid);
 // Returns the kernels launched (one per span size class).
 int launch_base_large(const Span* spans, uint64_t n, uint32_t max_len, uint64_t* A, const uint64_t* Bbuf, void* VA,
                       const void* VBuf, uint32_t vb, int dt, cudaStream_t st);
@@ -367,7 +370,7 @@ void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
 // (the level counters); n_max bounds them (grid sizing).  which: SPANS_*.
 // Returns the kernels launched.
 enum { SPANS_SMALL = 1, SPANS_LARGE = 2, SPANS_COPY = 4, SPANS_FALLBACK = 8 };
-int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* large,
+int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* mid, const Span* large,
                         const Span* copy, const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A,
                         uint64_t* Bbuf, int dt, cudaStream_t st);
 

@@ -832,7 +832,7 @@ __device__ __forceinline__ void k2_exchange(uint32_t (&x)[N], uint32_t (&tot)[N]
   }
 }
 
-enum { L_NEXT = 0, L_SMALL, L_LARGE, L_COPY, L_FALLBACK, L_N };
+enum { L_NEXT = 0, L_SMALL, L_MID, L_LARGE, L_COPY, L_FALLBACK, L_N };
 
 // K2, one block per item: bucket starts and write cursors from the counts,
 // the item's level statistics, and the children lists (next level, base
@@ -1029,7 +1029,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   // bucket; one copy run per maximal run of final buckets (only when the
   // destination is the workspace buffer)
   unsigned long long eqk = 0, bk = 0, bki = 0, fbk = 0, fbi = 0;
-  uint32_t nl[L_N] = {0, 0, 0, 0, 0};
+  uint32_t nl[L_N] = {0, 0, 0, 0, 0, 0};
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
     if (eq && (b & 1)) eqk += sz;
@@ -1042,7 +1042,8 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
       continue;
     }
     if (sz <= rp.T) {
-      if (sz <= kWarpSortMax) nl[L_SMALL]++;
+      if (sz <= kWarpSmallMax) nl[L_SMALL]++;
+      else if (sz <= kWarpSortMax) nl[L_MID]++;
       else nl[L_LARGE]++;
       bki++;
       bk += sz;
@@ -1067,6 +1068,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
     for (int q = 0; q < L_N; ++q) {
       unsigned long long* ctr = (q == L_NEXT)    ? &a.ctr->n_next
                                 : (q == L_SMALL) ? &a.ctr->n_base_small
+                                : (q == L_MID)   ? &a.ctr->n_base_mid
                                 : (q == L_LARGE) ? &a.ctr->n_base_large
                                 : (q == L_COPY)  ? &a.ctr->n_copy
                                                  : &a.ctr->n_fallback;
@@ -1085,7 +1087,7 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
   __syncthreads();
   unsigned long long wp[L_N];
   for (int q = 0; q < L_N; ++q) wp[q] = s_base[q] + nl[q];
-  const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.large_cap, a.copy_cap, a.fallback_cap};
+  const uint64_t caps[L_N] = {a.next_cap, a.base_cap, a.mid_cap, a.large_cap, a.copy_cap, a.fallback_cap};
   bool ovf = false;
   for (uint32_t b = b0; b < b1; ++b) {
     uint64_t sz = cnt[b];
@@ -1104,8 +1106,8 @@ __global__ void __launch_bounds__(kK2Threads) k_children(ChildArgs a, RunParams 
       continue;
     }
     if (sz <= rp.T) {
-      int q = sz <= kWarpSortMax ? L_SMALL : L_LARGE;
-      Span* lst = q == L_SMALL ? a.base_small : a.base_large;
+      const int q = sz <= kWarpSmallMax ? L_SMALL : sz <= kWarpSortMax ? L_MID : L_LARGE;
+      Span* lst = q == L_SMALL ? a.base_small : q == L_MID ? a.base_mid : a.base_large;
       if (wp[q] < caps[q]) lst[wp[q]] = Span{clo, (uint32_t)sz, dest};
       else ovf = true;
       wp[q]++;
@@ -1427,17 +1429,25 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
   return true;
 }
 
-__global__ void __launch_bounds__(kTPB, 4) k_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf,
-                                                     int dt, const unsigned long long* dn) {
+// Warp base case in two size classes with lists of their own, so that the
+// short spans (up to kWarpSmallMax keys, most of them) run in an instance
+// with fewer registers and more warps per SM: RHI = 4 takes spans of up to
+// 128 keys, RHI = 8 any span of up to 256.  RLO: spans of at most 32 RLO
+// keys are left to the other instance (0: none).
+template <int RLO, int RHI, int MINB>
+__global__ void __launch_bounds__(kTPB, MINB) k_base_small(const Span* spans, uint64_t n, uint64_t* A,
+                                                          const uint64_t* Bbuf, int dt, const unsigned long long* dn) {
   pdl_wait();
   if (dn) n = *dn;  // span count written on the device
-  __shared__ uint64_t s_keys[kTPB / 32][kWarpSortMax];
-  __shared__ uint32_t s_cnt[kTPB / 32][kSlots];
+  __shared__ uint64_t s_keys[kTPB / 32][32 * RHI];
+  __shared__ uint32_t s_cnt[kTPB / 32][32 * RHI];
   const unsigned wid = threadIdx.x >> 5;
   uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
   for (; w < n; w += nw) {
     const Span s = spans[w];
+    const uint32_t R = (s.n + 31) >> 5;
+    if (R <= RLO || R > RHI) continue;  // the other class's span (uniform across the warp)
     if (s.n < 2) {  // nothing to order; bring home if needed
       if (s.n == 1 && s.buf && (threadIdx.x & 31) == 0) A[s.lo] = Bbuf[s.lo];
       continue;
@@ -1445,23 +1455,39 @@ __global__ void __launch_bounds__(kTPB, 4) k_base_small(const Span* spans, uint6
     uint64_t* sk = s_keys[wid];
     uint32_t* sc = s_cnt[wid];
     bool done;
-    switch ((s.n + 31) >> 5) {  // uniform across the warp
-      case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
-      case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
-      case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
-      case 4: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
-      case 5: done = warp_placed_sort<5>(s, A, Bbuf, dt, sk, sc); break;
-      case 6: done = warp_placed_sort<6>(s, A, Bbuf, dt, sk, sc); break;
-      case 7: done = warp_placed_sort<7>(s, A, Bbuf, dt, sk, sc); break;
-      default: done = warp_placed_sort<8>(s, A, Bbuf, dt, sk, sc); break;
+    if (RHI <= 4) {
+      switch (R) {  // uniform across the warp
+        case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
+        case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
+        case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
+        default: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
+      }
+    } else {
+      switch (R) {
+        case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
+        case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
+        case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
+        case 4: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
+        case 5: done = warp_placed_sort<5>(s, A, Bbuf, dt, sk, sc); break;
+        case 6: done = warp_placed_sort<6>(s, A, Bbuf, dt, sk, sc); break;
+        case 7: done = warp_placed_sort<7>(s, A, Bbuf, dt, sk, sc); break;
+        default: done = warp_placed_sort<8>(s, A, Bbuf, dt, sk, sc); break;
+      }
     }
     if (done) continue;
-    if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
-    else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
-    else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
-    else warp_sort_span<8>(s, A, Bbuf, dt);
+    if (RHI <= 4) {
+      if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
+      else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
+      else warp_sort_span<4>(s, A, Bbuf, dt);
+    } else {
+      if (s.n <= 32) warp_sort_span<1>(s, A, Bbuf, dt);
+      else if (s.n <= 64) warp_sort_span<2>(s, A, Bbuf, dt);
+      else if (s.n <= 128) warp_sort_span<4>(s, A, Bbuf, dt);
+      else warp_sort_span<8>(s, A, Bbuf, dt);
+    }
   }
 }
+static_assert(kWarpSortMax == 256, "the warp base case classes cover spans of up to 8 keys per lane");
 
 // warp_placed_sort for a key-value span: the slots order (ord key, index)
 // pairs (si holds each staged key's index in the span), and the values are
@@ -2374,8 +2400,16 @@ void launch_children(const ChildArgs& a, const RunParams& rp, cudaStream_t st) {
   pdl_launch(k_children, a.nitems, kK2Threads, sm, st, a, rp);
 }
 
+// Keys-only warp base case of one list: mid = false for the short class
+// (spans of up to kWarpSmallMax keys), true for the long one.
+static void launch_small_class(bool mid, const Span* spans, uint64_t n, uint64_t blocks, uint64_t* A,
+                               const uint64_t* Bbuf, int dt, const unsigned long long* dn, cudaStream_t st) {
+  if (mid) pdl_launch(k_base_small<0, 8, 4>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt, dn);
+  else pdl_launch(k_base_small<0, 4, 5>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt, dn);
+}
+
 void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_t* Bbuf, void* VA, const void* VBuf,
-                       uint32_t vb, int dt, cudaStream_t st) {
+                       uint32_t vb, int dt, cudaStream_t st, bool mid) {
   if (!n) return;
   uint64_t warps = n;
   uint64_t blocks = (warps * 32 + kTPB - 1) / kTPB;
@@ -2383,8 +2417,7 @@ void launch_base_small(const Span* spans, uint64_t n, uint64_t* A, const uint64_
   if (blocks > cap) blocks = cap;
   if (vb == 8) pdl_launch(k_base_small_kv<8>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
   else if (vb == 4) pdl_launch(k_base_small_kv<4>, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, VA, VBuf, dt);
-  else pdl_launch(k_base_small, (unsigned)blocks, kTPB, 0, st, spans, n, A, Bbuf, dt,
-                  static_cast<const unsigned long long*>(nullptr));
+  else launch_small_class(mid, spans, n, blocks, A, Bbuf, dt, nullptr, st);
 }
 
 template <typename F>
@@ -2458,7 +2491,7 @@ void launch_fallback(const Span* spans, uint64_t n, uint64_t* A, uint64_t* Bbuf,
                   static_cast<const unsigned long long*>(nullptr));
 }
 
-int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* large,
+int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, const Span* mid, const Span* large,
                         const Span* copy, const Span* fallback, uint64_t n_max, uint32_t max_len, uint64_t* A,
                         uint64_t* Bbuf, int dt, cudaStream_t st) {
   const uint64_t sms = (uint64_t)sm_count();
@@ -2466,9 +2499,9 @@ int launch_spans_device(int which, const LevelCounters* ctr, const Span* small, 
   const uint64_t gs = cap < sms * 16 ? cap : sms * 16;
   int launched = 0;
   if (which & SPANS_SMALL) {
-    pdl_launch(k_base_small, (unsigned)gs, kTPB, 0, st, small, cap, A, static_cast<const uint64_t*>(Bbuf), dt,
-               &ctr->n_base_small);
-    ++launched;
+    launch_small_class(false, small, cap, gs, A, static_cast<const uint64_t*>(Bbuf), dt, &ctr->n_base_small, st);
+    launch_small_class(true, mid, cap, gs, A, static_cast<const uint64_t*>(Bbuf), dt, &ctr->n_base_mid, st);
+    launched += 2;
   }
   if (which & SPANS_LARGE) launched += launch_large_classes(large, cap, max_len, A, Bbuf, dt, &ctr->n_base_large, st);
   if (which & SPANS_COPY) {

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kPlanTPB) k_plan_batch(PlanArgs a, RunParams r
   // planned on the host before the first batch are sorted with it)
   if (q->iter > 0 && threadIdx.x == 0) {
     a.ctr->n_base_small = 0;
+    a.ctr->n_base_mid = 0;
     a.ctr->n_base_large = 0;
     a.ctr->n_copy = 0;
     a.ctr->n_fallback = 0;
@@ -291,7 +292,7 @@ __global__ void k_batch_end(QueueState* q, const LevelCounters* ctr, const unsig
   }
   q->cont = c;
   if (hs.in_graph) {
-    cudaGraphSetConditional(hs.small, ctr->n_base_small > 0);
+    cudaGraphSetConditional(hs.small, ctr->n_base_small > 0 || ctr->n_base_mid > 0);
     cudaGraphSetConditional(hs.large, ctr->n_base_large > 0);
     cudaGraphSetConditional(hs.copy, ctr->n_copy > 0);
     cudaGraphSetConditional(hs.fallback, ctr->n_fallback > 0);
