@@ -103,6 +103,86 @@ __device__ double thread_tree_sum(double* p, uint64_t m) {
   return p[0];
 }
 
+// thread_tree_sum's tree done by a warp, in place, over K arrays at once
+// (p[q] + q * stride, m partials each): every level adds the pairs
+// (2i, 2i+1) with 32 lanes at a time (all reads of a group before its
+// writes; later groups read only indices above the ones written) and
+// carries an odd last value, so each total is bit-identical.  Every lane
+// returns the totals.
+template <int K>
+__device__ void warp_tree_sum_inplace(double* p, uint64_t stride, uint64_t m, double (&out)[K]) {
+  const unsigned lane = threadIdx.x & 31;
+  if (m == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) out[q] = 0.0;
+    return;
+  }
+  while (m > 1) {
+    const uint64_t h = m >> 1;
+    for (uint64_t i0 = 0; i0 < h; i0 += 32) {
+      const uint64_t i = i0 + lane;
+      double v[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] = i < h ? __dadd_rn(p[q * stride + 2 * i], p[q * stride + 2 * i + 1]) : 0.0;
+      __syncwarp();
+      if (i < h)
+#pragma unroll
+        for (int q = 0; q < K; ++q) p[q * stride + i] = v[q];
+      __syncwarp();
+    }
+    if ((m & 1) && lane == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) p[q * stride + h] = p[q * stride + m - 1];
+    __syncwarp();
+    m = h + (m & 1);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = p[q * stride];
+}
+
+// The same tree done by a block over K arrays staged in shared memory
+// (s: K * m words, filled from p[q] + q * stride), in place: each level's
+// reads happen before its writes (a barrier between them).  Every thread
+// returns the totals.
+template <int K>
+__device__ void block_tree_sum_smem(const double* p, uint64_t stride, uint32_t m, double* s, double (&out)[K]) {
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < K; ++q) s[q * m + i] = p[q * stride + i];
+  __syncthreads();
+  uint32_t cur = m;
+  while (cur > 1) {
+    const uint32_t h = cur >> 1;
+    constexpr int kPer = 4;  // pairs per thread per round (h <= 4 * blockDim.x per round)
+    for (uint32_t i0 = 0; i0 < h; i0 += kPer * blockDim.x) {
+      double v[kPer][K];
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const uint32_t i = i0 + r * blockDim.x + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[r][q] = i < h ? __dadd_rn(s[q * m + 2 * i], s[q * m + 2 * i + 1]) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const uint32_t i = i0 + r * blockDim.x + threadIdx.x;
+        if (i < h)
+#pragma unroll
+          for (int q = 0; q < K; ++q) s[q * m + i] = v[r][q];
+      }
+      __syncthreads();
+    }
+    if ((cur & 1) && threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < K; ++q) s[q * m + h] = s[q * m + cur - 1];
+    __syncthreads();
+    cur = h + (cur & 1);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = s[q * m];
+  __syncthreads();
+}
+
 // Same tree done by a whole block, ping-ponging between p and q (same size).
 __device__ double block_tree_sum(double* p, double* q, uint64_t m) {
   if (m == 0) return 0.0;
@@ -212,41 +292,90 @@ __global__ void __launch_bounds__(kSortTPB) k_sort_chunks(uint64_t* __restrict__
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) a[base + i] = sm[i];
 }
 
+// Merge-path split of diagonal d between sorted runs A (na keys) and B (nb
+// keys): the number of A's keys among the first d outputs (ties take A).
+// One warp, 32 probes per round, so a search of 2^20 positions takes four
+// rounds of loads instead of twenty dependent ones.  Every lane returns it.
+__device__ __forceinline__ uint64_t warp_merge_split(const uint64_t* __restrict__ A, uint64_t na,
+                                                     const uint64_t* __restrict__ B, uint64_t nb, uint64_t d) {
+  const unsigned lane = threadIdx.x & 31;
+  uint64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {  // uniform across the warp
+    const uint64_t step = (hi - lo + 31) / 32;
+    const uint64_t i = lo + lane * step;
+    const bool in = i < hi;
+    const bool p = in && A[i] <= B[d - 1 - i];  // the split lies above i
+    const unsigned mp = __ballot_sync(0xFFFFFFFFu, p), mf = __ballot_sync(0xFFFFFFFFu, in && !p);
+    const uint64_t nlo = mp ? lo + (uint64_t)(31 - __clz(mp)) * step + 1 : lo;
+    const uint64_t nhi = mf ? lo + (uint64_t)(__ffs(mf) - 1) * step : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  return lo;
+}
+
 // One merge pass: within each segment, runs [2pw, 2pw+w) and [2pw+w, 2pw+2w)
-// are merged (merge path, 8 outputs per thread; ties take the left run).
-__global__ void __launch_bounds__(kTPB) k_merge_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                     const uint64_t* __restrict__ off,
-                                                     const uint64_t* __restrict__ cpre, uint32_t nseg, uint64_t w) {
+// are merged (merge path, ties take the left run).  A block produces one
+// chunk of kSortChunk outputs (a chunk lies inside one pair of runs): two
+// warps find the splits at the chunk's ends, the block stages the two input
+// slices in shared memory, and each thread merges eight outputs from there.
+constexpr int kMergeTPB = kSortChunk / 8;
+__global__ void __launch_bounds__(kMergeTPB) k_merge_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                          const uint64_t* __restrict__ off,
+                                                          const uint64_t* __restrict__ cpre, uint32_t nseg,
+                                                          uint64_t w) {
   pdl_wait();
-  uint64_t c = blockIdx.x;
-  uint32_t s = find_seg(cpre, nseg, c);
-  uint64_t sb = off[s];
-  uint64_t len = off[s + 1] - sb;
-  uint64_t o = (c - cpre[s]) * kSortChunk + (uint64_t)threadIdx.x * 8;
-  if (o >= len) return;
-  uint64_t a0 = (o / (2 * w)) * (2 * w);
-  uint64_t a1 = a0 + w < len ? a0 + w : len;
-  uint64_t b1 = a0 + 2 * w < len ? a0 + 2 * w : len;
-  uint64_t na = a1 - a0, nbb = b1 - a1;
+  __shared__ uint64_t sm[kSortChunk];
+  __shared__ uint64_t s_split[2];
+  const uint64_t c = blockIdx.x;
+  const uint32_t s = find_seg(cpre, nseg, c);
+  const uint64_t sb = off[s];
+  const uint64_t len = off[s + 1] - sb;
+  const uint64_t o0 = (c - cpre[s]) * kSortChunk;
+  if (o0 >= len) return;  // uniform across the block
+  const uint64_t a0 = (o0 / (2 * w)) * (2 * w);
+  const uint64_t a1 = a0 + w < len ? a0 + w : len;
+  const uint64_t b1 = a0 + 2 * w < len ? a0 + 2 * w : len;
+  const uint64_t na = a1 - a0, nbb = b1 - a1;
   const uint64_t* A = in + sb + a0;
   const uint64_t* Bv = in + sb + a1;
-  uint64_t diag = o - a0;
-  uint64_t lo = diag > nbb ? diag - nbb : 0;
-  uint64_t hi = diag < na ? diag : na;
+  const uint64_t d0 = o0 - a0;
+  const uint64_t d1 = d0 + kSortChunk < na + nbb ? d0 + kSortChunk : na + nbb;
+  const unsigned wid = threadIdx.x >> 5;
+  if (wid < 2) {
+    const uint64_t sp = warp_merge_split(A, na, Bv, nbb, wid ? d1 : d0);
+    if ((threadIdx.x & 31) == 0) s_split[wid] = sp;
+  }
+  __syncthreads();
+  const uint64_t i0 = s_split[0], i1 = s_split[1];
+  const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+  const uint32_t la = (uint32_t)(i1 - i0), lb = (uint32_t)(j1 - j0);  // la + lb = d1 - d0 <= kSortChunk
+  for (uint32_t t = threadIdx.x; t < la + lb; t += blockDim.x) sm[t] = t < la ? A[i0 + t] : Bv[j0 + t - la];
+  __syncthreads();
+  const uint64_t* SA = sm;
+  const uint64_t* SB = sm + la;
+  const uint32_t dt = 8 * threadIdx.x;
+  if (dt >= la + lb) return;
+  uint32_t lo = dt > lb ? dt - lb : 0, hi = dt < la ? dt : la;
   while (lo < hi) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (A[mid] <= Bv[diag - 1 - mid]) lo = mid + 1;
+    const uint32_t mid = (lo + hi) >> 1;
+    if (SA[mid] <= SB[dt - 1 - mid]) lo = mid + 1;
     else hi = mid;
   }
-  uint64_t i = lo, j = diag - lo;
-  uint64_t lim = b1 - o < 8 ? b1 - o : 8;
-  for (uint64_t k = 0; k < lim; ++k) {
-    bool takeA = (j >= nbb) || (i < na && A[i] <= Bv[j]);
-    out[sb + o + k] = takeA ? A[i++] : Bv[j++];
+  uint32_t i = lo, j = dt - lo;
+  const uint32_t lim = la + lb - dt < 8 ? la + lb - dt : 8;
+  uint64_t* o = out + sb + a0 + d0 + dt;
+  for (uint32_t k = 0; k < lim; ++k) {
+    const bool takeA = (j >= lb) || (i < la && SA[i] <= SB[j]);
+    o[k] = takeA ? SA[i++] : SB[j++];
   }
 }
 
 // ---------------------------------------------------------------- fit
+
+// Root partials staged in shared memory by the finish kernel (4 sums of
+// up to this many chunks: 128 KB); more chunks take the global tree.
+constexpr uint32_t kRootSmemChunks = 4096;
 
 // One warp per root chunk of every candidate.
 __global__ void k_fit_root_partials(FitArgs a, RunParams rp) {
@@ -275,11 +404,19 @@ __global__ void k_fit_root_finish(FitArgs a, RunParams rp) {
   uint64_t b0 = a.rchunk_prefix[c];
   uint64_t m = a.rchunk_prefix[c + 1] - b0;
   __shared__ double sums[4];
-  for (int q = 0; q < 4; ++q) {
-    double* p = a.rpart + q * a.total_rchunks + b0;
-    double* t = a.rpart + (4 + q) * a.total_rchunks + b0;  // ping-pong half
-    double v = block_tree_sum(p, t, m);
-    if (threadIdx.x == 0) sums[q] = v;
+  if (m <= kRootSmemChunks) {  // the candidate's partials fit in shared memory
+    extern __shared__ double s_part[];
+    double out[4];
+    block_tree_sum_smem<4>(a.rpart + b0, a.total_rchunks, (uint32_t)m, s_part, out);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 4; ++q) sums[q] = out[q];
+  } else {
+    for (int q = 0; q < 4; ++q) {
+      double* p = a.rpart + q * a.total_rchunks + b0;
+      double* t = a.rpart + (4 + q) * a.total_rchunks + b0;  // ping-pong half
+      double v = block_tree_sum(p, t, m);
+      if (threadIdx.x == 0) sums[q] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -422,8 +559,8 @@ __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict_
         const double v = lane < nch ? a.lpart[q * a.lchunk_bound + p0 + lane] : 0.0;
         sm[q] = warp_tree_sum32(v, (uint32_t)nch, lane);
       }
-    } else if (lane == 0) {
-      for (int q = 0; q < 4; ++q) sm[q] = thread_tree_sum(a.lpart + q * a.lchunk_bound + p0, nch);
+    } else {
+      warp_tree_sum_inplace<4>(a.lpart + p0, a.lchunk_bound, nch, sm);
     }
     if (lane == 0) {
       double x_first = ord_value(s[st], rp.dt);
@@ -1356,7 +1493,7 @@ uint64_t* segmented_sort_u64(uint64_t* a, uint64_t* b, const uint64_t* d_off, co
   uint64_t* cur = a;
   uint64_t* oth = b;
   for (uint64_t w = kSortChunk; w < max_len; w *= 2) {
-    pdl_launch(k_merge_pass, (unsigned)total_chunks, kTPB, 0, st, cur, oth, d_off, d_chunk_prefix, nseg, w);
+    pdl_launch(k_merge_pass, (unsigned)total_chunks, kMergeTPB, 0, st, cur, oth, d_off, d_chunk_prefix, nseg, w);
     ++*launches;
     uint64_t* t = cur;
     cur = oth;
@@ -1383,7 +1520,17 @@ void launch_dups(const FreshArgs& f, const uint64_t* samp, cudaStream_t st) {
 void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t* launches) {
   if (!a.ncand) return;
   pdl_launch(k_fit_root_partials, grid_for(a.total_rchunks * 32, 128), 128, 0, st, a, rp);
-  pdl_launch(k_fit_root_finish, a.ncand, 1024, 0, st, a, rp);
+  {
+    static size_t set[64] = {};
+    const size_t sm = (size_t)4 * kRootSmemChunks * sizeof(double);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && set[dev] < sm) {
+      cudaFuncSetAttribute(k_fit_root_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      set[dev] = sm;
+    }
+    pdl_launch(k_fit_root_finish, a.ncand, 1024, sm, st, a, rp);
+  }
   cudaMemsetAsync(a.leaf_start, 0, (size_t)a.ncand * (a.L + 1) * sizeof(uint32_t), st);
   pdl_launch(k_fit_route_leaf, grid_for(a.total_cand_samples), kTPB, 0, st, a, rp, a.leaf_of);
   pdl_launch(k_fit_route_starts, grid_for(a.total_cand_samples), kTPB, 0, st, a, a.leaf_of);
