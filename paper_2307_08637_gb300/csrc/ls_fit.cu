@@ -1556,7 +1556,16 @@ void launch_learned_pivots(Plan* plans, const Item* items, const uint32_t* list,
   // with bd, nlist bounds the list length read on the device
   if (!nlist) return;
   uint64_t n = (uint64_t)nlist * nb_pad;
-  const uint32_t tpb = nb_pad >= kPivotTPB ? kPivotTPB : 128;  // pooled blocks when tpb divides nb_pad
+  uint32_t tpb = nb_pad >= kPivotTPB ? kPivotTPB : 128;  // pooled blocks when tpb divides nb_pad
+  if (!bd) {
+    // short lists (a root, the few items of a deep level): smaller blocks
+    // spread the searches over more SMs' FP64 pipes (the rounds of a block
+    // are a chain of FP64 evaluations)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (tpb > 32 && n / tpb < 2ull * (uint64_t)(sms > 0 ? sms : 1) && nb_pad % (tpb / 2) == 0) tpb /= 2;
+  }
   // one block per block of slots of the largest list (blocks past the
   // device-side list end return at once): the search rounds of a block are
   // synchronised, so blocks are scheduled as slots free up rather than
