@@ -260,7 +260,12 @@ __global__ void k_dups(FreshArgs f, const uint64_t* __restrict__ samp) {
 // ------------------------------------------------ segmented sample sort
 
 constexpr int kSortTPB = 1024;  // threads of a chunk sort: two of the chunk's 2048 keys each
+static_assert(kSortChunk == 2 * kSortTPB, "two keys per thread");
 
+// Bitonic sort of one chunk of kSortChunk keys (padding ~0).  Each warp
+// holds 64 consecutive keys, two per lane: the stages whose pairs lie inside
+// 64 keys run in registers (lane shuffles), the wider ones in shared memory
+// with one thread per pair.
 __global__ void __launch_bounds__(kSortTPB) k_sort_chunks(uint64_t* __restrict__ a, const uint64_t* __restrict__ off,
                                                       const uint64_t* __restrict__ cpre, uint32_t nseg) {
   pdl_wait();
@@ -273,22 +278,45 @@ __global__ void __launch_bounds__(kSortTPB) k_sort_chunks(uint64_t* __restrict__
   uint32_t len = (uint32_t)(end - base);
   for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) sm[i] = (i < len) ? a[base + i] : ~0ull;
   __syncthreads();
-  for (uint32_t k = 2; k <= kSortChunk; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
-        uint32_t ixj = i ^ j;
-        if (ixj > i) {
-          uint64_t x = sm[i], y = sm[ixj];
-          bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            sm[i] = y;
-            sm[ixj] = x;
-          }
-        }
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t e0 = 64 * wid + 2 * lane;  // this lane's keys: e0 and e0 + 1
+  uint64_t r0 = sm[e0], r1 = sm[e0 + 1];
+  // stages j = jtop .. 1 of the bitonic merge of size k, in registers
+  auto reg_stages = [&](uint32_t k, uint32_t jtop) {
+    const bool up = (e0 & k) == 0;  // k >= 2: e0 and e0 + 1 agree on bit k
+    for (uint32_t j = jtop; j >= 2; j >>= 1) {
+      const uint64_t y0 = __shfl_xor_sync(0xFFFFFFFFu, r0, j >> 1);
+      const uint64_t y1 = __shfl_xor_sync(0xFFFFFFFFu, r1, j >> 1);
+      const bool keep_min = ((e0 & j) == 0) == up;
+      r0 = keep_min ? (r0 < y0 ? r0 : y0) : (r0 < y0 ? y0 : r0);
+      r1 = keep_min ? (r1 < y1 ? r1 : y1) : (r1 < y1 ? y1 : r1);
+    }
+    const uint64_t mn = r0 < r1 ? r0 : r1, mx = r0 < r1 ? r1 : r0;
+    r0 = up ? mn : mx;
+    r1 = up ? mx : mn;
+  };
+  for (uint32_t k = 2; k <= 64; k <<= 1) reg_stages(k, k >> 1);
+  for (uint32_t k = 128; k <= kSortChunk; k <<= 1) {
+    sm[e0] = r0;
+    sm[e0 + 1] = r1;
+    __syncthreads();
+    for (uint32_t j = k >> 1; j >= 64; j >>= 1) {
+      const uint32_t p = threadIdx.x;
+      const uint32_t i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+      const uint64_t x = sm[i], y = sm[i + j];
+      if ((x > y) == ((i & k) == 0)) {
+        sm[i] = y;
+        sm[i + j] = x;
       }
       __syncthreads();
     }
+    r0 = sm[e0];
+    r1 = sm[e0 + 1];
+    reg_stages(k, 32);
   }
+  sm[e0] = r0;
+  sm[e0 + 1] = r1;
+  __syncthreads();
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) a[base + i] = sm[i];
 }
 
