@@ -49,7 +49,8 @@ struct Cls {
   uint32_t nb_pad, kmax, shift, B;
   int32_t model;
   uint8_t cls;
-  uint8_t agg;  // warp-aggregate histogram increments (splitters: duplicates collide)
+  uint8_t agg;    // warp-aggregate histogram increments (splitters: duplicates collide)
+  uint8_t clamp;  // refined item (P > B): the FP32 guess applies the leaves' clamps
 };
 
 // Load item pi's classifier into shared memory (all threads).
@@ -71,6 +72,7 @@ __device__ void load_cls(const PassArgs& a, const RunParams& rp, uint32_t pi, Cl
   c.B = rp.B;
   c.model = pl.model;
   c.agg = pl.decision != LS_DEC_LEARNED;
+  c.clamp = pl.P > (double)rp.B;  // at P = B the unclamped guess is already within one bucket
   if (c.cls == CLS_DIRECT) {
     c.kmax = rp.B - 1;
     return;
@@ -122,6 +124,16 @@ __device__ __forceinline__ uint32_t fix_guess(const uint64_t* __restrict__ T, ui
   return b;
 }
 
+// fix_guess for guesses that are almost always exact (root items, P = B:
+// the FP32 image's error is far below a bucket): the two table entries
+// around g confirm it, and only the rare miss takes the general fix.
+__device__ __forceinline__ uint32_t fix_guess_likely(const uint64_t* __restrict__ T, uint32_t nb_pad, uint32_t kmax,
+                                                     uint32_t g, uint64_t u) {
+  const uint32_t g1 = g < kmax ? g + 1 : kmax;
+  if (T[g] <= u && (g == kmax || T[g1] > u)) return g;
+  return fix_guess(T, nb_pad, kmax, g, u);
+}
+
 // Bucket of one key for a classifier kind and key type known at compile time.
 template <int CLS, int DT>
 __device__ __forceinline__ uint32_t classify_as(uint64_t bits, const Cls& c, const uint64_t* sT, const void* sAux,
@@ -134,9 +146,9 @@ __device__ __forceinline__ uint32_t classify_as(uint64_t bits, const Cls& c, con
   if (CLS == CLS_RADIX) return (uint32_t)(u >> c.shift) & c.kmax;  // kmax = buckets - 1, a power of two minus 1
   if (CLS == CLS_GUESS) {
     const FLeaf* sF = static_cast<const FLeaf*>(sAux);
-    const uint32_t g = guess_bucket(c.fm, sF, reinterpret_cast<const FClamp*>(sF + c.fm.L), c.Pf, c.Bgf, c.kmax, bits,
-                                    DT);
-    return fix_guess(sT, c.nb_pad, c.kmax, g, u);
+    const FClamp* sC = c.clamp ? reinterpret_cast<const FClamp*>(sF + c.fm.L) : nullptr;
+    const uint32_t g = guess_bucket(c.fm, sF, sC, c.Pf, c.Bgf, c.kmax, bits, DT);
+    return c.clamp ? fix_guess(sT, c.nb_pad, c.kmax, g, u) : fix_guess_likely(sT, c.nb_pad, c.kmax, g, u);
   }
   const uint32_t b = (CLS == CLS_DIR)
                          ? pivot_count_dir(sT, static_cast<const uint16_t*>(sAux), c.dir_lo, c.dir_hi, c.shift, c.kmax, u)
