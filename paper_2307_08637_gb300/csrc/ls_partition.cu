@@ -614,11 +614,14 @@ __global__ void __launch_bounds__(kBufTPB, 2)
       else bad = true;
     }
     __syncthreads();
+    // positions within a region are counted from the line boundary before
+    // its start: a key's slot in the line buffer is its position mod 8, and
+    // the buffered line ends at a multiple of 8
     for (uint32_t b = threadIdx.x; b < nbk; b += kBufTPB) {
       const uint64_t x = ab + a.cursors[pl.cnt_off + b] + ex[b] + cur[b];
       rs[b] = x;
-      cur[b] = 0;
-      le[b] = (uint32_t)((x & M) + kLineKeys - x);
+      cur[b] = (uint32_t)(x & (kLineKeys - 1));
+      le[b] = kLineKeys;
     }
     __syncthreads();
     uint64_t v[kBufKT];
@@ -648,7 +651,7 @@ __global__ void __launch_bounds__(kBufTPB, 2)
           rr[k] = r;
           e = le[b];
           if (r < e) {
-            buf[b * kLineKeys + (((uint32_t)rs[b] + r) & (kLineKeys - 1))] = v[k];
+            buf[b * kLineKeys + (r & (kLineKeys - 1))] = v[k];
             f = r == e - 1;
           } else {
             late |= 1u << k;
@@ -668,9 +671,9 @@ __global__ void __launch_bounds__(kBufTPB, 2)
       for (uint32_t i = wid * kLPI + lane / kLPL; i < nf; i += kW * kLPI) {
         const uint32_t b = fb[i];
         const uint64_t r0 = rs[b];
-        const uint64_t ls = (r0 + fe[i] - 1) & M;
+        const uint64_t ls = (r0 & M) + fe[i] - kLineKeys;
         const uint32_t q = lane % kLPL;
-        if (q == 0) le[b] = (uint32_t)(((r0 + cur[b]) & M) + kLineKeys - r0);
+        if (q == 0) le[b] = (cur[b] & ~(kLineKeys - 1)) + kLineKeys;
         if (ls >= r0) {
           if (ls >= alo && ls + kLineKeys <= ahi)
             reinterpret_cast<uint4*>(ls << 3)[q] = reinterpret_cast<const uint4*>(buf + b * kLineKeys)[q];
@@ -693,13 +696,12 @@ __global__ void __launch_bounds__(kBufTPB, 2)
       for (int k = 0; k < (int)kBufKT; ++k) {
         if (!(late & (1u << k))) continue;
         const uint32_t b = bk[k];
-        const uint64_t r0 = rs[b];
-        const uint64_t g = r0 + rr[k];
-        if (g < r0 + le[b] - kLineKeys) {
+        if (rr[k] < le[b] - kLineKeys) {
+          const uint64_t g = (rs[b] & M) + rr[k];
           if (g >= alo && g < ahi) *reinterpret_cast<uint64_t*>(g << 3) = v[k];
           else bad = true;
         } else {
-          buf[b * kLineKeys + (g & (kLineKeys - 1))] = v[k];
+          buf[b * kLineKeys + (rr[k] & (kLineKeys - 1))] = v[k];
         }
       }
       if (t0 + kBufTile < rn.len) load_tile(t0 + kBufTile);
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kBufTPB, 2)
     // the regions' last (partial) lines
     for (uint32_t i = threadIdx.x; i < nbk * kLineKeys; i += kBufTPB) {
       const uint32_t b = i / kLineKeys, j = i % kLineKeys;
-      const uint64_t r0 = rs[b], e = r0 + cur[b];
+      const uint64_t r0 = rs[b], e = (r0 & M) + cur[b];
       const uint64_t g = (e & M) + j;
       if (g < e && g >= r0) {
         if (g >= alo && g < ahi) *reinterpret_cast<uint64_t*>(g << 3) = buf[i];
