@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
 // slots, and line ends change only in the flush, so two barriers per tile
 // suffice.  Every global write is checked against the item's range.
 constexpr uint32_t kBufTPB = 512;
-constexpr uint32_t kBufKT = 8;
+constexpr uint32_t kBufKT = 6;
 constexpr uint32_t kBufTile = kBufTPB * kBufKT;
 constexpr uint32_t kLineKeys = 8;
 constexpr size_t kBufSmem = (size_t)kBufMaxBuckets * (kLineKeys * 8 + 8 + 4 + 4 + 4 + 2);
@@ -639,31 +639,35 @@ __global__ void __launch_bounds__(kBufTPB, 2)
     load_tile(0);
     uint32_t par = 0;
     for (uint64_t t0 = 0; t0 < rn.len; t0 += kBufTile, par ^= 1) {
-      uint32_t late = 0;
+      // the thread's claims first (independent atomics, in flight together),
+      // then the buffer stores
+      uint32_t late = 0, full = 0;
+#pragma unroll
+      for (int k = 0; k < (int)kBufKT; ++k) rr[k] = bk[k] < nbk ? atomicAdd(&cur[bk[k]], 1u) : 0u;
 #pragma unroll
       for (int k = 0; k < (int)kBufKT; ++k) {
         const uint32_t b = bk[k];
-        bool f = false;
-        uint32_t e = 0;
-        rr[k] = 0;
         if (b < nbk) {
-          const uint32_t r = atomicAdd(&cur[b], 1u);
-          rr[k] = r;
-          e = le[b];
-          if (r < e) {
-            buf[b * kLineKeys + (r & (kLineKeys - 1))] = v[k];
-            f = r == e - 1;
+          const uint32_t e = le[b];
+          if (rr[k] < e) {
+            buf[b * kLineKeys + (rr[k] & (kLineKeys - 1))] = v[k];
+            if (rr[k] == e - 1) full |= 1u << k;
           } else {
             late |= 1u << k;
           }
         } else if (b != 0xFFFFu) {
           bad = true;  // K1 and K3 disagree
         }
-        if (f) {  // about one key in eight: a plain atomic append is cheaper than a warp vote per key
-          const uint32_t q = atomicAdd(&s_nfl[par], 1u);
-          fb[q] = (uint16_t)b;
-          fe[q] = e;
-        }
+      }
+      if (full) {  // lines this thread completed (about one key in eight): one append for all of them
+        uint32_t q = atomicAdd(&s_nfl[par], (uint32_t)__popc(full));
+#pragma unroll
+        for (int k = 0; k < (int)kBufKT; ++k)
+          if (full & (1u << k)) {
+            fb[q] = (uint16_t)bk[k];
+            fe[q] = rr[k] + 1;
+            ++q;
+          }
       }
       __syncthreads();
       // write the completed lines and advance their line ends
