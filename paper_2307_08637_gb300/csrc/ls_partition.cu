@@ -192,7 +192,70 @@ __device__ __forceinline__ void k1_chunk(const PassArgs& a, const Cls& c, const 
     const uint32_t len = clen - t0 < kK1Tile ? (uint32_t)(clen - t0) : kK1Tile;
     const uint64_t* s = src + t0 + threadIdx.x;
     uint16_t* d = idout + t0 + threadIdx.x;
-    if (len == kK1Tile) {
+    if (CLS == CLS_GUESS && len == kK1Tile) {
+      // the guess classifier in steps over groups of the thread's keys, so
+      // that their shared-memory reads are in flight together: the guesses
+      // (leaf reads), the table entries around them, then the rare keys
+      // whose guess is two or more buckets off (the full search)
+      constexpr int KG = 2;
+      uint64_t v[kK1KPT];
+#pragma unroll
+      for (int k = 0; k < kK1KPT; ++k) v[k] = s[k * kTPB];
+      const FLeaf* sF = static_cast<const FLeaf*>(sD);
+      const FClamp* sC = c.clamp ? reinterpret_cast<const FClamp*>(sF + c.fm.L) : nullptr;
+      const uint32_t kmax = c.kmax;
+#pragma unroll
+      for (int h = 0; h < kK1KPT; h += KG) {
+        uint32_t g[KG];
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          const uint64_t bits = v[h + k];
+          if (NANCHK) nan |= (bits & kAbs) > kInf;
+          diff |= ord_of(bits, DT) ^ first;
+          g[k] = guess_bucket(c.fm, sF, sC, c.Pf, c.Bgf, kmax, bits, DT);
+        }
+        uint32_t miss = 0;
+        if (c.clamp) {  // often one off: the reads on both sides decide -1 / 0 / +1
+#pragma unroll
+          for (int k = 0; k < KG; ++k) {
+            const uint64_t u = ord_of(v[h + k], DT);
+            const uint32_t gk = g[k], g1 = gk < kmax ? gk + 1 : kmax;
+            const uint32_t g2 = g1 < kmax ? g1 + 1 : kmax, gm = gk ? gk - 1 : 0u;
+            const uint64_t A = sT[gk], B1 = sT[g1], Cm = sT[gm], C2 = sT[g2];
+            const bool lo = A > u;
+            const bool hi = gk < kmax && B1 <= u;
+            const bool far = lo ? (gk == 0 || Cm > u) : (hi && g1 < kmax && C2 <= u);
+            g[k] = gk - (uint32_t)lo + (uint32_t)hi;
+            if (far) miss |= 1u << k;
+          }
+          if (miss) {
+#pragma unroll
+            for (int k = 0; k < KG; ++k)
+              if (miss & (1u << k)) {
+                const uint32_t b = pivot_count(sT, c.nb_pad, ord_of(v[h + k], DT));
+                g[k] = b < kmax ? b : kmax;
+              }
+          }
+        } else {  // almost always exact: the two reads around the guess confirm it
+#pragma unroll
+          for (int k = 0; k < KG; ++k) {
+            const uint64_t u = ord_of(v[h + k], DT);
+            const uint32_t gk = g[k], g1 = gk < kmax ? gk + 1 : kmax;
+            if (!(sT[gk] <= u && (gk == kmax || sT[g1] > u))) miss |= 1u << k;
+          }
+          if (miss) {
+#pragma unroll
+            for (int k = 0; k < KG; ++k)
+              if (miss & (1u << k)) g[k] = fix_guess(sT, c.nb_pad, kmax, g[k], ord_of(v[h + k], DT));
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          d[(h + k) * kTPB] = (uint16_t)g[k];
+          hist_add(sH, g[k], c.agg);
+        }
+      }
+    } else if (len == kK1Tile) {
       uint64_t v[kK1KPT];
 #pragma unroll
       for (int k = 0; k < kK1KPT; ++k) v[k] = s[k * kTPB];
