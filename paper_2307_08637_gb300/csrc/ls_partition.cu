@@ -1378,27 +1378,30 @@ __device__ __forceinline__ void warp_sort_span_kv(const Span& s, uint64_t* A, co
 // GPU form of LearnedSort 2.0's counting sort by predicted position plus an
 // insertion-sort fix, Sec. 2.2): inside a bucket the keys are close to
 // uniform in ord space, so a linear map between the span's extremes places
-// them into 32R slots (R = ceil(n / 32) keys per lane); a counting sort by
-// slot and a rank count inside each slot (the insertion-sort fix done as one
-// comparison pass per key, without a dependent chain) give the exact order.  Spans
+// them into 32 R SPK slots (R = ceil(n / 32) keys per lane, SPK slots per
+// key); a counting sort by slot and a rank count inside each slot (the
+// insertion-sort fix done as one comparison pass per key, without a
+// dependent chain) give the exact order.  Spans
 // whose largest slot holds more than kMaxSlot keys (clustered data) return
 // false and take the bitonic network instead.
 constexpr uint32_t kSlots = 256;  // slots of the largest size class (32 per key register)
 constexpr uint32_t kMaxSlot = 24;
+constexpr int kSlotsShort = 2, kSlotsMid = 1;  // slots per key of the two warp classes
 
 // Counting sort by predicted slot of one span of n keys, 32(R-1) < n <= 32R.
 // The map: with hmin / hmax the smallest / largest high word of the ords,
 // base = hmin:0 and w = the top 32 bits of (u - base) << clz(hmax - hmin)
 // (or, when every key has the same high word, w = (low - lmin) <<
-// clz(lmax - lmin)); slot = floor(w 32R / 2^32).  Monotone in u, so sorting
-// by slot and then inside slots sorts the span.  Slot s belongs to lane
-// s / R (= w >> 27) and is stored at (s mod R) * 32 + s / R, so the per-lane
-// reads of the scan hit distinct banks; after the scan the word holds the
-// slot's start and count.
-template <int R>
+// clz(lmax - lmin)); slot = floor(w Q 32 / 2^32) with Q = R SPK slots per
+// lane.  Monotone in u, so sorting by slot and then inside slots sorts the
+// span.  Slot s belongs to lane s / Q (= w >> 27) and is stored at
+// (s mod Q) * 32 + s / Q, so the per-lane reads of the scan hit distinct
+// banks; after the scan the word holds the slot's start and count.
+template <int R, int SPK>
 __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, const uint64_t* Bbuf, int dt,
                                                  uint64_t* sk, uint32_t* sc) {
-  constexpr uint32_t NS = 32 * R;
+  constexpr uint32_t Q = R * SPK;  // slots per lane
+  constexpr uint32_t NS = 32 * Q;
   const unsigned lane = threadIdx.x & 31;
   const uint64_t* src = (s.buf ? Bbuf : A) + s.lo;
   const uint32_t n = s.n;
@@ -1443,20 +1446,20 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
     for (int r = 0; r < R; ++r) w[r] = (uint32_t)(((u[r] - base) << sh) >> 32);
   }
 #pragma unroll
-  for (int q = 0; q < R; ++q) sc[q * 32 + lane] = 0;
+  for (int q = 0; q < (int)Q; ++q) sc[q * 32 + lane] = 0;
   __syncwarp();
   uint32_t at[R], rk[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const uint32_t slot = __umulhi(w[r], NS), owner = w[r] >> 27;
-    at[r] = (slot - owner * R) * 32 + owner;
+    at[r] = (slot - owner * Q) * 32 + owner;
     rk[r] = (r < R - 1 || lane + 32 * r < n) ? atomicAdd(&sc[at[r]], 1u) : 0u;
   }
   __syncwarp();
   // exclusive scan of the slot counts (slots lane*R .. lane*R+R-1 per lane)
-  uint32_t c[R], loc = 0, big = 0;
+  uint32_t c[Q], loc = 0, big = 0;
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
+  for (int q = 0; q < (int)Q; ++q) {
     c[q] = sc[q * 32 + lane];
     loc += c[q];
     big = max(big, c[q]);
@@ -1470,7 +1473,7 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
   if (__reduce_max_sync(0xFFFFFFFFu, big) > kMaxSlot) return false;  // uniform across the warp
   uint32_t run = incl - loc;
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
+  for (int q = 0; q < (int)Q; ++q) {
     sc[q * 32 + lane] = run | (c[q] << 16);  // slot start and count
     run += c[q];
   }
@@ -1484,19 +1487,25 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
   __syncwarp();
   // order inside the slots: a key's place is its slot's start plus the keys
   // of the slot before it (smaller, or equal and staged earlier); the reads
-  // are independent, so a slot of c keys costs c loads, not a chain
-  uint32_t pos[R];
+  // are independent, so a slot of c keys costs c loads, not a chain.  The
+  // warp takes as many steps as its largest slot holds, each step one
+  // comparison for each of a lane's keys whose slot is that long.
+  uint32_t pos[R], a0[R], cn[R], mx = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const uint32_t a0 = e[r] & 0xFFFFu, me = a0 + rk[r];
-    const uint32_t cn = (r < R - 1 || lane + 32 * r < n) ? e[r] >> 16 : 0u;
-    uint32_t p = a0;
-#pragma unroll 4
-    for (uint32_t i = a0; i < a0 + cn; ++i) {
-      const uint64_t x = sk[i];
-      p += (x < u[r]) | ((x == u[r]) & (i < me));
-    }
-    pos[r] = p;
+    a0[r] = e[r] & 0xFFFFu;
+    cn[r] = (r < R - 1 || lane + 32 * r < n) ? e[r] >> 16 : 0u;
+    pos[r] = a0[r];
+    mx = max(mx, cn[r]);
+  }
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  for (uint32_t i = 0; i < mx; ++i) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (i < cn[r]) {
+        const uint64_t x = sk[a0[r] + i];
+        pos[r] += (x < u[r]) | ((x == u[r]) & (i < rk[r]));
+      }
   }
   __syncwarp();
 #pragma unroll
@@ -1521,7 +1530,8 @@ __global__ void __launch_bounds__(kTPB, MINB) k_base_small(const Span* spans, ui
   pdl_wait();
   if (dn) n = *dn;  // span count written on the device
   __shared__ uint64_t s_keys[kTPB / 32][32 * RHI];
-  __shared__ uint32_t s_cnt[kTPB / 32][32 * RHI];
+  constexpr int kSPK = RHI <= 4 ? kSlotsShort : kSlotsMid;  // slots per key
+  __shared__ uint32_t s_cnt[kTPB / 32][32 * RHI * kSPK];
   const unsigned wid = threadIdx.x >> 5;
   uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = (gridDim.x * (uint64_t)blockDim.x) >> 5;
@@ -1538,21 +1548,21 @@ __global__ void __launch_bounds__(kTPB, MINB) k_base_small(const Span* spans, ui
     bool done;
     if (RHI <= 4) {
       switch (R) {  // uniform across the warp
-        case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
-        case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
-        case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
-        default: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
+        case 1: done = warp_placed_sort<1, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 2: done = warp_placed_sort<2, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 3: done = warp_placed_sort<3, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        default: done = warp_placed_sort<4, kSPK>(s, A, Bbuf, dt, sk, sc); break;
       }
     } else {
       switch (R) {
-        case 1: done = warp_placed_sort<1>(s, A, Bbuf, dt, sk, sc); break;
-        case 2: done = warp_placed_sort<2>(s, A, Bbuf, dt, sk, sc); break;
-        case 3: done = warp_placed_sort<3>(s, A, Bbuf, dt, sk, sc); break;
-        case 4: done = warp_placed_sort<4>(s, A, Bbuf, dt, sk, sc); break;
-        case 5: done = warp_placed_sort<5>(s, A, Bbuf, dt, sk, sc); break;
-        case 6: done = warp_placed_sort<6>(s, A, Bbuf, dt, sk, sc); break;
-        case 7: done = warp_placed_sort<7>(s, A, Bbuf, dt, sk, sc); break;
-        default: done = warp_placed_sort<8>(s, A, Bbuf, dt, sk, sc); break;
+        case 1: done = warp_placed_sort<1, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 2: done = warp_placed_sort<2, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 3: done = warp_placed_sort<3, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 4: done = warp_placed_sort<4, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 5: done = warp_placed_sort<5, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 6: done = warp_placed_sort<6, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        case 7: done = warp_placed_sort<7, kSPK>(s, A, Bbuf, dt, sk, sc); break;
+        default: done = warp_placed_sort<8, kSPK>(s, A, Bbuf, dt, sk, sc); break;
       }
     }
     if (done) continue;
