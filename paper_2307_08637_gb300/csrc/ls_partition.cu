@@ -1507,14 +1507,9 @@ __device__ __forceinline__ bool warp_placed_sort(const Span& s, uint64_t* A, con
         pos[r] += (x < u[r]) | ((x == u[r]) & (i < rk[r]));
       }
   }
-  __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (r < R - 1 || lane + 32 * r < n) sk[pos[r]] = u[r];
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (r < R - 1 || lane + 32 * r < n) A[s.lo + lane + 32 * r] = unord(sk[lane + 32 * r], dt);
+    if (r < R - 1 || lane + 32 * r < n) A[s.lo + pos[r]] = unord(u[r], dt);
   __syncwarp();
   return true;
 }
