@@ -105,17 +105,24 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def k3b_source_sha256(text: str) -> str:
+    """sha256 of the buffered scatter kernel's section of ls_partition.cu
+    (from its constants up to the chunk-prefix section)."""
+    a = text.index("constexpr uint32_t kBufTPB")
+    b = text.index("// ------------------------------------------------------------------ chunk prefixes", a)
+    return hashlib.sha256(text[a:b].encode()).hexdigest()
+
+
 def ncu_traffic():
     """DRAM bytes per key of the buffered scatter kernel (K3b) from the
-    committed ncu summary, only while the kernel source is unchanged since
+    committed ncu summary, only while the kernel's source is unchanged since
     the capture."""
     path = os.path.join(ROOT, "profiles", "scatter_traffic.json")
     src = os.path.join(ROOT, "paper_2307_08637_gb300", "csrc", "ls_partition.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("source_sha256") != sha:
+        if d.get("kernel_source_sha256") != k3b_source_sha256(open(src).read()):
             return None
         return float(d["dram_bytes_per_key"])
     except Exception:
