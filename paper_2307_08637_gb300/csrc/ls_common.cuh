@@ -303,17 +303,15 @@ __device__ __forceinline__ uint32_t guess_bucket(const FModel& m, const FLeaf* _
                                                  uint64_t bits, int dt) {
   float x = key_to_float(bits, dt);
   x = fminf(fmaxf(x, m.xminf), m.xmaxf);
-  float r = __fmaf_rn(m.raL, x - m.rx0f, m.rbL);
-  int li = (int)fminf(fmaxf(floorf(r), 0.0f), (float)(m.L - 1));
+  // floor to int (saturating) and clamp as integers
+  const int li = min(max(__float2int_rd(__fmaf_rn(m.raL, x - m.rx0f, m.rbL)), 0), (int)m.L - 1);
   FLeaf l = fl[li];
   float F = __fmaf_rn(l.y, x - l.x, l.z);
   if (fc) {
     const FClamp c = fc[li];
     F = fminf(fmaxf(F, c.x), c.y);
   }
-  float t = floorf(__fmaf_rn(F, Pf, -Bgf));
-  t = fminf(fmaxf(t, 0.0f), (float)kmax);  // NaN-free inputs: the model image is finite
-  return (uint32_t)t;
+  return (uint32_t)min(max(__float2int_rd(__fmaf_rn(F, Pf, -Bgf)), 0), (int)kmax);
 }
 
 // Exact bucket #{j <= kmax : T[j] <= u} from a guess: two steps either way,
