@@ -900,7 +900,20 @@ __device__ __forceinline__ bool pivot_start(uint32_t j, uint32_t B, const PivotP
     const uint64_t u = root_boundary(m, l0, dt, lo, hi);
     if (u > L && u <= H) guess = u;
   } else if (lf.a > 0.0) {
-    const double xs = lf.x0 + (tF - lf.b) / lf.a;
+    // 1/a from an FP32 reciprocal refined by two Newton-Raphson steps
+    // (r <- r + r (1 - a r)): an FP64 division costs several times as much
+    // on this part, and the guess only steers the search (exact
+    // evaluations confirm the pivot)
+    const float af = (float)lf.a;
+    double xs;
+    if (af > 1e-30f && af < 1e30f) {
+      double r = (double)__frcp_rn(af);
+      r = __fma_rn(r, __fma_rn(-lf.a, r, 1.0), r);
+      r = __fma_rn(r, __fma_rn(-lf.a, r, 1.0), r);
+      xs = __fma_rn(__dsub_rn(tF, lf.b), r, lf.x0);
+    } else {
+      xs = lf.x0 + (tF - lf.b) / lf.a;
+    }
     if (xs >= q.xlo && xs <= q.xhi) {
       uint64_t u;
       if (dt) u = xs >= 18446744073709549568.0 ? ~0ull : (uint64_t)xs;
