@@ -614,9 +614,13 @@ __global__ void __launch_bounds__(TPB, k3_min_blocks(TPB, QM, VB)) k_scatter(Pas
 // item before the run (the chunk prefixes, plus a count over the ids of the
 // run's first chunk when the run starts inside it).  Complete lines leave as
 // whole 64-byte writes; only the first and last line of a region are written
-// in part.  Per tile: phase A puts each key that falls in its bucket's
-// buffered line into the buffer and lists the lines that complete (the key
-// that fills a line's last slot appends it); after a barrier the listed
+// in part.  Positions inside a region count from the line boundary before
+// its start, so a key's buffer slot is its position mod kLineKeys.  Per
+// tile: phase A claims the positions of a thread's keys (the atomics
+// issued together), puts each key that falls in its bucket's buffered line
+// into the buffer and lists the lines that complete (the thread whose key
+// fills a line's last slot; one append for all of a thread's lines); after
+// a barrier the listed
 // lines are written (four lanes per line) and their line
 // ends advanced; after a second barrier phase B places the keys past the
 // buffered line (whole lines straight out, the new partial line into the
