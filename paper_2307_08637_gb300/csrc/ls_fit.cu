@@ -499,6 +499,12 @@ __global__ void k_fit_route_starts(FitArgs a, const uint32_t* __restrict__ leaf_
   }
 }
 
+// Leaves of at most kLaneLeafMax samples (one chunk) are fitted by one lane
+// each (k_fit_leaf_lane) instead of a warp per chunk and a warp per leaf:
+// with few samples per leaf (retrained models of small buckets) the
+// warp-wide trees cost per leaf, not per sample, on a slow FP64 pipe.
+constexpr uint64_t kLaneLeafMax = 32;
+
 __global__ void k_fit_leaf_chunk_count(FitArgs a) {
   pdl_wait();
   uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -511,7 +517,7 @@ __global__ void k_fit_leaf_chunk_count(FitArgs a) {
   uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
   const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
   uint64_t cnt = ls[i + 1] > ls[i] ? ls[i + 1] - ls[i] : 0;
-  a.lchunk_cnt[g] = (cnt + kChunk - 1) / kChunk;
+  a.lchunk_cnt[g] = cnt <= kLaneLeafMax ? 0 : (cnt + kChunk - 1) / kChunk;  // short leaves: k_fit_leaf_lane
 }
 
 // One warp per leaf chunk of every candidate.
@@ -570,6 +576,7 @@ __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict_
   uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
   uint64_t st = ls[i] < en ? ls[i] : en;
   uint64_t cnt = en - st;
+  if (cnt != 0 && cnt <= kLaneLeafMax) return;  // k_fit_leaf_lane's leaf (uniform across the warp)
   const uint32_t leaf_off = a.models[pl.model].leaf_off;
   Leaf l;
   if (cnt == 0) {
@@ -603,6 +610,71 @@ __global__ void k_fit_leaf_finish(FitArgs a, RunParams rp, uint32_t* __restrict_
     a.leaves[leaf_off + i] = l;
     leaf_cnt[leaf_off + i] = (uint32_t)cnt;
   }
+}
+
+// One lane per (candidate, leaf) of 1..kLaneLeafMax samples: the four sums
+// as the same fixed pairwise tree as warp_chunk_sums (the complete binary
+// tree over the chunk, zero padded; adding +0.0 to a term >= +0 is exact),
+// built in sample order like a binary counter: a new term enters level 0,
+// equal levels merge (earlier partial + later), and at the end the pending
+// partials combine from the lowest level up, which is the padded tree's
+// right spine.  Then the leaf's line and raw clamps as in k_fit_leaf_finish.
+__global__ void k_fit_leaf_lane(FitArgs a, RunParams rp, uint32_t* __restrict__ leaf_cnt) {
+  pdl_wait();
+  constexpr int kLv = 6;  // levels of a 32-term tree
+  static_assert(kLaneLeafMax <= (1u << (kLv - 1)), "the counter holds 2^(kLv-1) terms");
+  const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)a.ncand * a.L) return;
+  const uint32_t c = (uint32_t)(g / a.L), i = (uint32_t)(g % a.L);
+  const Plan& pl = a.plans[a.cand[c]];
+  const uint64_t* s = a.samp + pl.sample_off;
+  const uint32_t* ls = a.leaf_start + (uint64_t)c * (a.L + 1);
+  const uint64_t S = pl.S;
+  const uint64_t en = ls[i + 1] < S ? ls[i + 1] : S;
+  const uint64_t st = ls[i] < en ? ls[i] : en;
+  const uint64_t cnt = en - st;
+  if (cnt == 0 || cnt > kLaneLeafMax) return;
+  const double x0 = ord_value(s[st], rp.dt), Sd = __ull2double_rn(S);
+  double lv[4][kLv];
+  uint32_t mask = 0;
+  for (uint64_t j = st; j < en; ++j) {
+    const double X = __dsub_rn(ord_value(s[j], rp.dt), x0);
+    const double y = __ddiv_rn(__ull2double_rn(j), Sd);
+    double cy[4] = {X, y, __dmul_rn(X, y), __dmul_rn(X, X)};
+    bool open = true;
+#pragma unroll
+    for (int k = 0; k < kLv; ++k) {
+      if (!open) continue;
+      if (mask & (1u << k)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cy[q] = __dadd_rn(lv[q][k], cy[q]);
+        mask &= ~(1u << k);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lv[q][k] = cy[q];
+        mask |= 1u << k;
+        open = false;
+      }
+    }
+  }
+  double sm[4] = {0.0, 0.0, 0.0, 0.0};
+  bool have = false;
+#pragma unroll
+  for (int k = 0; k < kLv; ++k) {
+    if (!(mask & (1u << k))) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sm[q] = have ? __dadd_rn(lv[q][k], sm[q]) : lv[q][k];
+    have = true;
+  }
+  Leaf l;
+  const double x_last = ord_value(s[en - 1], rp.dt);
+  l.x0 = x0;
+  linfit(__ull2double_rn(cnt), sm[0], sm[1], sm[2], sm[3], &l.a, &l.b);
+  l.lo = leaf_eval(l, x0);  // raw min of the leaf (slope >= 0)
+  l.hi = leaf_eval(l, x_last);  // raw max
+  const uint32_t leaf_off = a.models[pl.model].leaf_off;
+  a.leaves[leaf_off + i] = l;
+  leaf_cnt[leaf_off + i] = (uint32_t)cnt;
 }
 
 // Monotone RMI (Sec. 4): hi_i = max(0, max over non-empty j <= i of raw
@@ -1580,9 +1652,10 @@ void launch_fit(const FitArgs& a, const RunParams& rp, cudaStream_t st, uint64_t
   launch_scan_exclusive_u64(a.lchunk_cnt, a.lchunk_prefix, tot, a.scan_tmp, a.scan_tmp_elems, st);
   pdl_launch(k_fit_leaf_partials, grid_for(a.lchunk_bound * 32, 128), 128, 0, st, a, rp);
   pdl_launch(k_fit_leaf_finish, grid_for(tot * 32, 128), 128, 0, st, a, rp, a.leaf_cnt);
+  pdl_launch(k_fit_leaf_lane, grid_for(tot, 128), 128, 0, st, a, rp, a.leaf_cnt);
   pdl_launch(k_fit_monotone, a.ncand, 1024, 0, st, a, a.leaf_cnt);
   pdl_launch(k_fmodel_fit, grid_for((uint64_t)a.ncand * (a.L + 1)), kTPB, 0, st, a);
-  *launches += 13;
+  *launches += 14;
 }
 
 void launch_fmodel(const DModel* models, const Leaf* leaves, const int32_t* slots, uint32_t nslots, uint32_t L,
